@@ -1,0 +1,350 @@
+"""CTR-IBIM benchmark: pair-interactions/s of the full solve path on one GB300.
+
+One step = the whole hot path for one synthetic molecule-sized problem:
+setup (tube, geometry, correction weights, right-hand side), the
+FP32-pair GMRES with FP64 refinement, and the polarization energy.
+Default workload: ellipsoid (4, 3, 2) A with three seeded charges, h = 0.05,
+tube 2h (about 178k tube nodes, 356k unknowns).
+
+value = sum over systems of M^2 x (operator applications in the step) / time,
+the pair count of every dense sum counted in full (including excluded pairs).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+OPS_PER_PAIR_FP32 = 44      # FP32-pipe instructions per pair in the FP32 pair kernel (see the design notes)
+SFU_PER_PAIR = 2            # rsqrt + ex2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--h", type=float, default=0.05, help="grid spacing of the ellipsoid workload")
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the baseline sample")
+    ap.add_argument("--skip-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if _cuda() else "gloo")
+    return world, rank, local
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([v.strip() for v in out.stdout.strip().split(",")])
+            except Exception:  # noqa: BLE001 - sampling is best effort
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for nm, v in zip(names, s[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "power_w_max": max((float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()),
+                                   default=None)}
+
+
+def workload(h):
+    import synthetic as syn
+    prob = syn.ellipsoid_problem(h=h)
+    return prob, {"workload": f"ellipsoid 4x3x2 A, 3 seeded charges, h={h:g} A, tube 2h, eps_in=1, eps_out=80, "
+                              f"kappa=0.1257", "grid": list(prob.grid.n), "solver": None}
+
+
+def cpu_baseline(prob, seconds, threads=None):
+    """The oracle's FP64 punctured dense sum on a bounded sample of target rows (host cores)."""
+    from oracle import native
+    from oracle.system import OracleSystem
+    import synthetic as syn
+    if threads:
+        native.set_threads(threads)
+    cores = native.max_threads()
+    M_probe = None
+    # probe rows to size the sample to ~`seconds` of CPU time
+    rng = np.random.Generator(np.random.PCG64(1))
+    from oracle import geometry
+    geo = geometry.tube_geometry(prob.grid.n, prob.grid.origin, prob.grid.h, prob.sdist, prob.tube)
+    M_probe = geo.M
+    rows = np.sort(rng.choice(M_probe, size=min(M_probe, 4 * cores), replace=False))
+    S = OracleSystem.from_problem(prob, rows=rows, tables=None,
+                                  table_cache=os.path.join(ROOT, "oracle", "_build", "cache"))
+    p = syn.random_density(S.M, seed=2)
+    t0 = time.perf_counter()
+    S.punctured_sum(p, rows)
+    dt = time.perf_counter() - t0
+    rate = rows.size * S.M / dt
+    n_rows = int(min(S.M, max(cores, rate * seconds / S.M)))
+    rows2 = np.sort(rng.choice(S.M, size=n_rows, replace=False))
+    S2 = OracleSystem.from_problem(prob, rows=rows2, tables=S.T)
+    t0 = time.perf_counter()
+    S2.punctured_sum(p, rows2)
+    dt2 = time.perf_counter() - t0
+    return {"value": rows2.size * S2.M / dt2, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 punctured dense sum of {rows2.size} sampled target rows x {S2.M} sources "
+                      f"({rows2.size * S2.M:.3g} pairs, {dt2:.1f} s) of the same workload"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, timed on the host cores, as the reference arm."""
+    if rank != 0:
+        return
+    prob, cfg = workload(args.h)
+    t_all = []
+    res = None
+    steps = []
+    for it in range(args.warmup + args.steps):
+        res = cpu_baseline(prob, seconds=max(2.0, min(args.cpu_seconds, 20.0)))
+        if it >= args.warmup:
+            steps.append(res["value"])
+    value = statistics.median(steps)
+    line = {"impl": "reference", "metric": "CTR-IBIM matvec pair-interactions/s", "value": value,
+            "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2210_03699_gb300 as ctr
+
+    prob, cfg = workload(args.h)
+    prec = ctr.FP32_REFINE if args.precision == "fp32_refine" else ctr.FP64
+    opts = ctr.Options(tube_halfwidth=prob.tube, precision=prec, tol=1e-10)
+    cfg["solver"] = f"{args.precision}, GMRES restart {opts.restart}, tol {opts.tol:g}"
+    cfg["l2"] = "256 MiB buffer written between timed steps (L2 flush, outside the step events)"
+    cfg["parallelism"] = f"replicas x{world}"
+    stream = torch.cuda.current_stream()
+    sd_dev = torch.tensor(prob.sdist, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
+            psi, dpsi, info = G.solve(device=True)
+            Gp, _ = G.energy(psi, dpsi)
+            return G.M, info, Gp
+
+    for _ in range(args.warmup):
+        M, info, Gp = step()
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = []
+    pairs = 0.0
+    infos = []
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M, info, Gp = step()
+            e1.record(stream)
+            ev.append((e0, e1))
+            infos.append(info)
+            pairs += float(M) ** 2 * (info.matvecs_fp32 + info.matvecs_fp64)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    t_max = max_over_ranks(t_dev, world)
+    pairs_all = sum_over_ranks(pairs, world)
+    value = pairs_all / t_max
+
+    # kernel-level roofline: one FP32-pair operator application, timed on the stream
+    with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
+        x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, 2 * G.M), device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(2):
+            G.matvec(x, ctr.FP32_REFINE, out=y)
+        reps = 5
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            G.matvec(x, ctr.FP32_REFINE, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_mv32 = e0.elapsed_time(e1) * 1e-3 / reps
+        e0.record(stream)
+        G.matvec(x, ctr.FP64, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_mv64 = e0.elapsed_time(e1) * 1e-3
+        Mk = G.M
+    # peaks from the probes (FP32 pipe)
+    rate_ffma = ctypes_probe(ctr, 0)
+    rate_ex2 = ctypes_probe(ctr, 2)
+    rate_dfma = ctypes_probe(ctr, 4)
+    peak_pairs = rate_ffma / OPS_PER_PAIR_FP32
+    achieved_pairs = Mk * Mk / t_mv32
+
+    # e2e through the public API with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        h2d = prob.sdist.nbytes + prob.charge_xyz.nbytes + prob.charge_q.nbytes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_pairs = 0.0
+        for _ in range(max(1, args.steps)):
+            with ctr.CtrIbim.from_problem(prob, options=opts) as G:
+                psi, dpsi, info = G.solve(device=False)
+                Gp, _ = G.energy(psi, dpsi)
+                e2e_pairs += float(G.M) ** 2 * (info.matvecs_fp32 + info.matvecs_fp64)
+                d2h = psi.nbytes + dpsi.nbytes + 8
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": sum_over_ranks(e2e_pairs, world) / t_e2e, "unit": "pair-interactions/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, args.cpu_seconds)
+
+    if rank == 0:
+        i0 = infos[-1]
+        line = {
+            "metric": "CTR-IBIM matvec pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pairs + f64" if prec == ctr.FP32_REFINE else "f64", "data": "synthetic",
+            "config": dict(cfg, M=int(M), unknowns=int(2 * M), iterations=int(i0.iterations),
+                           refinements=int(i0.refinements), matvecs_fp32=int(i0.matvecs_fp32),
+                           matvecs_fp64=int(i0.matvecs_fp64), residual=i0.residual, G_pol=Gp),
+            "roofline": {"bound": "alu", "kernel": "pair_kernel<float4> (FP32 pair sum)",
+                         "achieved": achieved_pairs, "peak": peak_pairs, "unit": "pair-interactions/s",
+                         "frac": achieved_pairs / peak_pairs, "traffic": None,
+                         "peak_basis": f"measured FFMA rate {rate_ffma:.4g}/s / {OPS_PER_PAIR_FP32} FP32 ops per pair",
+                         "ex2_rate": rate_ex2, "dfma_rate": rate_dfma,
+                         "t_matvec_fp32_ms": t_mv32 * 1e3, "t_matvec_fp64_ms": t_mv64 * 1e3},
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "gpu_launches": None,
+            "wall_s": t_wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def ctypes_probe(ctr, kind, iters=20000):
+    import ctypes
+    L = ctr.lib
+    L.ctr_probe_rate.restype = ctypes.c_int
+    L.ctr_probe_rate.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    r = ctypes.c_double()
+    s = ctypes.c_double()
+    st = L.ctr_probe_rate(kind, iters, ctypes.byref(r), ctypes.byref(s))
+    return float(r.value) if st == 0 else None
+
+
+if __name__ == "__main__":
+    main()

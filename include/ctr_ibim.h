@@ -1,0 +1,199 @@
+/*
+ * ctr_ibim.h -- C ABI of the GB300 CTR-IBIM engine.
+ *
+ * Solves the linearized Poisson-Boltzmann interface problem (Eq. 1.1) through
+ * the boundary integral pair of Eqs. (1.2)-(1.3), written as volume integrals
+ * over a tube around the surface (Sec. 2.1, Eq. 2.13) and discretized on the
+ * grid nodes of the tube by the corrected trapezoidal rule (Sec. 2.2,
+ * Eqs. 2.14-2.15; matrix form Eq. 2.30, corrections of Sec. 2.4).
+ *
+ * Conventions shared by every entry point:
+ *   - Units are those of the paper (lengths in Angstrom, charges in e,
+ *     G0 = 1/(4 pi r), no Coulomb constant).
+ *   - Grid node (i, j, k) sits at origin + h (i, j, k); grid arrays are flat,
+ *     x fastest: index i + nx (j + ny k).
+ *   - The signed distance is positive OUTSIDE the molecule (the paper, Sec.
+ *     2.1, uses the opposite sign); the normal grad d then points outward.
+ *   - The M unknown nodes are the grid nodes with |d| < eps, in increasing
+ *     grid index; vectors of unknowns are p = [rho1 (M); rho2 (M)], rho1 the
+ *     potential psi, rho2 its interior normal derivative (Eq. 2.13).
+ *   - "Host" pointers are ordinary CPU memory; with on_device != 0 the
+ *     pointer must be CUDA device memory of the handle's device.  The caller
+ *     owns every buffer it passes; the library copies inputs and keeps no
+ *     caller pointer after a call returns.
+ *   - Every call returns CTR_OK (0) on success, CTR_NOT_CONVERGED (1) when a
+ *     solve stops at its iteration limit (outputs are still written), or a
+ *     negative status.  ctr_last_error() gives a message for the calling
+ *     thread.  No C++ exception crosses this interface.
+ *   - One handle is used by one host thread at a time.  All device work of
+ *     a handle runs on the stream given at setup; calls return after that
+ *     stream has finished the call's work (results are ready).
+ */
+#ifndef CTR_IBIM_H
+#define CTR_IBIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CTR_OK 0
+#define CTR_NOT_CONVERGED 1
+#define CTR_ERR_INVALID (-1)       /* a bad argument (null pointer, size, option) */
+#define CTR_ERR_EMPTY_TUBE (-2)    /* no grid node with |d| < eps */
+#define CTR_ERR_GRID_MARGIN (-3)   /* a tube node lies within 2 nodes of the grid boundary */
+#define CTR_ERR_CUDA (-4)          /* a CUDA runtime error */
+#define CTR_ERR_NOMEM (-5)         /* device allocation failed */
+#define CTR_ERR_NUMERIC (-6)       /* a non-finite value appeared (geometry or solve) */
+#define CTR_ERR_DEVICE_WAIT (-7)   /* a kernel gave up a bounded wait (internal error) */
+#define CTR_ERR_CAPACITY (-8)      /* request larger than a fixed capacity */
+
+enum { CTR_FP64 = 0, CTR_FP32_REFINE = 1 };
+
+typedef struct {
+    int64_t n[3];       /* nodes per axis (nx, ny, nz), each >= 5 */
+    double origin[3];   /* coordinates of node (0, 0, 0) */
+    double h;           /* grid spacing, > 0 */
+} ctr_grid;
+
+typedef struct {
+    double tube_halfwidth; /* eps of the tube |d| < eps; <= 0 selects 2h (Secs. 2.5, 3.3) */
+    int precision;         /* CTR_FP64, or CTR_FP32_REFINE: FP32 pair sums inside FP64 refinement */
+    double tol;            /* relative residual |g - A x| / |g| to reach; <= 0 selects 1e-10 */
+    int restart;           /* Krylov vectors per GMRES cycle; <= 0 selects 64 */
+    int max_iter;          /* limit on GMRES iterations (all cycles, all refinements); <= 0: 400 */
+    int max_refine;        /* limit on refinement steps (CTR_FP32_REFINE); <= 0 selects 10 */
+    double inner_tol;      /* relative tolerance of each FP32 GMRES solve; <= 0 selects 1e-5 */
+    int tile_targets;      /* pair-kernel targets per thread (1, 2 or 4); <= 0: automatic */
+} ctr_options;
+
+typedef struct {
+    int64_t iterations;    /* GMRES iterations, all cycles and refinements */
+    int64_t refinements;   /* FP64 residual evaluations (refinement steps) */
+    int64_t matvecs_fp32;  /* FP32-pair operator applications */
+    int64_t matvecs_fp64;  /* FP64-pair operator applications */
+    double residual;       /* final |g - A x| / |g| with the FP64 operator */
+    int converged;         /* 1 when residual <= tol */
+} ctr_solve_info;
+
+typedef struct ctr_ibim ctr_ibim;
+
+/* Fills *opt with the defaults described in ctr_options. */
+void ctr_default_options(ctr_options* opt);
+
+/*
+ * Builds the discrete system for one surface and one set of charges.
+ * Steps, all on the GPU: tube nodes |d| < eps (Eq. 2.4); finite-difference
+ * normals, closest points P = y - d n, principal curvatures and directions,
+ * Jacobian J and weights W = J delta_eps(d) (Sec. 2.1, Eqs. 2.6-2.8, phi of
+ * Sec. 2.6); correction nodes and weights omega^(ij) (Sec. 2.4, Eqs.
+ * 2.19-2.29); right-hand side g (Eq. 2.12).
+ *   grid       grid description (host struct).
+ *   sdist      signed distance, nx*ny*nz doubles, positive outside; host
+ *              memory, or device memory when sdist_on_device != 0.
+ *   eps_in, eps_out  dielectric constants inside / outside (> 0).
+ *   kappa      screening parameter (>= 0), 1/Angstrom.
+ *   n_charges  number of point charges (>= 0); charge_xyz holds 3*n_charges
+ *              doubles (x, y, z per charge), charge_q n_charges doubles; host.
+ *   opt        options, or NULL for the defaults.
+ *   stream     cudaStream_t to run on (NULL: the legacy default stream).
+ *   out        receives the handle; set to NULL on failure.
+ * Errors: CTR_ERR_INVALID, CTR_ERR_EMPTY_TUBE, CTR_ERR_GRID_MARGIN,
+ * CTR_ERR_NUMERIC (non-finite geometry), CTR_ERR_NOMEM, CTR_ERR_CUDA.
+ */
+int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_device,
+                   double eps_in, double eps_out, double kappa,
+                   int64_t n_charges, const double* charge_xyz, const double* charge_q,
+                   const ctr_options* opt, void* stream, ctr_ibim** out);
+
+/* Releases every device and host resource of the handle (NULL is ignored). */
+void ctr_ibim_destroy(ctr_ibim* sys);
+
+/* Number of tube nodes M (the system has 2M unknowns). */
+int ctr_ibim_num_nodes(const ctr_ibim* sys, int64_t* M);
+
+/* Grid linear index of each tube node: M int64 values, host memory. */
+int ctr_ibim_nodes(const ctr_ibim* sys, int64_t* grid_index);
+
+/*
+ * Node geometry (Sec. 2.1), host memory: P (3M, x y z per node), normal
+ * (3M), W = J delta_eps(d) (M).  Any pointer may be NULL to skip it.
+ */
+int ctr_ibim_geometry(const ctr_ibim* sys, double* P, double* normal, double* W);
+
+/* Number of correction entries E = sum over targets of |N_h(y_i)| (Eq. 2.14). */
+int ctr_ibim_num_corrections(const ctr_ibim* sys, int64_t* E);
+
+/*
+ * Correction matrix Omega of Eq. (2.30) in CSR form by target, host memory:
+ * ptr (M+1 int64), node (E int64, ascending plane order per target),
+ * omega11, omega21, omega22 (E doubles each; omega12 is kappa/(4 pi) for
+ * every entry, Theorem of Sec. 2.4.1).  Any output may be NULL.
+ */
+int ctr_ibim_corrections(const ctr_ibim* sys, int64_t* ptr, int64_t* node,
+                         double* omega11, double* omega21, double* omega22);
+
+/* Right-hand side g = [g1; g2] of Eq. (2.12) at the nodes' P: 2M doubles. */
+int ctr_ibim_rhs(const ctr_ibim* sys, double* g, int on_device);
+
+/* Surface area by the tube rule, Eq. (2.6) with f = 1: h^3 sum_j W_j. */
+int ctr_ibim_area(const ctr_ibim* sys, double* area);
+
+/*
+ * y = A x for the operator of Eq. (2.30) (rows of Eqs. 2.14-2.15): the
+ * punctured dense kernel sum, the sparse correction and the diagonal.
+ *   x, y       2M doubles each ([rho1; rho2]); host or device (on_device).
+ *   precision  CTR_FP64: pair kernels in FP64.  CTR_FP32_REFINE: pair
+ *              kernels in FP32 with FP64 accumulation per source tile; the
+ *              correction and diagonal are FP64 in both cases.
+ */
+int ctr_ibim_matvec(ctr_ibim* sys, const double* x, double* y, int precision, int on_device);
+
+/*
+ * Solves A p = g (Eq. 2.30) by GMRES (Sec. 2.5), x0 = 0.  With CTR_FP64 the
+ * operator is FP64 throughout; with CTR_FP32_REFINE each GMRES solve uses the
+ * FP32-pair operator and an FP64 refinement loop r = g - A x recomputes the
+ * residual with FP64 pairs.  Orthogonalisation and Givens rotations are FP64.
+ *   psi, dpsi_n  M doubles each (rho1, rho2); host or device (on_device).
+ *   info         may be NULL.
+ * Returns CTR_NOT_CONVERGED when the iteration limits stop it first.
+ */
+int ctr_ibim_solve(ctr_ibim* sys, double* psi, double* dpsi_n, int on_device, ctr_solve_info* info);
+
+/*
+ * Reaction potential at every charge (Eq. 2.31, trapezoidal rule on the
+ * tube) and the polarization energy G_pol = 1/2 sum_k q_k psi_rxn(z_k)
+ * (Eq. 3.3).  psi, dpsi_n: M doubles each (host or device, on_device);
+ * G_pol: host double; psi_rxn: n_charges host doubles or NULL.
+ */
+int ctr_ibim_energy(ctr_ibim* sys, const double* psi, const double* dpsi_n, int on_device,
+                    double* G_pol, double* psi_rxn);
+
+/*
+ * psi_rxn of Eq. (2.31) at arbitrary points z (away from the surface):
+ * n_points points, xyz 3*n_points doubles (host), out n_points doubles (host).
+ */
+int ctr_ibim_reaction_potential(ctr_ibim* sys, const double* psi, const double* dpsi_n, int on_device,
+                                int64_t n_points, const double* xyz, double* out);
+
+/*
+ * The correction-weight tables of Sec. 2.4.2 as this library computes them
+ * (Ewald summation of the limit of Eq. 2.29): out holds
+ * 2 * 9 * 39 * 39 doubles, [kind][mode][ia][ib], kind 0 = |y|^-1 cos(k psi),
+ * kind 1 = |y|^-1 sin(k psi), k = 0, 2, ..., 16, shift (ia - 19)/32 and
+ * (ib - 19)/32.  Host memory.  Runs on the current device's default stream.
+ */
+int ctr_weight_tables(double* out);
+
+/* Status code -> short description (static string). */
+const char* ctr_status_string(int status);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* ctr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTR_IBIM_H */

@@ -65,8 +65,11 @@ def dominant_axis(n: np.ndarray) -> np.ndarray:
     return np.argmax(np.abs(n), axis=1)
 
 
-def correction_nodes(geo: TubeGeometry):
-    """All (target, node, alpha, beta, eta) entries, targets ascending, planes ascending."""
+def correction_nodes(geo: TubeGeometry, targets=None):
+    """(target, node, alpha, beta, eta) entries, targets ascending, planes ascending.
+
+    `targets`: optional subset of target rows (default: all tube nodes).
+    """
     h, eps = geo.h, geo.eps
     nx, ny, nz = geo.grid_n
     dims = (nx, ny, nz)
@@ -74,7 +77,7 @@ def correction_nodes(geo: TubeGeometry):
     K = int(math.ceil(2.0 * eps / h)) + 2
     ax = dominant_axis(geo.n)
     rows = []
-    for i in range(geo.M):
+    for i in (range(geo.M) if targets is None else sorted(int(t) for t in targets)):
         a = int(ax[i])
         b, c = [v for v in range(3) if v != a]
         Pa, Pb, Pc = geo.P[i, a], geo.P[i, b], geo.P[i, c]
@@ -139,11 +142,32 @@ def fourier_coefficients(samples: np.ndarray):
     return a, b
 
 
-def interpolated_tables(T: np.ndarray, alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
-    """Tabulated weights interpolated at every (alpha, beta): [E, 2, n_modes]."""
-    out = np.empty((alpha.size, 2, len(tb.MODES)))
-    for e in range(alpha.size):
-        out[e] = tb.interpolate(T, float(alpha[e]), float(beta[e]))
+def interpolated_tables(T: np.ndarray, alpha: np.ndarray, beta: np.ndarray, chunk: int = 8192) -> np.ndarray:
+    """Tabulated weights interpolated at every (alpha, beta): [E, 2, n_modes].
+
+    Same arithmetic as tables.interpolate, for many shifts at once.
+    """
+    E = alpha.size
+    out = np.empty((E, 2, len(tb.MODES)))
+    six = np.arange(6)
+    for s in range(0, E, chunk):
+        a = alpha[s:s + chunk]
+        b = beta[s:s + chunk]
+        ia = np.floor(a / tb.SPACING).astype(np.int64) - 2
+        ib = np.floor(b / tb.SPACING).astype(np.int64) - 2
+        xa = (ia[:, None] + six[None, :]) * tb.SPACING
+        xb = (ib[:, None] + six[None, :]) * tb.SPACING
+        ca = np.ones((a.size, 6))
+        cb = np.ones((a.size, 6))
+        for m in range(6):
+            for l in range(6):
+                if l != m:
+                    ca[:, m] *= (a - xa[:, l]) / (xa[:, m] - xa[:, l])
+                    cb[:, m] *= (b - xb[:, l]) / (xb[:, m] - xb[:, l])
+        IA = ia[:, None, None] + tb.HALF + six[None, :, None]
+        IB = ib[:, None, None] + tb.HALF + six[None, None, :]
+        blk = T[:, :, IA, IB]                                  # [2, modes, e, 6, 6]
+        out[s:s + chunk] = np.einsum("kmeab,ea,eb->ekm", blk, ca, cb)
     return out
 
 
@@ -153,8 +177,8 @@ def weights_from_coefficients(a: np.ndarray, b: np.ndarray, Tint: np.ndarray) ->
     return np.sum(a[:, modes] * Tint[:, 0, :] + b[:, modes] * Tint[:, 1, :], axis=1)
 
 
-def build_correction(geo: TubeGeometry, T: np.ndarray) -> Correction:
-    arr, ax = correction_nodes(geo)
+def build_correction(geo: TubeGeometry, T: np.ndarray, targets=None) -> Correction:
+    arr, ax = correction_nodes(geo, targets)
     tgt = arr[:, 0].astype(np.int64)
     node = arr[:, 1].astype(np.int64)
     alpha, beta, eta = arr[:, 2], arr[:, 3], arr[:, 4]

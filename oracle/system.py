@@ -30,7 +30,9 @@ class OracleSystem:
     """Setup (tube, geometry, correction, rhs) and the operator of Eq. (2.30)."""
 
     def __init__(self, grid_n, origin, h, sdist, eps_in, eps_out, kappa, charge_xyz, charge_q, tube,
-                 tables=None, table_cache=None):
+                 tables=None, table_cache=None, rows=None):
+        """rows: optional subset of target rows whose corrections are built (sampled checks);
+        matvec is then valid for those rows only."""
         self.h = float(h)
         self.eps_in, self.eps_out, self.kappa = float(eps_in), float(eps_out), float(kappa)
         self.ratio = self.eps_out / self.eps_in                         # eps_E / eps_I
@@ -40,7 +42,8 @@ class OracleSystem:
         self.charge_q = np.ascontiguousarray(charge_q, dtype=np.float64).ravel()
         self.geo: TubeGeometry = tube_geometry(grid_n, origin, h, sdist, tube)
         self.T = tables if tables is not None else tb.build_tables(table_cache)
-        self.corr: Correction = build_correction(self.geo, self.T)
+        self.rows = None if rows is None else np.array(sorted(int(r) for r in rows), dtype=np.int64)
+        self.corr: Correction = build_correction(self.geo, self.T, targets=self.rows)
         self.omega11 = (1.0 - self.eps_out / self.eps_in) * self.corr.omega_A
         self.omega22 = (1.0 - self.eps_in / self.eps_out) * self.corr.omega_A
         self.omega21 = self.kappa ** 2 * self.corr.omega_B
@@ -112,6 +115,8 @@ class OracleSystem:
         M = self.M
         p = np.asarray(p, dtype=np.float64)
         r = np.arange(M) if rows is None else np.asarray(rows)
+        if self.rows is not None and not np.all(np.isin(r, self.rows)):
+            raise ValueError("corrections were built for a subset of rows only")
         s1, s2 = self.punctured_sum(p, r)
         c1, c2 = self.correction_apply(p, r)
         out1 = self.lam1 * p[:M][r] + s1 + c1

@@ -28,7 +28,7 @@ design notes):
     path needs table values to ~1e-12).
   * Only even k: every kernel's angular function l is even, l(-y) = l(y), so
     odd Fourier coefficients vanish identically.
-  * N = 16 modes, stencil grid spacing 1/32 on [-18/32, 18/32]^2, tensor
+  * N = 16 modes, stencil grid spacing 1/32 on [-19/32, 19/32]^2, tensor
     Lagrange interpolation of degree 5 (6 x 6 stencil) around (alpha, beta).
 
 Test infrastructure only: see the package docstring.
@@ -45,7 +45,7 @@ from . import native
 N_MODES = 16                  # highest Fourier mode kept
 MODES = tuple(range(0, N_MODES + 1, 2))
 SPACING = 1.0 / 32.0          # stencil grid spacing of (alpha_m, beta_n)
-HALF = 18                     # grid indices -HALF..HALF per axis
+HALF = 19                     # grid indices -HALF..HALF per axis (alpha may round to just below -1/2)
 R0 = 0.3                      # flat-top radius of g
 TOL = 1e-12
 JMAX = 12

@@ -1,0 +1,305 @@
+"""GB300-native CTR-IBIM for the linearized Poisson-Boltzmann equation.
+
+Thin Python binding (argument marshalling only) over the C ABI of
+libctr_ibim.so (include/ctr_ibim.h); every step of the method runs in the
+library's CUDA kernels.  Importing this package loads the library and fails
+loudly when it has not been built (python -m paper_2210_03699_gb300.build).
+
+Arrays may be numpy (host) or torch CUDA tensors (device, float64,
+contiguous); outputs follow the input kind unless stated otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "library_path", "lib",
+           "FP64", "FP32_REFINE"]
+
+FP64 = 0
+FP32_REFINE = 1
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+class CtrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64 * 3), ("origin", ctypes.c_double * 3), ("h", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("tube_halfwidth", ctypes.c_double), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("refinements", ctypes.c_int64),
+                ("matvecs_fp32", ctypes.c_int64), ("matvecs_fp64", ctypes.c_int64),
+                ("residual", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+@dataclasses.dataclass
+class Options:
+    tube_halfwidth: float = 0.0
+    precision: int = FP64
+    tol: float = 1e-10
+    restart: int = 64
+    max_iter: int = 400
+    max_refine: int = 10
+    inner_tol: float = 1e-5
+    tile_targets: int = 0
+
+    def _c(self) -> _Options:
+        return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
+                        self.max_refine, self.inner_tol, self.tile_targets)
+
+
+@dataclasses.dataclass
+class SolveInfo:
+    iterations: int
+    refinements: int
+    matvecs_fp32: int
+    matvecs_fp64: int
+    residual: float
+    converged: bool
+    status: int
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libctr_ibim.so is not built ({path}); run python -m paper_2210_03699_gb300.build")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    sig = {
+        "ctr_default_options": (None, [ctypes.POINTER(_Options)]),
+        "ctr_ibim_setup": (ctypes.c_int, [ctypes.POINTER(_Grid), P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int64, P, P, ctypes.POINTER(_Options), P,
+                                          ctypes.POINTER(P)]),
+        "ctr_ibim_destroy": (None, [P]),
+        "ctr_ibim_num_nodes": (ctypes.c_int, [P, _I64]),
+        "ctr_ibim_nodes": (ctypes.c_int, [P, P]),
+        "ctr_ibim_geometry": (ctypes.c_int, [P, P, P, P]),
+        "ctr_ibim_num_corrections": (ctypes.c_int, [P, _I64]),
+        "ctr_ibim_corrections": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ctr_ibim_rhs": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "ctr_ibim_area": (ctypes.c_int, [P, _D]),
+        "ctr_ibim_matvec": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int]),
+        "ctr_ibim_solve": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.POINTER(_Info)]),
+        "ctr_ibim_energy": (ctypes.c_int, [P, P, P, ctypes.c_int, _D, P]),
+        "ctr_ibim_reaction_potential": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int64, P, P]),
+        "ctr_weight_tables": (ctypes.c_int, [P]),
+        "ctr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "ctr_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int, allow=(0,)):
+    if status in allow:
+        return status
+    msg = lib.ctr_last_error().decode() or lib.ctr_status_string(status).decode()
+    raise CtrError(status, msg)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _dptr(x, n=None):
+    """(pointer, on_device) for a float64 contiguous numpy array or torch CUDA tensor."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda:
+            raise TypeError("device arrays must be contiguous float64 CUDA tensors")
+        if n is not None and x.numel() != n:
+            raise ValueError(f"expected {n} elements, got {x.numel()}")
+        return ctypes.c_void_p(x.data_ptr()), 1
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} elements, got {a.size}")
+    return a, 0
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # noqa: BLE001 - torch is optional for the binding
+        pass
+    return ctypes.c_void_p(None)
+
+
+class CtrIbim:
+    """One discretized CTR-IBIM system (surface + charges) resident on the GPU."""
+
+    def __init__(self, grid_n, origin, h, sdist, eps_in, eps_out, kappa, charge_xyz, charge_q,
+                 options: Options | None = None, stream=None):
+        g = _Grid((ctypes.c_int64 * 3)(*[int(v) for v in grid_n]), (ctypes.c_double * 3)(*[float(v) for v in origin]),
+                  float(h))
+        n_total = int(grid_n[0]) * int(grid_n[1]) * int(grid_n[2])
+        sd, sd_dev = _dptr(sdist, n_total)
+        xyz = np.ascontiguousarray(charge_xyz, dtype=np.float64).reshape(-1, 3)
+        q = np.ascontiguousarray(charge_q, dtype=np.float64).ravel()
+        if xyz.shape[0] != q.size:
+            raise ValueError("charge_xyz and charge_q disagree")
+        self.options = options or Options()
+        opt = self.options._c()
+        self._stream = stream if stream is not None else _current_stream()
+        handle = ctypes.c_void_p()
+        sd_p = sd.ctypes.data_as(ctypes.c_void_p) if not sd_dev else sd
+        st = lib.ctr_ibim_setup(ctypes.byref(g), sd_p, sd_dev, float(eps_in), float(eps_out), float(kappa), q.size,
+                                xyz.ctypes.data_as(ctypes.c_void_p), q.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(opt), self._stream, ctypes.byref(handle))
+        _check(st)
+        self._h = handle
+        self.n_charges = q.size
+        Mv = ctypes.c_int64()
+        _check(lib.ctr_ibim_num_nodes(self._h, ctypes.byref(Mv)))
+        self.M = int(Mv.value)
+        Ev = ctypes.c_int64()
+        _check(lib.ctr_ibim_num_corrections(self._h, ctypes.byref(Ev)))
+        self.E = int(Ev.value)
+
+    @classmethod
+    def from_problem(cls, prob, options: Options | None = None, stream=None, sdist=None):
+        g = prob.grid
+        return cls(g.n, g.origin, g.h, prob.sdist if sdist is None else sdist, prob.eps_in, prob.eps_out,
+                   prob.kappa, prob.charge_xyz, prob.charge_q,
+                   options=options or Options(tube_halfwidth=prob.tube), stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.ctr_ibim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ inspection
+    def nodes(self) -> np.ndarray:
+        out = np.empty(self.M, dtype=np.int64)
+        _check(lib.ctr_ibim_nodes(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def geometry(self):
+        P = np.empty((self.M, 3))
+        n = np.empty((self.M, 3))
+        W = np.empty(self.M)
+        _check(lib.ctr_ibim_geometry(self._h, P.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                                     W.ctypes.data_as(ctypes.c_void_p)))
+        return P, n, W
+
+    def corrections(self):
+        ptr = np.empty(self.M + 1, dtype=np.int64)
+        node = np.empty(self.E, dtype=np.int64)
+        w = np.empty((3, self.E))
+        _check(lib.ctr_ibim_corrections(self._h, ptr.ctypes.data_as(ctypes.c_void_p),
+                                        node.ctypes.data_as(ctypes.c_void_p), w[0].ctypes.data_as(ctypes.c_void_p),
+                                        w[1].ctypes.data_as(ctypes.c_void_p), w[2].ctypes.data_as(ctypes.c_void_p)))
+        return ptr, node, w
+
+    def rhs(self) -> np.ndarray:
+        g = np.empty(2 * self.M)
+        _check(lib.ctr_ibim_rhs(self._h, g.ctypes.data_as(ctypes.c_void_p), 0))
+        return g
+
+    def area(self) -> float:
+        a = ctypes.c_double()
+        _check(lib.ctr_ibim_area(self._h, ctypes.byref(a)))
+        return float(a.value)
+
+    # ------------------------------------------------------------ operator / solve / energy
+    def matvec(self, x, precision: int = FP64, out=None):
+        n = 2 * self.M
+        xp, dev = _dptr(x, n)
+        if dev:
+            import torch
+            y = out if out is not None else torch.empty_like(x)
+            yp, _ = _dptr(y, n)
+            _check(lib.ctr_ibim_matvec(self._h, xp, yp, int(precision), 1))
+            return y
+        y = np.empty(n)
+        _check(lib.ctr_ibim_matvec(self._h, xp.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p),
+                                   int(precision), 0))
+        return y
+
+    def solve(self, device: bool = False):
+        info = _Info()
+        if device:
+            import torch
+            psi = torch.empty(self.M, dtype=torch.float64, device="cuda")
+            dpsi = torch.empty(self.M, dtype=torch.float64, device="cuda")
+            st = lib.ctr_ibim_solve(self._h, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(dpsi.data_ptr()), 1,
+                                    ctypes.byref(info))
+        else:
+            psi = np.empty(self.M)
+            dpsi = np.empty(self.M)
+            st = lib.ctr_ibim_solve(self._h, psi.ctypes.data_as(ctypes.c_void_p), dpsi.ctypes.data_as(ctypes.c_void_p),
+                                    0, ctypes.byref(info))
+        _check(st, allow=(0, 1))
+        return psi, dpsi, SolveInfo(info.iterations, info.refinements, info.matvecs_fp32, info.matvecs_fp64,
+                                    info.residual, bool(info.converged), st)
+
+    def energy(self, psi, dpsi):
+        p, dev = _dptr(psi, self.M)
+        d, dev2 = _dptr(dpsi, self.M)
+        if dev != dev2:
+            raise ValueError("psi and dpsi must both be host or both device arrays")
+        G = ctypes.c_double()
+        prx = np.empty(self.n_charges)
+        pp = p if dev else p.ctypes.data_as(ctypes.c_void_p)
+        dd = d if dev else d.ctypes.data_as(ctypes.c_void_p)
+        _check(lib.ctr_ibim_energy(self._h, pp, dd, dev, ctypes.byref(G), prx.ctypes.data_as(ctypes.c_void_p)))
+        return float(G.value), prx
+
+    def reaction_potential(self, psi, dpsi, points):
+        p, dev = _dptr(psi, self.M)
+        d, _ = _dptr(dpsi, self.M)
+        z = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        out = np.empty(z.shape[0])
+        pp = p if dev else p.ctypes.data_as(ctypes.c_void_p)
+        dd = d if dev else d.ctypes.data_as(ctypes.c_void_p)
+        _check(lib.ctr_ibim_reaction_potential(self._h, pp, dd, dev, z.shape[0], z.ctypes.data_as(ctypes.c_void_p),
+                                               out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+
+def weight_tables() -> np.ndarray:
+    """The library's correction-weight tables, shape (2, 9, 39, 39) (see ctr_weight_tables)."""
+    out = np.empty((2, 9, 39, 39))
+    _check(lib.ctr_weight_tables(out.ctypes.data_as(ctypes.c_void_p)))
+    return out

@@ -1,0 +1,372 @@
+// C ABI entry points (declared in include/ctr_ibim.h): argument checks, handle
+// lifetime, host/device staging.  No exception crosses this boundary.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace ctr {
+
+static thread_local std::string t_last_error;
+
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+    set_last_error(msg);
+    return status;
+}
+
+}  // namespace ctr
+
+using namespace ctr;
+
+namespace {
+
+int copy_in(const double* src, int on_device, int64_t n, DevBuf& tmp, const double** out, cudaStream_t st) {
+    if (on_device) {
+        *out = src;
+        return CTR_OK;
+    }
+    CTR_TRY(tmp.alloc(sizeof(double) * (n > 0 ? n : 1)));
+    if (n > 0) CTR_CUDA_TRY(cudaMemcpyAsync(tmp.p, src, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    *out = tmp.as<double>();
+    return CTR_OK;
+}
+
+int use_device(const ctr_ibim* s) {
+    int cur = -1;
+    CTR_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != s->device) CTR_CUDA_TRY(cudaSetDevice(s->device));
+    return CTR_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return fail(CTR_ERR_NOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(CTR_ERR_INVALID, "unexpected internal exception");
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void ctr_default_options(ctr_options* o) {
+    if (!o) return;
+    o->tube_halfwidth = 0.0;
+    o->precision = CTR_FP64;
+    o->tol = 1e-10;
+    o->restart = 64;
+    o->max_iter = 400;
+    o->max_refine = 10;
+    o->inner_tol = 1e-5;
+    o->tile_targets = 0;
+}
+
+const char* ctr_status_string(int st) {
+    switch (st) {
+        case CTR_OK: return "ok";
+        case CTR_NOT_CONVERGED: return "not converged";
+        case CTR_ERR_INVALID: return "invalid argument";
+        case CTR_ERR_EMPTY_TUBE: return "empty tube";
+        case CTR_ERR_GRID_MARGIN: return "tube node too close to the grid boundary";
+        case CTR_ERR_CUDA: return "CUDA error";
+        case CTR_ERR_NOMEM: return "out of device memory";
+        case CTR_ERR_NUMERIC: return "non-finite value";
+        case CTR_ERR_DEVICE_WAIT: return "bounded device wait expired";
+        case CTR_ERR_CAPACITY: return "capacity exceeded";
+        default: return "unknown status";
+    }
+}
+
+const char* ctr_last_error(void) { return t_last_error.c_str(); }
+
+void ctr_ibim_destroy(ctr_ibim* s) {
+    if (!s) return;
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != s->device) cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    delete s;
+    if (cur >= 0) cudaSetDevice(cur);
+}
+
+int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_device, double eps_in, double eps_out,
+                   double kappa, int64_t n_charges, const double* charge_xyz, const double* charge_q,
+                   const ctr_options* opt, void* stream, ctr_ibim** out) {
+    return guarded([&]() -> int {
+        if (!out) return fail(CTR_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        if (!grid || !sdist) return fail(CTR_ERR_INVALID, "grid or sdist is NULL");
+        for (int c = 0; c < 3; ++c)
+            if (grid->n[c] < 5) return fail(CTR_ERR_INVALID, "grid needs at least 5 nodes per axis");
+        if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return fail(CTR_ERR_INVALID, "grid spacing must be > 0");
+        const int64_t total = grid->n[0] * grid->n[1] * grid->n[2];
+        if (total > ((int64_t)1 << 31) - 1) return fail(CTR_ERR_CAPACITY, "grid larger than 2^31 nodes");
+        if (!(eps_in > 0.0) || !(eps_out > 0.0) || !(kappa >= 0.0))
+            return fail(CTR_ERR_INVALID, "eps_in, eps_out must be > 0 and kappa >= 0");
+        if (n_charges < 0 || (n_charges > 0 && (!charge_xyz || !charge_q)))
+            return fail(CTR_ERR_INVALID, "bad charges");
+        ctr_options o;
+        ctr_default_options(&o);
+        if (opt) {
+            o = *opt;
+            if (!(o.tol > 0)) o.tol = 1e-10;
+            if (o.restart <= 0) o.restart = 64;
+            if (o.max_iter <= 0) o.max_iter = 400;
+            if (o.max_refine <= 0) o.max_refine = 10;
+            if (!(o.inner_tol > 0)) o.inner_tol = 1e-5;
+            if (o.precision != CTR_FP64 && o.precision != CTR_FP32_REFINE)
+                return fail(CTR_ERR_INVALID, "unknown precision");
+        }
+        if (o.restart > 1000) return fail(CTR_ERR_INVALID, "restart must be <= 1000");
+        ctr_ibim* s = new ctr_ibim();
+        s->opt = o;
+        CTR_CUDA_TRY(cudaGetDevice(&s->device));
+        s->stream = static_cast<cudaStream_t>(stream);
+        for (int c = 0; c < 3; ++c) {
+            s->n[c] = grid->n[c];
+            s->origin[c] = grid->origin[c];
+        }
+        s->h = grid->h;
+        s->eps = (o.tube_halfwidth > 0.0) ? o.tube_halfwidth : 2.0 * grid->h;
+        s->eps_in = eps_in;
+        s->eps_out = eps_out;
+        s->kappa = kappa;
+        s->nc = n_charges;
+        auto cleanup = [&](int st) {
+            if (s->stream) cudaStreamSynchronize(s->stream);
+            delete s;
+            return st;
+        };
+        int st = s->err.alloc(sizeof(int));
+        if (st < 0) return cleanup(st);
+        if (cudaMemsetAsync(s->err.p, 0, sizeof(int), s->stream) != cudaSuccess)
+            return cleanup(fail(CTR_ERR_CUDA, "memset"));
+        DevBuf sd_tmp;
+        const double* d_sd = nullptr;
+        st = copy_in(sdist, sdist_on_device, total, sd_tmp, &d_sd, s->stream);
+        if (st < 0) return cleanup(st);
+        st = setup_tube_and_geometry(s, d_sd);
+        if (st < 0) return cleanup(st);
+        // charges as SoA x[nc], y[nc], z[nc], q[nc]
+        std::vector<double> ch(4 * (size_t)std::max<int64_t>(n_charges, 1), 0.0);
+        for (int64_t c = 0; c < n_charges; ++c) {
+            ch[c] = charge_xyz[3 * c];
+            ch[n_charges + c] = charge_xyz[3 * c + 1];
+            ch[2 * n_charges + c] = charge_xyz[3 * c + 2];
+            ch[3 * n_charges + c] = charge_q[c];
+        }
+        st = s->charges.alloc(sizeof(double) * ch.size());
+        if (st < 0) return cleanup(st);
+        if (cudaMemcpyAsync(s->charges.p, ch.data(), sizeof(double) * ch.size(), cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess)
+            return cleanup(fail(CTR_ERR_CUDA, "charge upload"));
+        st = setup_rhs(s);
+        if (st < 0) return cleanup(st);
+        st = plan_pairs(s);
+        if (st < 0) return cleanup(st);
+        st = s->vecs.alloc(sizeof(double) * 6 * 2 * (size_t)s->M);
+        if (st < 0) return cleanup(st);
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return cleanup(fail(CTR_ERR_CUDA, "setup sync"));
+        st = check_device_error(s, "setup");
+        if (st < 0) return cleanup(st);
+        *out = s;
+        return CTR_OK;
+    });
+}
+
+int ctr_ibim_num_nodes(const ctr_ibim* s, int64_t* M) {
+    if (!s || !M) return fail(CTR_ERR_INVALID, "NULL argument");
+    *M = s->M;
+    return CTR_OK;
+}
+
+int ctr_ibim_num_corrections(const ctr_ibim* s, int64_t* E) {
+    if (!s || !E) return fail(CTR_ERR_INVALID, "NULL argument");
+    *E = s->E;
+    return CTR_OK;
+}
+
+int ctr_ibim_nodes(const ctr_ibim* s, int64_t* gi) {
+    if (!s || !gi) return fail(CTR_ERR_INVALID, "NULL argument");
+    CTR_TRY(use_device(s));
+    CTR_CUDA_TRY(cudaMemcpyAsync(gi, s->lin.p, sizeof(int64_t) * s->M, cudaMemcpyDeviceToHost, s->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return CTR_OK;
+}
+
+int ctr_ibim_geometry(const ctr_ibim* s, double* P, double* normal, double* W) {
+    if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        const int64_t M = s->M;
+        std::vector<double> h(6 * (size_t)M + M);
+        CTR_CUDA_TRY(cudaMemcpyAsync(h.data(), s->nodes.p, sizeof(double) * 7 * M, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        for (int64_t m = 0; m < M; ++m) {
+            if (P) {
+                P[3 * m] = h[m];
+                P[3 * m + 1] = h[M + m];
+                P[3 * m + 2] = h[2 * M + m];
+            }
+            if (normal) {
+                normal[3 * m] = h[3 * M + m];
+                normal[3 * m + 1] = h[4 * M + m];
+                normal[3 * m + 2] = h[5 * M + m];
+            }
+            if (W) W[m] = h[6 * M + m];
+        }
+        return CTR_OK;
+    });
+}
+
+int ctr_ibim_corrections(const ctr_ibim* s, int64_t* ptr, int64_t* node, double* w11, double* w21, double* w22) {
+    if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        const int64_t M = s->M, E = s->E;
+        std::vector<int32_t> p(M + 1), nd(E);
+        std::vector<double> w(3 * (size_t)E);
+        CTR_CUDA_TRY(cudaMemcpyAsync(p.data(), s->corr_ptr.p, sizeof(int32_t) * (M + 1), cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaMemcpyAsync(nd.data(), s->corr_node.p, sizeof(int32_t) * E, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaMemcpyAsync(w.data(), s->corr_w.p, sizeof(double) * 3 * E, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (ptr) for (int64_t i = 0; i <= M; ++i) ptr[i] = p[i];
+        if (node) for (int64_t e = 0; e < E; ++e) node[e] = nd[e];
+        if (w11) std::memcpy(w11, w.data(), sizeof(double) * E);
+        if (w21) std::memcpy(w21, w.data() + E, sizeof(double) * E);
+        if (w22) std::memcpy(w22, w.data() + 2 * E, sizeof(double) * E);
+        return CTR_OK;
+    });
+}
+
+int ctr_ibim_rhs(const ctr_ibim* s, double* g, int on_device) {
+    if (!s || !g) return fail(CTR_ERR_INVALID, "NULL argument");
+    CTR_TRY(use_device(s));
+    CTR_CUDA_TRY(cudaMemcpyAsync(g, s->rhs.p, sizeof(double) * 2 * s->M,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return CTR_OK;
+}
+
+int ctr_ibim_area(const ctr_ibim* s, double* area) {
+    if (!s || !area) return fail(CTR_ERR_INVALID, "NULL argument");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        std::vector<double> W(s->M);
+        CTR_CUDA_TRY(cudaMemcpyAsync(W.data(), s->na.W, sizeof(double) * s->M, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        double a = 0.0;
+        for (double v : W) a += v;
+        *area = a * s->h * s->h * s->h;
+        return CTR_OK;
+    });
+}
+
+int ctr_ibim_matvec(ctr_ibim* s, const double* x, double* y, int precision, int on_device) {
+    if (!s || !x || !y) return fail(CTR_ERR_INVALID, "NULL argument");
+    if (precision != CTR_FP64 && precision != CTR_FP32_REFINE) return fail(CTR_ERR_INVALID, "unknown precision");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        const int64_t n = 2 * s->M;
+        DevBuf xin, yout;
+        const double* dx = nullptr;
+        CTR_TRY(copy_in(x, on_device, n, xin, &dx, s->stream));
+        double* dy = y;
+        if (!on_device) {
+            CTR_TRY(yout.alloc(sizeof(double) * n));
+            dy = yout.as<double>();
+        }
+        CTR_TRY(apply_operator(s, dx, dy, precision));
+        if (!on_device) CTR_CUDA_TRY(cudaMemcpyAsync(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return check_device_error(s, "matvec");
+    });
+}
+
+int ctr_ibim_solve(ctr_ibim* s, double* psi, double* dpsi_n, int on_device, ctr_solve_info* info) {
+    if (!s || !psi || !dpsi_n) return fail(CTR_ERR_INVALID, "NULL argument");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        ctr_solve_info local;
+        std::memset(&local, 0, sizeof(local));
+        const int64_t M = s->M;
+        DevBuf out;
+        double *dp = psi, *dd = dpsi_n;
+        if (!on_device) {
+            CTR_TRY(out.alloc(sizeof(double) * 2 * M));
+            dp = out.as<double>();
+            dd = dp + M;
+        }
+        int st = solve_system(s, dp, dd, &local);
+        if (info) *info = local;
+        if (st < 0) return st;
+        if (!on_device) {
+            CTR_CUDA_TRY(cudaMemcpyAsync(psi, dp, sizeof(double) * M, cudaMemcpyDeviceToHost, s->stream));
+            CTR_CUDA_TRY(cudaMemcpyAsync(dpsi_n, dd, sizeof(double) * M, cudaMemcpyDeviceToHost, s->stream));
+        }
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return st;
+    });
+}
+
+int ctr_ibim_reaction_potential(ctr_ibim* s, const double* psi, const double* dpsi_n, int on_device, int64_t n_points,
+                                const double* xyz, double* out) {
+    if (!s || !psi || !dpsi_n || (n_points > 0 && (!xyz || !out)) || n_points < 0)
+        return fail(CTR_ERR_INVALID, "NULL argument");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        if (n_points == 0) return CTR_OK;
+        DevBuf p1, p2, z, o;
+        const double *dp = nullptr, *dd = nullptr, *dz = nullptr;
+        CTR_TRY(copy_in(psi, on_device, s->M, p1, &dp, s->stream));
+        CTR_TRY(copy_in(dpsi_n, on_device, s->M, p2, &dd, s->stream));
+        CTR_TRY(copy_in(xyz, 0, 3 * n_points, z, &dz, s->stream));
+        CTR_TRY(o.alloc(sizeof(double) * n_points));
+        CTR_TRY(reaction_potential(s, dp, dd, n_points, dz, o.as<double>()));
+        CTR_CUDA_TRY(cudaMemcpyAsync(out, o.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return CTR_OK;
+    });
+}
+
+int ctr_ibim_energy(ctr_ibim* s, const double* psi, const double* dpsi_n, int on_device, double* G_pol,
+                    double* psi_rxn) {
+    if (!s || !psi || !dpsi_n || !G_pol) return fail(CTR_ERR_INVALID, "NULL argument");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        const int64_t nc = s->nc;
+        *G_pol = 0.0;
+        if (nc == 0) return CTR_OK;
+        std::vector<double> ch(4 * (size_t)nc), xyz(3 * (size_t)nc), prx(nc);
+        CTR_CUDA_TRY(cudaMemcpyAsync(ch.data(), s->charges.p, sizeof(double) * 4 * nc, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        for (int64_t c = 0; c < nc; ++c) {
+            xyz[3 * c] = ch[c];
+            xyz[3 * c + 1] = ch[nc + c];
+            xyz[3 * c + 2] = ch[2 * nc + c];
+        }
+        CTR_TRY(ctr_ibim_reaction_potential(s, psi, dpsi_n, on_device, nc, xyz.data(), prx.data()));
+        double G = 0.0;
+        for (int64_t c = 0; c < nc; ++c) G += ch[3 * nc + c] * prx[c];
+        *G_pol = 0.5 * G;
+        if (psi_rxn) std::memcpy(psi_rxn, prx.data(), sizeof(double) * nc);
+        return CTR_OK;
+    });
+}
+
+int ctr_weight_tables(double* out) {
+    if (!out) return fail(CTR_ERR_INVALID, "NULL argument");
+    DevBuf t;
+    CTR_TRY(t.alloc(sizeof(double) * kTabSize));
+    CTR_TRY(weight_tables_device(t.as<double>(), nullptr));
+    CTR_CUDA_TRY(cudaMemcpy(out, t.p, sizeof(double) * kTabSize, cudaMemcpyDeviceToHost));
+    return CTR_OK;
+}
+
+}  // extern "C"

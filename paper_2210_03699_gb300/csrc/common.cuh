@@ -1,0 +1,175 @@
+// Internal declarations of the GB300 CTR-IBIM engine (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "ctr_ibim.h"
+
+namespace ctr {
+
+// ---------------------------------------------------------------- constants
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kModes = 9;          // Fourier modes k = 0, 2, ..., 16 (even: every l is even)
+constexpr int kModeMax = 16;
+constexpr int kSamples = 64;       // samples of l(theta) for the DFT, 4 * 16
+constexpr int kTabHalf = 19;       // table shifts (i - 19)/32, i = 0..38
+constexpr int kTabN = 2 * kTabHalf + 1;
+constexpr double kTabSpacing = 1.0 / 32.0;
+constexpr int kTabSize = 2 * kModes * kTabN * kTabN;
+
+// device-side error word bits
+enum : int { kErrWait = 1, kErrMargin = 2, kErrNumeric = 4, kErrCapacity = 8 };
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    int status;
+    std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+
+#define CTR_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            return ::ctr::fail(e_ == cudaErrorMemoryAllocation ? CTR_ERR_NOMEM : CTR_ERR_CUDA, \
+                               std::string(#expr) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                   \
+    } while (0)
+
+#define CTR_TRY(expr)              \
+    do {                           \
+        int s_ = (expr);           \
+        if (s_ < 0) return s_;     \
+    } while (0)
+
+// ---------------------------------------------------------------- device buffers
+// Plain owning device allocation (cudaMalloc / cudaFree).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t n) {
+        if (n <= bytes && p) return CTR_OK;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(CTR_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        bytes = n;
+        return CTR_OK;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- node data
+// Structure-of-arrays of the tube nodes in FP64 (one allocation).
+struct NodeArrays {
+    double *Px, *Py, *Pz, *nx, *ny, *nz, *W, *d;
+    double *t1x, *t1y, *t1z, *t2x, *t2y, *t2z;  // principal directions
+    double *m1, *m2;                           // M = diag(m1, m2) of the expansions
+    static constexpr int kCount = 16;
+};
+
+// Pair-kernel launch plan for one precision.
+struct PairPlan {
+    int R = 2;          // targets per thread
+    int splits = 1;     // source splits (blockIdx.y)
+    int src_per_split = 0;
+    int target_blocks = 0;
+};
+
+// Per-handle GMRES workspace.
+struct Krylov {
+    int m = 0;           // restart length
+    int64_t n = 0;       // vector length 2M
+    DevBuf V;            // (m+1) x n
+    DevBuf H;            // (m+1) x m, column-major by column j: H[j*(m+1) + i]
+    DevBuf cs, sn, s;    // Givens and rhs of the least-squares problem
+    DevBuf y;            // m
+    DevBuf part;         // partial dot products: (m+1) x nblk
+    DevBuf scal;         // scalars: [0] beta, [1] hnorm, [2] residual estimate, [3] converged flag ...
+    int nblk = 0;
+};
+
+}  // namespace ctr
+
+// The handle behind the opaque C type.
+struct ctr_ibim {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ctr_options opt{};
+    int64_t n[3]{};
+    double origin[3]{};
+    double h = 0, eps = 0, eps_in = 1, eps_out = 1, kappa = 0;
+    int64_t M = 0, E = 0;
+    int64_t nc = 0;
+
+    ctr::DevBuf lin;         // int64 [M] grid index
+    ctr::DevBuf nodes;       // double [16][M]
+    ctr::NodeArrays na{};
+    ctr::DevBuf src32;       // float4 [2M]: {P, a} {n, b}
+    ctr::DevBuf src64;       // double4 [2M]
+    ctr::DevBuf corr_ptr;    // int32 [M+1]
+    ctr::DevBuf corr_node;   // int32 [E]
+    ctr::DevBuf corr_w;      // double [3][E]: omega11, omega21, omega22
+    ctr::DevBuf excl;        // int32 [E] sorted correction nodes per target
+    ctr::DevBuf rhs;         // double [2M]
+    ctr::DevBuf charges;     // double [4][nc]: x, y, z, q
+    ctr::DevBuf partial;     // double scratch of the pair kernels
+    ctr::DevBuf err;         // int device error word
+    ctr::DevBuf vecs;        // double [6][2M] solver vectors
+    ctr::DevBuf red;         // reduction scratch
+    ctr::PairPlan plan32, plan64;
+    ctr::Krylov kr;
+};
+
+namespace ctr {
+
+// setup.cu
+int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist);
+int setup_rhs(ctr_ibim* s);
+// weights.cu
+int weight_tables_device(double* d_tables, cudaStream_t st);
+int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node_of);
+// pairsum.cu
+int plan_pairs(ctr_ibim* s);
+int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision);
+// krylov.cu
+int solve_system(ctr_ibim* s, double* d_psi, double* d_dpsi, ctr_solve_info* info);
+// energy.cu
+int reaction_potential(ctr_ibim* s, const double* d_psi, const double* d_dpsi, int64_t npts,
+                       const double* d_xyz, double* d_out);
+// reductions (krylov.cu)
+int device_dot(ctr_ibim* s, const double* a, const double* b, int64_t n, double* h_out);
+int check_device_error(ctr_ibim* s, const char* where);
+
+// Exclusive scan of n int32 counts into offsets (n+1 entries, last = total), on stream.
+int exclusive_scan_i32(const int32_t* d_counts, int32_t* d_offsets, int64_t n, cudaStream_t st,
+                       DevBuf& scratch);
+
+inline unsigned grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace ctr

@@ -1,0 +1,217 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (arithmetic behind them in the design notes):
+  * integer / decision outputs (tube nodes, correction CSR, node ids): exact;
+  * P and n: exact (both sides evaluate the same unfused IEEE sequence);
+  * W, correction weights, rhs: 1e-12 relative to the largest magnitude;
+  * FP64 operator: 1e-12 relative (max norm), FP64 solve: 1e-10 relative;
+  * FP32-pair operator: 2e-5 relative (FP32 pair terms, FP64 accumulation per tile);
+  * FP32 + FP64-refinement solve: 1e-6 relative in psi, dpsi and G_pol.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import energy as oenergy
+from oracle.system import OracleSystem
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ctr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_03699_gb300 as ctr
+    return ctr
+
+
+@pytest.fixture(scope="module")
+def sphere(ctr, oracle_tables):
+    prob = syn.sphere_problem(h=0.25)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables)
+    G = ctr.CtrIbim.from_problem(prob)
+    yield prob, S, G
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def ellipsoid(ctr, oracle_tables):
+    prob = syn.ellipsoid_problem(h=0.2)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables)
+    G = ctr.CtrIbim.from_problem(prob)
+    yield prob, S, G
+    G.close()
+
+
+def test_weight_tables_match_oracle(ctr, oracle_tables):
+    T = ctr.weight_tables()
+    assert T.shape == oracle_tables.shape == (2, 9, 39, 39)
+    assert np.max(np.abs(T - oracle_tables)) < 1e-11
+
+
+@pytest.mark.parametrize("which", ["sphere", "ellipsoid"])
+def test_setup_parity(which, request):
+    prob, S, G = request.getfixturevalue(which)
+    assert G.M == S.M
+    assert np.array_equal(G.nodes(), S.geo.lin)
+    P, n, W = G.geometry()
+    assert np.array_equal(P, S.geo.P)
+    assert np.array_equal(n, S.geo.n)
+    assert _rel(W, S.geo.W) < 1e-12
+    ptr, node, w = G.corrections()
+    assert np.array_equal(ptr, S.corr.ptr)
+    assert np.array_equal(node, S.corr.node)
+    assert _rel(w[0], S.omega11) < 1e-10
+    assert _rel(w[1], S.omega21) < 1e-10
+    assert _rel(w[2], S.omega22) < 1e-10
+    assert _rel(G.rhs(), S.rhs()) < 1e-12
+    assert abs(G.area() / S.area() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["sphere", "ellipsoid"])
+def test_operator_parity(which, request, ctr):
+    prob, S, G = request.getfixturevalue(which)
+    p = syn.random_density(S.M, seed=11, smooth_points=S.geo.P)
+    ref = S.matvec(p)
+    y64 = G.matvec(p, ctr.FP64)
+    assert _rel(y64, ref) < 1e-12
+    y32 = G.matvec(p, ctr.FP32_REFINE)
+    assert _rel(y32, ref) < 2e-5
+    # deterministic: fixed-order reductions
+    assert np.array_equal(G.matvec(p, ctr.FP64), y64)
+    assert np.array_equal(G.matvec(p, ctr.FP32_REFINE), y32)
+
+
+def test_operator_device_buffers(sphere, ctr):
+    import torch
+    prob, S, G = sphere
+    p = syn.random_density(S.M, seed=3)
+    x = torch.tensor(p, dtype=torch.float64, device="cuda")
+    y = G.matvec(x, ctr.FP64)
+    assert isinstance(y, torch.Tensor) and y.is_cuda
+    assert np.array_equal(y.cpu().numpy(), G.matvec(p, ctr.FP64))
+
+
+def test_solve_fp64_parity(sphere, ctr):
+    prob, S, G = sphere
+    psi_o, dpsi_o, info_o = S.solve(tol=1e-13)
+    G.options.tol = 1e-13
+    G2 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, tol=1e-13))
+    psi, dpsi, info = G2.solve()
+    assert info.converged and info.residual <= 1e-13
+    assert 5 <= info.iterations <= 60
+    assert _rel(psi, psi_o) < 1e-10
+    assert _rel(dpsi, dpsi_o) < 1e-10
+    Gp, prx = G2.energy(psi, dpsi)
+    Go, prx_o = oenergy.polarization_energy(S, psi_o, dpsi_o)
+    assert abs(Gp / Go - 1) < 1e-10
+    # Kirkwood closed form (discretization error at h = 0.25)
+    assert abs(Gp / -0.019695646775266615 - 1) < 5e-4
+    G2.close()
+
+
+def test_solve_fp32_refine_parity(ellipsoid, ctr):
+    prob, S, G = ellipsoid
+    psi_o, dpsi_o, info_o = S.solve(tol=1e-13)
+    Go, _ = oenergy.polarization_energy(S, psi_o, dpsi_o)
+    G32 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube,
+                                                               precision=ctr.FP32_REFINE, tol=1e-11))
+    psi, dpsi, info = G32.solve()
+    assert info.converged and info.refinements >= 1 and info.matvecs_fp32 > info.matvecs_fp64
+    assert _rel(psi, psi_o) < 1e-6
+    assert _rel(dpsi, dpsi_o) < 1e-6
+    Gp, _ = G32.energy(psi, dpsi)
+    assert abs(Gp / Go - 1) < 1e-6
+    # FP64 GPU path on the same system
+    G64 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, tol=1e-13))
+    psi64, dpsi64, _ = G64.solve()
+    assert _rel(psi64, psi_o) < 1e-10
+    G32.close()
+    G64.close()
+
+
+def test_solve_on_device_buffers(sphere, ctr):
+    import torch
+    prob, S, G = sphere
+    psi_h, dpsi_h, _ = G.solve()
+    psi_d, dpsi_d, info = G.solve(device=True)
+    assert isinstance(psi_d, torch.Tensor)
+    assert np.array_equal(psi_d.cpu().numpy(), psi_h)
+    Gh, _ = G.energy(psi_h, dpsi_h)
+    Gd, _ = G.energy(psi_d, dpsi_d)
+    assert Gh == Gd
+
+
+def test_reaction_potential_points(sphere):
+    prob, S, G = sphere
+    psi, dpsi, _ = G.solve()
+    z = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1], [0.0, 0.5, -0.4]])
+    got = G.reaction_potential(psi, dpsi, z)
+    ref = oenergy.reaction_potential(S, psi, dpsi, z)
+    assert _rel(got, ref) < 1e-12
+
+
+# ---------------------------------------------------------------- edge cases
+def test_small_system_and_laplace(ctr, oracle_tables):
+    # fewer nodes than one thread block; kappa = 0 (pure Laplace kernels)
+    prob = syn.sphere_problem(h=0.25, R=0.75, half_box=1.5, kappa=0.0)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables)
+    G = ctr.CtrIbim.from_problem(prob)
+    assert G.M == S.M and G.M < 512
+    p = syn.random_density(S.M, seed=5)
+    assert _rel(G.matvec(p, ctr.FP64), S.matvec(p)) < 1e-12
+    assert _rel(G.matvec(p, ctr.FP32_REFINE), S.matvec(p)) < 2e-5
+    G.close()
+
+
+def test_no_charges_gives_zero_solution(ctr):
+    prob = syn.sphere_problem(h=0.25)
+    G = ctr.CtrIbim(prob.grid.n, prob.grid.origin, prob.grid.h, prob.sdist, 1.0, 80.0, 0.1257,
+                    np.zeros((0, 3)), np.zeros(0))
+    assert np.all(G.rhs() == 0)
+    psi, dpsi, info = G.solve()
+    assert info.converged and np.all(psi == 0) and np.all(dpsi == 0)
+    Gp, prx = G.energy(psi, dpsi)
+    assert Gp == 0.0 and prx.size == 0
+    G.close()
+
+
+def test_error_statuses(ctr):
+    prob = syn.sphere_problem(h=0.25)
+    with pytest.raises(ctr.CtrError) as e:       # empty tube
+        ctr.CtrIbim(prob.grid.n, prob.grid.origin, prob.grid.h, np.full(prob.grid.size, 10.0), 1.0, 80.0, 0.1,
+                    np.zeros((1, 3)), np.ones(1))
+    assert e.value.status == -2
+    g = syn.box_grid((-2.25,) * 3, (2.25,) * 3, 0.25)   # sphere reaches the grid margin
+    with pytest.raises(ctr.CtrError) as e:
+        ctr.CtrIbim(g.n, g.origin, g.h, syn.sphere_sdist(g, 2.0), 1.0, 80.0, 0.1, np.zeros((1, 3)), np.ones(1))
+    assert e.value.status == -3
+
+
+# ---------------------------------------------------------------- full size, sampled rows
+@pytest.mark.parametrize("tile_targets", [2])
+def test_full_size_sampled_rows(ctr, oracle_tables, tile_targets):
+    """Ellipsoid at h = 0.05 (~178k nodes), the benchmark's launch configuration; rows sampled."""
+    prob = syn.ellipsoid_problem(h=0.05)
+    G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, tile_targets=tile_targets))
+    rng = np.random.Generator(np.random.PCG64(7))
+    rows = np.unique(np.concatenate([[0, G.M - 1], rng.integers(0, G.M, size=46)]))
+    S = OracleSystem.from_problem(prob, tables=oracle_tables, rows=rows)
+    assert G.M == S.M > 150_000
+    p = syn.random_density(S.M, seed=13, smooth_points=S.geo.P)
+    ref = S.matvec(p, rows=rows)
+    y64 = G.matvec(p, ctr.FP64)
+    y32 = G.matvec(p, ctr.FP32_REFINE)
+    sel = np.concatenate([rows, G.M + rows])
+    assert _rel(y64[sel], ref) < 1e-12
+    assert _rel(y32[sel], ref) < 2e-5
+    assert np.all(np.isfinite(y32)) and np.all(np.isfinite(y64))
+    G.close()
