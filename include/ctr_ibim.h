@@ -49,7 +49,18 @@ extern "C" {
 #define CTR_ERR_DEVICE_WAIT (-7)   /* a kernel gave up a bounded wait (internal error) */
 #define CTR_ERR_CAPACITY (-8)      /* request larger than a fixed capacity */
 
-enum { CTR_FP64 = 0, CTR_FP32_REFINE = 1 };
+/*
+ * Arithmetic of the dense pair sums (the correction, the diagonal, vectors
+ * and the Krylov algebra are FP64 in every mode):
+ *   CTR_FP64         IEEE FP64 (DFMA).
+ *   CTR_FP32_REFINE  FP32 pair terms, per-tile FP32 sums added in FP64; as a
+ *                    solve mode, GMRES on this operator inside FP64-accurate
+ *                    iterative refinement.
+ *   CTR_DF64         double-FP32 ("float-float") arithmetic on the FP32 pipe:
+ *                    every quantity a pair of floats, about 2^-44 relative
+ *                    accuracy, within 1e-12 of the FP64 operator.
+ */
+enum { CTR_FP64 = 0, CTR_FP32_REFINE = 1, CTR_DF64 = 2 };
 
 typedef struct {
     int64_t n[3];       /* nodes per axis (nx, ny, nz), each >= 5 */
@@ -66,14 +77,16 @@ typedef struct {
     int max_refine;        /* limit on refinement steps (CTR_FP32_REFINE); <= 0 selects 10 */
     double inner_tol;      /* relative tolerance of each FP32 GMRES solve; <= 0 selects 1e-5 */
     int tile_targets;      /* pair-kernel targets per thread (1, 2 or 4); <= 0: automatic */
+    int residual;          /* pair arithmetic of the refinement residual r = g - A x:
+                              CTR_DF64 (the default of ctr_default_options) or CTR_FP64 */
 } ctr_options;
 
 typedef struct {
     int64_t iterations;    /* GMRES iterations, all cycles and refinements */
-    int64_t refinements;   /* FP64 residual evaluations (refinement steps) */
+    int64_t refinements;   /* refinement steps (FP64-accurate residual evaluations) */
     int64_t matvecs_fp32;  /* FP32-pair operator applications */
-    int64_t matvecs_fp64;  /* FP64-pair operator applications */
-    double residual;       /* final |g - A x| / |g| with the FP64 operator */
+    int64_t matvecs_fp64;  /* FP64-accurate (CTR_FP64 or CTR_DF64) operator applications */
+    double residual;       /* final |g - A x| / |g| with the FP64-accurate operator */
     int converged;         /* 1 when residual <= tol */
 } ctr_solve_info;
 
@@ -144,17 +157,19 @@ int ctr_ibim_area(const ctr_ibim* sys, double* area);
  * y = A x for the operator of Eq. (2.30) (rows of Eqs. 2.14-2.15): the
  * punctured dense kernel sum, the sparse correction and the diagonal.
  *   x, y       2M doubles each ([rho1; rho2]); host or device (on_device).
- *   precision  CTR_FP64: pair kernels in FP64.  CTR_FP32_REFINE: pair
- *              kernels in FP32 with FP64 accumulation per source tile; the
- *              correction and diagonal are FP64 in both cases.
+ *   precision  CTR_FP64, CTR_FP32_REFINE or CTR_DF64 (see above): the
+ *              arithmetic of the pair sums; the correction and the diagonal
+ *              are FP64 in every case.
  */
 int ctr_ibim_matvec(ctr_ibim* sys, const double* x, double* y, int precision, int on_device);
 
 /*
- * Solves A p = g (Eq. 2.30) by GMRES (Sec. 2.5), x0 = 0.  With CTR_FP64 the
- * operator is FP64 throughout; with CTR_FP32_REFINE each GMRES solve uses the
- * FP32-pair operator and an FP64 refinement loop r = g - A x recomputes the
- * residual with FP64 pairs.  Orthogonalisation and Givens rotations are FP64.
+ * Solves A p = g (Eq. 2.30) by GMRES (Sec. 2.5), x0 = 0, right-preconditioned
+ * by the diagonal Lambda.  With CTR_FP64 (or CTR_DF64) the operator uses that
+ * pair arithmetic throughout; with CTR_FP32_REFINE each GMRES solve uses the
+ * FP32-pair operator inside a refinement loop whose residual r = g - A x uses
+ * the pair arithmetic opt.residual (CTR_DF64 or CTR_FP64).  Vectors,
+ * orthogonalisation and Givens rotations are FP64.
  *   psi, dpsi_n  M doubles each (rho1, rho2); host or device (on_device).
  *   info         may be NULL.
  * Returns CTR_NOT_CONVERGED when the iteration limits stop it first.

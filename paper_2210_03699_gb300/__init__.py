@@ -19,10 +19,11 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "library_path", "lib",
-           "FP64", "FP32_REFINE"]
+           "FP64", "FP32_REFINE", "DF64"]
 
 FP64 = 0
 FP32_REFINE = 1
+DF64 = 2
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -41,7 +42,7 @@ class _Grid(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("tube_halfwidth", ctypes.c_double), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -60,10 +61,11 @@ class Options:
     max_refine: int = 10
     inner_tol: float = 1e-5
     tile_targets: int = 0
+    residual: int = DF64
 
     def _c(self) -> _Options:
         return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
-                        self.max_refine, self.inner_tol, self.tile_targets)
+                        self.max_refine, self.inner_tol, self.tile_targets, self.residual)
 
 
 @dataclasses.dataclass

@@ -66,6 +66,7 @@ void ctr_default_options(ctr_options* o) {
     o->max_refine = 10;
     o->inner_tol = 1e-5;
     o->tile_targets = 0;
+    o->residual = CTR_DF64;
 }
 
 const char* ctr_status_string(int st) {
@@ -120,8 +121,10 @@ int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_devic
             if (o.max_iter <= 0) o.max_iter = 400;
             if (o.max_refine <= 0) o.max_refine = 10;
             if (!(o.inner_tol > 0)) o.inner_tol = 1e-5;
-            if (o.precision != CTR_FP64 && o.precision != CTR_FP32_REFINE)
+            if (o.precision != CTR_FP64 && o.precision != CTR_FP32_REFINE && o.precision != CTR_DF64)
                 return fail(CTR_ERR_INVALID, "unknown precision");
+            if (o.residual != CTR_FP64 && o.residual != CTR_DF64)
+                return fail(CTR_ERR_INVALID, "residual must be CTR_FP64 or CTR_DF64");
         }
         if (o.restart > 1000) return fail(CTR_ERR_INVALID, "restart must be <= 1000");
         ctr_ibim* s = new ctr_ibim();
@@ -270,7 +273,8 @@ int ctr_ibim_area(const ctr_ibim* s, double* area) {
 
 int ctr_ibim_matvec(ctr_ibim* s, const double* x, double* y, int precision, int on_device) {
     if (!s || !x || !y) return fail(CTR_ERR_INVALID, "NULL argument");
-    if (precision != CTR_FP64 && precision != CTR_FP32_REFINE) return fail(CTR_ERR_INVALID, "unknown precision");
+    if (precision != CTR_FP64 && precision != CTR_FP32_REFINE && precision != CTR_DF64)
+        return fail(CTR_ERR_INVALID, "unknown precision");
     return guarded([&]() -> int {
         CTR_TRY(use_device(s));
         const int64_t n = 2 * s->M;

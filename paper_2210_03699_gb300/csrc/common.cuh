@@ -129,6 +129,7 @@ struct ctr_ibim {
     ctr::NodeArrays na{};
     ctr::DevBuf src32;       // float4 [2M]: {P, a} {n, b}
     ctr::DevBuf src64;       // double4 [2M]
+    ctr::DevBuf srcdf;       // float4 [4M]: float-float {P.hi, a.hi} {P.lo, a.lo} {n.hi, b.hi} {n.lo, b.lo}
     ctr::DevBuf corr_ptr;    // int32 [M+1]
     ctr::DevBuf corr_node;   // int32 [E]
     ctr::DevBuf corr_w;      // double [3][E]: omega11, omega21, omega22
@@ -139,7 +140,7 @@ struct ctr_ibim {
     ctr::DevBuf err;         // int device error word
     ctr::DevBuf vecs;        // double [6][2M] solver vectors
     ctr::DevBuf red;         // reduction scratch
-    ctr::PairPlan plan32, plan64;
+    ctr::PairPlan plan32, plan64, plandf;
     ctr::Krylov kr;
 };
 

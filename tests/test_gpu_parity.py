@@ -4,7 +4,8 @@ Tolerances (arithmetic behind them in the design notes):
   * integer / decision outputs (tube nodes, correction CSR, node ids): exact;
   * P and n: exact (both sides evaluate the same unfused IEEE sequence);
   * W, correction weights, rhs: 1e-12 relative to the largest magnitude;
-  * FP64 operator: 1e-12 relative (max norm), FP64 solve: 1e-10 relative;
+  * FP64 and float-float (DF64) operators: 1e-12 relative (max norm);
+  * FP64 solve: 1e-10 relative;
   * FP32-pair operator: 2e-5 relative (FP32 pair terms, FP64 accumulation per tile);
   * FP32 + FP64-refinement solve: 1e-6 relative in psi, dpsi and G_pol.
 """
@@ -83,6 +84,8 @@ def test_operator_parity(which, request, ctr):
     ref = S.matvec(p)
     y64 = G.matvec(p, ctr.FP64)
     assert _rel(y64, ref) < 1e-12
+    ydf = G.matvec(p, ctr.DF64)
+    assert _rel(ydf, ref) < 1e-12
     y32 = G.matvec(p, ctr.FP32_REFINE)
     assert _rel(y32, ref) < 2e-5
     # deterministic: fixed-order reductions
@@ -122,20 +125,28 @@ def test_solve_fp32_refine_parity(ellipsoid, ctr):
     prob, S, G = ellipsoid
     psi_o, dpsi_o, info_o = S.solve(tol=1e-13)
     Go, _ = oenergy.polarization_energy(S, psi_o, dpsi_o)
-    G32 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube,
-                                                               precision=ctr.FP32_REFINE, tol=1e-11))
-    psi, dpsi, info = G32.solve()
-    assert info.converged and info.refinements >= 1 and info.matvecs_fp32 > info.matvecs_fp64
-    assert _rel(psi, psi_o) < 1e-6
-    assert _rel(dpsi, dpsi_o) < 1e-6
-    Gp, _ = G32.energy(psi, dpsi)
-    assert abs(Gp / Go - 1) < 1e-6
+    for residual in (ctr.DF64, ctr.FP64):
+        G32 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, residual=residual,
+                                                                   precision=ctr.FP32_REFINE, tol=1e-11))
+        psi, dpsi, info = G32.solve()
+        assert info.converged and info.refinements >= 1 and info.matvecs_fp32 > info.matvecs_fp64
+        assert _rel(psi, psi_o) < 1e-6
+        assert _rel(dpsi, dpsi_o) < 1e-6
+        Gp, _ = G32.energy(psi, dpsi)
+        assert abs(Gp / Go - 1) < 1e-6
+        G32.close()
     # FP64 GPU path on the same system
     G64 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, tol=1e-13))
     psi64, dpsi64, _ = G64.solve()
     assert _rel(psi64, psi_o) < 1e-10
-    G32.close()
     G64.close()
+    # float-float operator as a plain solve mode
+    Gdf = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, tol=1e-13,
+                                                               precision=ctr.DF64))
+    psid, dpsid, info = Gdf.solve()
+    assert info.converged
+    assert _rel(psid, psi_o) < 1e-10 and _rel(dpsid, dpsi_o) < 1e-10
+    Gdf.close()
 
 
 def test_solve_on_device_buffers(sphere, ctr):
@@ -168,6 +179,7 @@ def test_small_system_and_laplace(ctr, oracle_tables):
     assert G.M == S.M and G.M < 512
     p = syn.random_density(S.M, seed=5)
     assert _rel(G.matvec(p, ctr.FP64), S.matvec(p)) < 1e-12
+    assert _rel(G.matvec(p, ctr.DF64), S.matvec(p)) < 1e-12
     assert _rel(G.matvec(p, ctr.FP32_REFINE), S.matvec(p)) < 2e-5
     G.close()
 
@@ -209,9 +221,11 @@ def test_full_size_sampled_rows(ctr, oracle_tables, tile_targets):
     p = syn.random_density(S.M, seed=13, smooth_points=S.geo.P)
     ref = S.matvec(p, rows=rows)
     y64 = G.matvec(p, ctr.FP64)
+    ydf = G.matvec(p, ctr.DF64)
     y32 = G.matvec(p, ctr.FP32_REFINE)
     sel = np.concatenate([rows, G.M + rows])
     assert _rel(y64[sel], ref) < 1e-12
+    assert _rel(ydf[sel], ref) < 1e-12
     assert _rel(y32[sel], ref) < 2e-5
     assert np.all(np.isfinite(y32)) and np.all(np.isfinite(y64))
     G.close()
