@@ -156,7 +156,7 @@ __device__ __forceinline__ F2 exp_neg_ff(F2 x, const float2* tab) {
         xl = 0.f;
     }
     const float t = __fmaf_rn(xh, 1024.f, 12582912.f);   // 1.5 * 2^23: round(x * 1024) in the mantissa
-    const int k = __float_as_int(t) - 0x4B400000;
+    const int k = min(max(__float_as_int(t) - 0x4B400000, 0), kExpHi * kExpLo - 1);   // in range for any input
     const float kf = __fsub_rn(t, 12582912.f);
     const F2 f = two_sum(__fmaf_rn(kf, -1.0f / 1024.f, xh), xl);   // the first term is exact
     const float fh = f.hi;
