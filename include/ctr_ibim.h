@@ -201,6 +201,40 @@ int ctr_ibim_reaction_potential(ctr_ibim* sys, const double* psi, const double* 
  */
 int ctr_weight_tables(double* out);
 
+/*
+ * Allocation-free variant of the FP32 dense pair sum (the paper has no
+ * counterpart: it is an interface for callers, not a step of the method).
+ * For callers that cannot call cudaMalloc -- code running while a CUDA graph
+ * is being captured, or under an allocator that owns all device memory, or a
+ * real-time loop that must not allocate -- this entry point takes every
+ * input and output from the caller and keeps its scratch (the per-split
+ * partial sums) in a fixed device array of 2 * CTR_STATIC_SCRATCH_NODES
+ * doubles (16 MiB), which each GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   M          nodes, 1 <= M <= CTR_STATIC_SCRATCH_NODES (else CTR_ERR_CAPACITY).
+ *   src        device, 16-byte aligned, 8 M floats: node j is
+ *              {Px, Py, Pz, a, nx, ny, nz, b} with a = h^3 W_j rho1_j / (4 pi),
+ *              b = h^3 W_j rho2_j / (4 pi).
+ *   row_ptr    device, M + 1 int32; excluded: device int32, for row i the
+ *              ascending node ids row_ptr[i] .. row_ptr[i+1]-1 omitted from
+ *              its sum (the correction nodes N(i)).
+ *   eps_ratio  eps_out / eps_in;  kappa  screening parameter (>= 0).
+ *   out        device, 2 M doubles: out[i] = sum_{j not excluded} (a_j 4pi K11 -
+ *              b_j 4pi K12), out[M + i] = sum (a_j 4pi K21 - b_j 4pi K22), the
+ *              same numbers ctr_ibim_matvec adds before the correction and
+ *              the diagonal (FP32 pair terms, FP64 tile sums).
+ *   stream     cudaStream_t (NULL: legacy default stream); the call returns
+ *              after the stream has finished its work.
+ * The first call on a device looks up that device's array address
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call shares the array, which keeps the
+ * last call's contents; calls that overlap on the GPU race on it.
+ */
+#define CTR_STATIC_SCRATCH_NODES 1048576
+int ctr_pair_sum_fp32_static(int64_t M, const float* src, const int32_t* row_ptr, const int32_t* excluded,
+                             double eps_ratio, double kappa, double* out, void* stream);
+
 /* Status code -> short description (static string). */
 const char* ctr_status_string(int status);
 

@@ -628,3 +628,42 @@ int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision) {
 }
 
 }  // namespace ctr
+
+namespace ctr {
+
+// FP32 pair sum of caller-provided packed sources into caller-provided split
+// scratch (partial, at most max_partial doubles); used by the entry point
+// whose scratch is a fixed device array.  Returns the number of splits used.
+int launch_fp32_pairs_external(const float4* src, int64_t M, const int32_t* eptr, const int32_t* excl,
+                               double eps_ratio, double kappa, int64_t max_partial, double* partial, int* err,
+                               cudaStream_t st, int* splits_out) {
+    int dev = 0, sms = 0;
+    CTR_CUDA_TRY(cudaGetDevice(&dev));
+    CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PairPlan p = make_plan(M, 2, Fp32Policy::kTile, sms);
+    const int64_t cap = max_partial / (2 * M);
+    if (cap < 1) return fail(CTR_ERR_CAPACITY, "scratch too small for this many nodes");
+    if (p.splits > cap) {
+        int64_t per = (M + cap - 1) / cap;
+        per = ((per + Fp32Policy::kTile - 1) / Fp32Policy::kTile) * Fp32Policy::kTile;
+        p.src_per_split = (int)per;
+        p.splits = (int)((M + per - 1) / per);
+    }
+    PairConsts kc{};
+    kc.c1 = eps_ratio;
+    kc.c2 = 1.0 / eps_ratio;
+    kc.kappa = kappa;
+    kc.c1f = (float)kc.c1;
+    kc.c2f = (float)kc.c2;
+    kc.kappaf = (float)kappa;
+    kc.kl2f = (float)(-kappa * 1.4426950408889634);
+    const size_t smem = 2 * Fp32Policy::kTile * Fp32Policy::kVec * sizeof(float4);
+    dim3 grid(p.target_blocks, p.splits);
+    pair_kernel<Fp32Policy, 2><<<grid, kThreads, smem, st>>>(src, (int)M, eptr, excl, p.src_per_split, partial, kc,
+                                                             err);
+    CTR_CUDA_TRY(cudaGetLastError());
+    *splits_out = p.splits;
+    return CTR_OK;
+}
+
+}  // namespace ctr
