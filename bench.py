@@ -147,37 +147,47 @@ def workload(h):
                               f"kappa=0.1257", "grid": list(prob.grid.n), "solver": None}
 
 
+class OracleSample:
+    """The oracle's FP64 punctured dense sum (Eqs. 2.14-2.15) on sampled target rows, host cores."""
+
+    def __init__(self, prob, seconds, threads=None):
+        from oracle import geometry, native
+        import synthetic as syn
+        if threads:
+            native.set_threads(threads)
+        self.cores = native.max_threads()
+        self.prob = prob
+        geo = geometry.tube_geometry(prob.grid.n, prob.grid.origin, prob.grid.h, prob.sdist, prob.tube)
+        self.M = geo.M
+        self.rng = np.random.Generator(np.random.PCG64(1))
+        self.p = syn.random_density(self.M, seed=2)
+        # calibrate the row count to about `seconds` of CPU time
+        rows = np.sort(self.rng.choice(self.M, size=min(self.M, 32 * self.cores), replace=False))
+        S = self._system(rows)
+        t0 = time.perf_counter()
+        S.punctured_sum(self.p, rows)
+        rate = rows.size * self.M / max(time.perf_counter() - t0, 1e-6)
+        n_rows = int(min(self.M, max(self.cores, rate * seconds / self.M)))
+        self.rows = np.sort(self.rng.choice(self.M, size=n_rows, replace=False))
+        self.S = self._system(self.rows)
+
+    def _system(self, rows):
+        from oracle.system import OracleSystem
+        return OracleSystem.from_problem(self.prob, rows=rows,
+                                         table_cache=os.path.join(ROOT, "oracle", "_build", "cache"))
+
+    def run(self):
+        t0 = time.perf_counter()
+        self.S.punctured_sum(self.p, self.rows)
+        dt = time.perf_counter() - t0
+        pairs = self.rows.size * self.M
+        return {"value": pairs / dt, "unit": "pair-interactions/s", "cores": self.cores, "kind": "oracle",
+                "sample": f"FP64 punctured dense sum of {self.rows.size} sampled target rows x {self.M} sources "
+                          f"({pairs:.3g} pairs, {dt:.1f} s) of the same workload"}
+
+
 def cpu_baseline(prob, seconds, threads=None):
-    """The oracle's FP64 punctured dense sum on a bounded sample of target rows (host cores)."""
-    from oracle import native
-    from oracle.system import OracleSystem
-    import synthetic as syn
-    if threads:
-        native.set_threads(threads)
-    cores = native.max_threads()
-    M_probe = None
-    # probe rows to size the sample to ~`seconds` of CPU time
-    rng = np.random.Generator(np.random.PCG64(1))
-    from oracle import geometry
-    geo = geometry.tube_geometry(prob.grid.n, prob.grid.origin, prob.grid.h, prob.sdist, prob.tube)
-    M_probe = geo.M
-    rows = np.sort(rng.choice(M_probe, size=min(M_probe, 4 * cores), replace=False))
-    S = OracleSystem.from_problem(prob, rows=rows, tables=None,
-                                  table_cache=os.path.join(ROOT, "oracle", "_build", "cache"))
-    p = syn.random_density(S.M, seed=2)
-    t0 = time.perf_counter()
-    S.punctured_sum(p, rows)
-    dt = time.perf_counter() - t0
-    rate = rows.size * S.M / dt
-    n_rows = int(min(S.M, max(cores, rate * seconds / S.M)))
-    rows2 = np.sort(rng.choice(S.M, size=n_rows, replace=False))
-    S2 = OracleSystem.from_problem(prob, rows=rows2, tables=S.T)
-    t0 = time.perf_counter()
-    S2.punctured_sum(p, rows2)
-    dt2 = time.perf_counter() - t0
-    return {"value": rows2.size * S2.M / dt2, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 punctured dense sum of {rows2.size} sampled target rows x {S2.M} sources "
-                      f"({rows2.size * S2.M:.3g} pairs, {dt2:.1f} s) of the same workload"}
+    return OracleSample(prob, seconds, threads).run()
 
 
 def run_reference(args, world, rank):
@@ -185,11 +195,11 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     prob, cfg = workload(args.h)
-    t_all = []
-    res = None
+    sample = OracleSample(prob, seconds=max(2.0, min(args.cpu_seconds, 20.0)))
     steps = []
+    res = None
     for it in range(args.warmup + args.steps):
-        res = cpu_baseline(prob, seconds=max(2.0, min(args.cpu_seconds, 20.0)))
+        res = sample.run()
         if it >= args.warmup:
             steps.append(res["value"])
     value = statistics.median(steps)
@@ -236,6 +246,7 @@ def main():
     ev = []
     pairs = 0.0
     infos = []
+    launches0 = ctr.kernel_launches()
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
         for _ in range(args.steps):
@@ -250,6 +261,7 @@ def main():
             pairs += float(M) ** 2 * (info.matvecs_fp32 + info.matvecs_fp64)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
+    launches = ctr.kernel_launches() - launches0
     barrier(world)
     t_dev = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
     t_max = max_over_ranks(t_dev, world)
@@ -324,7 +336,7 @@ def main():
                          "t_matvec_fp32_ms": t_mv32 * 1e3, "t_matvec_fp64_ms": t_mv64 * 1e3},
             "clocks": clk.summary(),
             "e2e": e2e,
-            "gpu_launches": None,
+            "gpu_launches": int(launches),
             "wall_s": t_wall,
             "cpu_baseline": cpu,
         }

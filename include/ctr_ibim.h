@@ -62,6 +62,18 @@ extern "C" {
  */
 enum { CTR_FP64 = 0, CTR_FP32_REFINE = 1, CTR_DF64 = 2 };
 
+/*
+ * Quadrature of the rows (Secs. 2.3, 2.4, 3.2):
+ *   CTR_METHOD_HYB   HYB-IBIM: CTR2 corrections (Sec. 2.4) at "good" nodes;
+ *                    K-reg rows and J = 1 (Eq. 3.2) at "bad" nodes, a node being
+ *                    bad when a finite-difference curvature is non-finite or
+ *                    |k_i| (eps + h) >= 0.8 (the tube would reach within 20% of
+ *                    the focal distance).  On smooth surfaces resolved by the
+ *                    grid no node is bad and this is plain CTR2.
+ *   CTR_METHOD_KREG  K-reg everywhere (Sec. 2.3), J = 1 everywhere.
+ */
+enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
+
 typedef struct {
     int64_t n[3];       /* nodes per axis (nx, ny, nz), each >= 5 */
     double origin[3];   /* coordinates of node (0, 0, 0) */
@@ -79,6 +91,7 @@ typedef struct {
     int tile_targets;      /* pair-kernel targets per thread (1, 2 or 4); <= 0: automatic */
     int residual;          /* pair arithmetic of the refinement residual r = g - A x:
                               CTR_DF64 (the default of ctr_default_options) or CTR_FP64 */
+    int method;            /* CTR_METHOD_HYB (default) or CTR_METHOD_KREG */
 } ctr_options;
 
 typedef struct {
@@ -140,12 +153,19 @@ int ctr_ibim_num_corrections(const ctr_ibim* sys, int64_t* E);
 
 /*
  * Correction matrix Omega of Eq. (2.30) in CSR form by target, host memory:
- * ptr (M+1 int64), node (E int64, ascending plane order per target),
- * omega11, omega21, omega22 (E doubles each; omega12 is kappa/(4 pi) for
- * every entry, Theorem of Sec. 2.4.1).  Any output may be NULL.
+ * ptr (M+1 int64), node (E int64), omega11, omega12, omega21, omega22 (E
+ * doubles each).  Row i adds sum_e W_m (h^2 omega11 rho1_m - h^3 omega12 rho2_m)
+ * and sum_e W_m (h^2 omega21 rho1_m - h^2 omega22 rho2_m).  CTR2 rows: one
+ * entry per corrected plane in ascending plane order, omega12 = kappa/(4 pi)
+ * (Theorem of Sec. 2.4.1).  K-reg rows (bad targets): the nodes of the
+ * tangent-plane cylinder of radius 2h in ascending node order, omega11 =
+ * omega21 = omega22 = 0, omega12 = C12 of Sec. 2.3.  Any output may be NULL.
  */
-int ctr_ibim_corrections(const ctr_ibim* sys, int64_t* ptr, int64_t* node,
-                         double* omega11, double* omega21, double* omega22);
+int ctr_ibim_corrections(const ctr_ibim* sys, int64_t* ptr, int64_t* node, double* omega11,
+                         double* omega12, double* omega21, double* omega22);
+
+/* Hybrid classification (Sec. 3.2): flags[i] = 1 when node i is bad; M bytes, host. */
+int ctr_ibim_bad_nodes(const ctr_ibim* sys, uint8_t* flags);
 
 /* Right-hand side g = [g1; g2] of Eq. (2.12) at the nodes' P: 2M doubles. */
 int ctr_ibim_rhs(const ctr_ibim* sys, double* g, int on_device);
@@ -240,6 +260,9 @@ const char* ctr_status_string(int status);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* ctr_last_error(void);
+
+/* Kernels this library has launched in this process so far (all devices and handles). */
+int64_t ctr_kernel_launches(void);
 
 #ifdef __cplusplus
 }

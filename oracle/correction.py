@@ -24,8 +24,19 @@ For the target node y_i with surface point x* = P_i and unit normal n:
     Fourier coefficients of l from an FFT of 4N equispaced samples, and the
     tabulated T interpolated on the (alpha_m, beta_n) stencil (Sec. 2.4.2).
 
+K-reg rows (Sec. 2.3) for the targets the hybrid classification marks bad
+(Sec. 3.2, HYB-IBIM): the kernel is replaced by the constant C in the
+tangent-plane disc |x - y|_P < tau, tau = 2h, where |x - y|_P is the distance
+between the projections of the grid node y and of x onto the tangent plane at
+P(x): the correction set is every tube node in that cylinder, with
+C11 = C21 = C22 = 0 and C12 = (e^{-kappa tau} - 1 + kappa tau) / (2 pi kappa tau^2)
+(kappa -> 0: kappa/(4 pi)).  Membership: v = y - P, s = (v0 n0 + v1 n1) + v2 n2,
+t_c = v_c - s n_c, (t0 t0 + t1 t1) + t2 t2 < tau^2, unfused FP64.  Entries in
+ascending node order.
+
 Parity status: pinned through the operator identities on the sphere
-(double layer, consistency with the exact solution) and the plane rule.
+(double layer, consistency with the exact solution), the plane rule, and the
+K-reg constant against a disc-average quadrature.
 """
 from __future__ import annotations
 
@@ -48,8 +59,9 @@ class Correction:
     beta: np.ndarray       # (E,)
     eta: np.ndarray        # (E,)
     axis: np.ndarray       # (M,) dominant axis per target
-    omega_A: np.ndarray    # (E,) omega[v^T M v / (8 pi |v|^3)]
-    omega_B: np.ndarray    # (E,) omega[1 / (8 pi |v|)]
+    omega_A: np.ndarray    # (E,) omega[v^T M v / (8 pi |v|^3)]  (0 in K-reg rows)
+    omega_B: np.ndarray    # (E,) omega[1 / (8 pi |v|)]          (0 in K-reg rows)
+    kreg: np.ndarray       # (E,) bool: entry of a K-reg row
 
     def excl_csr(self):
         """Sorted correction node ids per target (the pairs the dense sum omits)."""
@@ -65,10 +77,44 @@ def dominant_axis(n: np.ndarray) -> np.ndarray:
     return np.argmax(np.abs(n), axis=1)
 
 
+def kreg_constant(kappa: float, tau: float) -> float:
+    """C12 of Sec. 2.3: the tangent-disc average of (G0 - Gk)."""
+    if kappa == 0.0:
+        return 0.0
+    return (math.exp(-kappa * tau) - 1.0 + kappa * tau) / (2.0 * math.pi * kappa * tau * tau)
+
+
+def kreg_nodes(geo: TubeGeometry, i: int, tau: float):
+    """Tube nodes in the tangent-plane cylinder of radius tau around target i (ascending ids)."""
+    h = geo.h
+    nx, ny, nz = geo.grid_n
+    K = int(math.ceil((geo.eps + tau) / h)) + 1
+    r = np.arange(-K, K + 1)
+    dk, dj, di = np.meshgrid(r, r, r, indexing="ij")          # k slowest: ascending grid index
+    q = geo.ijk[i, 0] + di.ravel()
+    j = geo.ijk[i, 1] + dj.ravel()
+    k = geo.ijk[i, 2] + dk.ravel()
+    ok = (q >= 0) & (q < nx) & (j >= 0) & (j < ny) & (k >= 0) & (k < nz)
+    m = geo.node_of[(q + nx * (j + ny * k))[ok]]
+    m = m[m >= 0]
+    P = geo.P[i]
+    n = geo.n[i]
+    v0 = geo.y[m, 0] - P[0]
+    v1 = geo.y[m, 1] - P[1]
+    v2 = geo.y[m, 2] - P[2]
+    s = (v0 * n[0] + v1 * n[1]) + v2 * n[2]
+    t0 = v0 - s * n[0]
+    t1 = v1 - s * n[1]
+    t2 = v2 - s * n[2]
+    inside = (t0 * t0 + t1 * t1) + t2 * t2 < tau * tau
+    return [int(v) for v in m[inside]]
+
+
 def correction_nodes(geo: TubeGeometry, targets=None):
-    """(target, node, alpha, beta, eta) entries, targets ascending, planes ascending.
+    """(target, node, alpha, beta, eta, kreg) entries, targets ascending, planes ascending.
 
     `targets`: optional subset of target rows (default: all tube nodes).
+    Bad targets get their K-reg cylinder instead (alpha = beta = eta = 0, kreg = 1).
     """
     h, eps = geo.h, geo.eps
     nx, ny, nz = geo.grid_n
@@ -77,7 +123,12 @@ def correction_nodes(geo: TubeGeometry, targets=None):
     K = int(math.ceil(2.0 * eps / h)) + 2
     ax = dominant_axis(geo.n)
     rows = []
+    tau = 2.0 * h
     for i in (range(geo.M) if targets is None else sorted(int(t) for t in targets)):
+        if geo.bad[i]:
+            for m in kreg_nodes(geo, i, tau):
+                rows.append((i, m, 0.0, 0.0, 0.0, 1.0))
+            continue
         a = int(ax[i])
         b, c = [v for v in range(3) if v != a]
         Pa, Pb, Pc = geo.P[i, a], geo.P[i, b], geo.P[i, c]
@@ -103,8 +154,8 @@ def correction_nodes(geo: TubeGeometry, targets=None):
             m = int(geo.node_of[idx[0] + nx * (idx[1] + ny * idx[2])])
             if m < 0:
                 continue
-            rows.append((i, m, alpha, beta, eta))
-    arr = np.array(rows, dtype=np.float64) if rows else np.zeros((0, 5))
+            rows.append((i, m, alpha, beta, eta, 0.0))
+    arr = np.array(rows, dtype=np.float64) if rows else np.zeros((0, 6))
     return arr, ax
 
 
@@ -182,14 +233,19 @@ def build_correction(geo: TubeGeometry, T: np.ndarray, targets=None) -> Correcti
     tgt = arr[:, 0].astype(np.int64)
     node = arr[:, 1].astype(np.int64)
     alpha, beta, eta = arr[:, 2], arr[:, 3], arr[:, 4]
-    lA, lB = angular_functions(geo, tgt, ax, eta)
-    aA, bA = fourier_coefficients(lA)
-    aB, bB = fourier_coefficients(lB)
-    Tint = interpolated_tables(T, alpha, beta)
-    omA = weights_from_coefficients(aA, bA, Tint)
-    omB = weights_from_coefficients(aB, bB, Tint)
+    kreg = arr[:, 5] != 0.0
+    omA = np.zeros(tgt.size)
+    omB = np.zeros(tgt.size)
+    c = ~kreg
+    if np.any(c):
+        lA, lB = angular_functions(geo, tgt[c], ax, eta[c])
+        aA, bA = fourier_coefficients(lA)
+        aB, bB = fourier_coefficients(lB)
+        Tint = interpolated_tables(T, alpha[c], beta[c])
+        omA[c] = weights_from_coefficients(aA, bA, Tint)
+        omB[c] = weights_from_coefficients(aB, bB, Tint)
     ptr = np.zeros(geo.M + 1, dtype=np.int64)
     np.add.at(ptr, tgt + 1, 1)
     ptr = np.cumsum(ptr)
     return Correction(ptr=ptr, node=node, alpha=alpha, beta=beta, eta=eta, axis=ax,
-                      omega_A=omA, omega_B=omB)
+                      omega_A=omA, omega_B=omB, kreg=kreg)

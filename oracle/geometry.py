@@ -17,6 +17,15 @@ Follows Sec. 2.1 and the finite-difference remark of Sec. 3.3.1:
   * W = J * delta_eps(d), delta_eps(eta) = phi(eta/eps)/eps with
     phi(x) = (1 + cos(pi x))/2 on |x| <= 1 (Sec. 2.6).
 
+Hybrid classification (Sec. 3.2, HYB-IBIM): a node is "bad" when its
+finite-difference geometry cannot be trusted -- reading of the paper's "stencil
+negatively impacted by the curvature discontinuity": a non-finite value, or a
+surface principal curvature with |k_i| (eps + h) >= 0.8, i.e. the tube (and
+every correction plane, |eta| <= eps + h) would reach within 20% of the focal
+distance 1/|k_i|.  Bad nodes take J = 1 (Eq. (3.2)); their rows use K-reg
+(module correction).  Method "kreg" marks every node bad (the K-reg method of
+Sec. 2.3 with J = 1, as in the paper's comparison).
+
 Arithmetic order matters where a floating-point value decides an integer
 (tube membership, the correction planes and nodes): y = origin + h*i,
 g_c = (d[+] - d[-]) / (2h), |g| = sqrt((g0*g0 + g1*g1) + g2*g2), n_c = g_c/|g|,
@@ -47,6 +56,7 @@ class TubeGeometry:
     kprime: np.ndarray     # (M, 2) level-set principal curvatures
     tau: np.ndarray        # (M, 2, 3) principal directions
     kappa_s: np.ndarray    # (M, 2) surface principal curvatures (convex > 0)
+    bad: np.ndarray        # (M,) bool: hybrid classification (Sec. 3.2)
     J: np.ndarray          # (M,)
     W: np.ndarray          # (M,) J * delta_eps(d)
     node_of: np.ndarray    # grid-sized int64 map: linear index -> node id or -1
@@ -67,7 +77,11 @@ def delta_eps(eta, eps):
     return phi(np.asarray(eta) / eps) / eps
 
 
-def tube_geometry(grid_n, origin, h, sdist, eps) -> TubeGeometry:
+BAD_CURVATURE = 0.8   # |k_i| (eps + h) at or above this marks a node bad
+
+
+def tube_geometry(grid_n, origin, h, sdist, eps, method: str = "hyb") -> TubeGeometry:
+    """method: "hyb" (CTR2 with the hybrid classification) or "kreg" (every node bad)."""
     nx, ny, nz = (int(v) for v in grid_n)
     D = np.asarray(sdist, dtype=np.float64).reshape(nz, ny, nx)
     flat = D.ravel()
@@ -124,12 +138,20 @@ def tube_geometry(grid_n, origin, h, sdist, eps) -> TubeGeometry:
     tau = np.einsum("mab,mai->mbi", V, E)                        # tau[:, b] = sum_a V[a, b] E[a]
     J = (1.0 - dd * kp[:, 0]) * (1.0 - dd * kp[:, 1])
     ks = kp / (1.0 - dd[:, None] * kp)
+    finite = np.isfinite(J) & np.all(np.isfinite(ks), axis=1) & np.all(np.isfinite(tau.reshape(lin.size, -1)), axis=1)
+    with np.errstate(invalid="ignore"):
+        bad = (~finite) | (np.max(np.abs(ks), axis=1) * (eps + h) >= BAD_CURVATURE)
+    if method == "kreg":
+        bad[:] = True
+    elif method != "hyb":
+        raise ValueError("method must be 'hyb' or 'kreg'")
+    J = np.where(bad, 1.0, J)                    # Eq. (3.2): J = 1 at bad nodes
     W = J * delta_eps(dd, eps)
     node_of = np.full(flat.size, -1, dtype=np.int64)
     node_of[lin] = np.arange(lin.size, dtype=np.int64)
     return TubeGeometry(h=float(h), eps=float(eps), grid_n=(nx, ny, nz), origin=tuple(float(v) for v in origin),
                         lin=lin, ijk=ijk, y=y, d=dd, grad_norm=gn, n=n, P=P, kprime=kp, tau=tau,
-                        kappa_s=ks, J=J, W=W, node_of=node_of)
+                        kappa_s=ks, bad=bad, J=J, W=W, node_of=node_of)
 
 
 def tube_area(geo: TubeGeometry) -> float:

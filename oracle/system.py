@@ -21,7 +21,7 @@ import numpy as np
 
 from . import native
 from . import tables as tb
-from .correction import Correction, build_correction
+from .correction import Correction, build_correction, kreg_constant
 from .geometry import TubeGeometry, tube_area, tube_geometry
 from .gmres import gmres
 
@@ -30,9 +30,10 @@ class OracleSystem:
     """Setup (tube, geometry, correction, rhs) and the operator of Eq. (2.30)."""
 
     def __init__(self, grid_n, origin, h, sdist, eps_in, eps_out, kappa, charge_xyz, charge_q, tube,
-                 tables=None, table_cache=None, rows=None):
+                 tables=None, table_cache=None, rows=None, method="hyb"):
         """rows: optional subset of target rows whose corrections are built (sampled checks);
-        matvec is then valid for those rows only."""
+        matvec is then valid for those rows only.  method: "hyb" (CTR2, K-reg at bad
+        nodes, Sec. 3.2) or "kreg" (K-reg everywhere, Sec. 2.3)."""
         self.h = float(h)
         self.eps_in, self.eps_out, self.kappa = float(eps_in), float(eps_out), float(kappa)
         self.ratio = self.eps_out / self.eps_in                         # eps_E / eps_I
@@ -40,14 +41,15 @@ class OracleSystem:
         self.lam2 = 0.5 * (1.0 + self.eps_in / self.eps_out)
         self.charge_xyz = np.ascontiguousarray(charge_xyz, dtype=np.float64).reshape(-1, 3)
         self.charge_q = np.ascontiguousarray(charge_q, dtype=np.float64).ravel()
-        self.geo: TubeGeometry = tube_geometry(grid_n, origin, h, sdist, tube)
+        self.geo: TubeGeometry = tube_geometry(grid_n, origin, h, sdist, tube, method=method)
         self.T = tables if tables is not None else tb.build_tables(table_cache)
         self.rows = None if rows is None else np.array(sorted(int(r) for r in rows), dtype=np.int64)
         self.corr: Correction = build_correction(self.geo, self.T, targets=self.rows)
         self.omega11 = (1.0 - self.eps_out / self.eps_in) * self.corr.omega_A
         self.omega22 = (1.0 - self.eps_in / self.eps_out) * self.corr.omega_A
         self.omega21 = self.kappa ** 2 * self.corr.omega_B
-        self.omega12 = self.kappa / (4.0 * math.pi)
+        self.omega12 = np.where(self.corr.kreg, kreg_constant(self.kappa, 2.0 * self.h),
+                                self.kappa / (4.0 * math.pi))
         self.excl_ptr, self.excl_idx = self.corr.excl_csr()
         self._P = np.ascontiguousarray(self.geo.P)
         self._N = np.ascontiguousarray(self.geo.n)
@@ -55,6 +57,7 @@ class OracleSystem:
 
     @classmethod
     def from_problem(cls, prob, **kw):
+        """System for a synthetic.Problem; keyword arguments go to the constructor."""
         g = prob.grid
         return cls(g.n, g.origin, g.h, prob.sdist, prob.eps_in, prob.eps_out, prob.kappa,
                    prob.charge_xyz, prob.charge_q, prob.tube, **kw)
@@ -106,7 +109,7 @@ class OracleSystem:
             s, e = c.ptr[i], c.ptr[i + 1]
             m = c.node[s:e]
             Wm = self.geo.W[m]
-            o1[t] = np.sum(Wm * (h2 * self.omega11[s:e] * rho1[m] - h3 * self.omega12 * rho2[m]))
+            o1[t] = np.sum(Wm * (h2 * self.omega11[s:e] * rho1[m] - h3 * self.omega12[s:e] * rho2[m]))
             o2[t] = np.sum(Wm * (h2 * self.omega21[s:e] * rho1[m] - h2 * self.omega22[s:e] * rho2[m]))
         return o1, o2
 

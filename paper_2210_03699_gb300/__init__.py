@@ -18,12 +18,14 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "library_path", "lib",
-           "FP64", "FP32_REFINE", "DF64"]
+__all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "kernel_launches", "library_path", "lib",
+           "FP64", "FP32_REFINE", "DF64", "METHOD_HYB", "METHOD_KREG"]
 
 FP64 = 0
 FP32_REFINE = 1
 DF64 = 2
+METHOD_HYB = 0
+METHOD_KREG = 1
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -42,7 +44,8 @@ class _Grid(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("tube_halfwidth", ctypes.c_double), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -62,10 +65,11 @@ class Options:
     inner_tol: float = 1e-5
     tile_targets: int = 0
     residual: int = DF64
+    method: int = METHOD_HYB
 
     def _c(self) -> _Options:
         return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
-                        self.max_refine, self.inner_tol, self.tile_targets, self.residual)
+                        self.max_refine, self.inner_tol, self.tile_targets, self.residual, self.method)
 
 
 @dataclasses.dataclass
@@ -99,7 +103,8 @@ def _load():
         "ctr_ibim_nodes": (ctypes.c_int, [P, P]),
         "ctr_ibim_geometry": (ctypes.c_int, [P, P, P, P]),
         "ctr_ibim_num_corrections": (ctypes.c_int, [P, _I64]),
-        "ctr_ibim_corrections": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ctr_ibim_corrections": (ctypes.c_int, [P, P, P, P, P, P, P]),
+        "ctr_ibim_bad_nodes": (ctypes.c_int, [P, P]),
         "ctr_ibim_rhs": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ctr_ibim_area": (ctypes.c_int, [P, _D]),
         "ctr_ibim_matvec": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int]),
@@ -109,6 +114,7 @@ def _load():
         "ctr_weight_tables": (ctypes.c_int, [P]),
         "ctr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "ctr_last_error": (ctypes.c_char_p, []),
+        "ctr_kernel_launches": (ctypes.c_int64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -189,6 +195,7 @@ class CtrIbim:
 
     @classmethod
     def from_problem(cls, prob, options: Options | None = None, stream=None, sdist=None):
+        """System for a synthetic.Problem (its tube half-width unless options say otherwise)."""
         g = prob.grid
         return cls(g.n, g.origin, g.h, prob.sdist if sdist is None else sdist, prob.eps_in, prob.eps_out,
                    prob.kappa, prob.charge_xyz, prob.charge_q,
@@ -226,13 +233,18 @@ class CtrIbim:
         return P, n, W
 
     def corrections(self):
+        """(ptr, node, w) with w rows omega11, omega21, omega22, omega12."""
         ptr = np.empty(self.M + 1, dtype=np.int64)
         node = np.empty(self.E, dtype=np.int64)
-        w = np.empty((3, self.E))
-        _check(lib.ctr_ibim_corrections(self._h, ptr.ctypes.data_as(ctypes.c_void_p),
-                                        node.ctypes.data_as(ctypes.c_void_p), w[0].ctypes.data_as(ctypes.c_void_p),
-                                        w[1].ctypes.data_as(ctypes.c_void_p), w[2].ctypes.data_as(ctypes.c_void_p)))
+        w = np.empty((4, self.E))
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _check(lib.ctr_ibim_corrections(self._h, vp(ptr), vp(node), vp(w[0]), vp(w[3]), vp(w[1]), vp(w[2])))
         return ptr, node, w
+
+    def bad_nodes(self) -> np.ndarray:
+        f = np.empty(self.M, dtype=np.uint8)
+        _check(lib.ctr_ibim_bad_nodes(self._h, f.ctypes.data_as(ctypes.c_void_p)))
+        return f.astype(bool)
 
     def rhs(self) -> np.ndarray:
         g = np.empty(2 * self.M)
@@ -298,6 +310,11 @@ class CtrIbim:
         _check(lib.ctr_ibim_reaction_potential(self._h, pp, dd, dev, z.shape[0], z.ctypes.data_as(ctypes.c_void_p),
                                                out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib.ctr_kernel_launches())
 
 
 def weight_tables() -> np.ndarray:

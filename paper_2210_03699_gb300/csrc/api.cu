@@ -1,5 +1,6 @@
 // C ABI entry points (declared in include/ctr_ibim.h): argument checks, handle
 // lifetime, host/device staging.  No exception crosses this boundary.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -16,6 +17,10 @@ int fail(int status, const std::string& msg) {
     set_last_error(msg);
     return status;
 }
+
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 }  // namespace ctr
 
@@ -67,6 +72,7 @@ void ctr_default_options(ctr_options* o) {
     o->inner_tol = 1e-5;
     o->tile_targets = 0;
     o->residual = CTR_DF64;
+    o->method = CTR_METHOD_HYB;
 }
 
 const char* ctr_status_string(int st) {
@@ -86,6 +92,8 @@ const char* ctr_status_string(int st) {
 }
 
 const char* ctr_last_error(void) { return t_last_error.c_str(); }
+
+int64_t ctr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void ctr_ibim_destroy(ctr_ibim* s) {
     if (!s) return;
@@ -125,6 +133,8 @@ int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_devic
                 return fail(CTR_ERR_INVALID, "unknown precision");
             if (o.residual != CTR_FP64 && o.residual != CTR_DF64)
                 return fail(CTR_ERR_INVALID, "residual must be CTR_FP64 or CTR_DF64");
+            if (o.method != CTR_METHOD_HYB && o.method != CTR_METHOD_KREG)
+                return fail(CTR_ERR_INVALID, "method must be CTR_METHOD_HYB or CTR_METHOD_KREG");
         }
         if (o.restart > 1000) return fail(CTR_ERR_INVALID, "restart must be <= 1000");
         ctr_ibim* s = new ctr_ibim();
@@ -228,24 +238,34 @@ int ctr_ibim_geometry(const ctr_ibim* s, double* P, double* normal, double* W) {
     });
 }
 
-int ctr_ibim_corrections(const ctr_ibim* s, int64_t* ptr, int64_t* node, double* w11, double* w21, double* w22) {
+int ctr_ibim_corrections(const ctr_ibim* s, int64_t* ptr, int64_t* node, double* w11, double* w12, double* w21,
+                         double* w22) {
     if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
     return guarded([&]() -> int {
         CTR_TRY(use_device(s));
         const int64_t M = s->M, E = s->E;
         std::vector<int32_t> p(M + 1), nd(E);
-        std::vector<double> w(3 * (size_t)E);
+        std::vector<double> w(4 * (size_t)E);
         CTR_CUDA_TRY(cudaMemcpyAsync(p.data(), s->corr_ptr.p, sizeof(int32_t) * (M + 1), cudaMemcpyDeviceToHost, s->stream));
         CTR_CUDA_TRY(cudaMemcpyAsync(nd.data(), s->corr_node.p, sizeof(int32_t) * E, cudaMemcpyDeviceToHost, s->stream));
-        CTR_CUDA_TRY(cudaMemcpyAsync(w.data(), s->corr_w.p, sizeof(double) * 3 * E, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaMemcpyAsync(w.data(), s->corr_w.p, sizeof(double) * 4 * E, cudaMemcpyDeviceToHost, s->stream));
         CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
         if (ptr) for (int64_t i = 0; i <= M; ++i) ptr[i] = p[i];
         if (node) for (int64_t e = 0; e < E; ++e) node[e] = nd[e];
         if (w11) std::memcpy(w11, w.data(), sizeof(double) * E);
         if (w21) std::memcpy(w21, w.data() + E, sizeof(double) * E);
         if (w22) std::memcpy(w22, w.data() + 2 * E, sizeof(double) * E);
+        if (w12) std::memcpy(w12, w.data() + 3 * E, sizeof(double) * E);
         return CTR_OK;
     });
+}
+
+int ctr_ibim_bad_nodes(const ctr_ibim* s, uint8_t* flags) {
+    if (!s || !flags) return fail(CTR_ERR_INVALID, "NULL argument");
+    CTR_TRY(use_device(s));
+    CTR_CUDA_TRY(cudaMemcpyAsync(flags, s->bad.p, s->M, cudaMemcpyDeviceToHost, s->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return CTR_OK;
 }
 
 int ctr_ibim_rhs(const ctr_ibim* s, double* g, int on_device) {

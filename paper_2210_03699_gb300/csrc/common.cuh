@@ -45,6 +45,14 @@ int fail(int status, const std::string& msg);
         }                                                                                   \
     } while (0)
 
+// After every kernel launch: count it and surface launch errors.
+void count_launch();
+#define CTR_LAUNCHED()                      \
+    do {                                    \
+        ::ctr::count_launch();              \
+        CTR_CUDA_TRY(cudaGetLastError());   \
+    } while (0)
+
 #define CTR_TRY(expr)              \
     do {                           \
         int s_ = (expr);           \
@@ -132,7 +140,8 @@ struct ctr_ibim {
     ctr::DevBuf srcdf;       // float4 [4M]: float-float {P.hi, a.hi} {P.lo, a.lo} {n.hi, b.hi} {n.lo, b.lo}
     ctr::DevBuf corr_ptr;    // int32 [M+1]
     ctr::DevBuf corr_node;   // int32 [E]
-    ctr::DevBuf corr_w;      // double [3][E]: omega11, omega21, omega22
+    ctr::DevBuf corr_w;      // double [4][E]: omega11, omega21, omega22, omega12
+    ctr::DevBuf bad;         // uint8 [M] hybrid classification
     ctr::DevBuf excl;        // int32 [E] sorted correction nodes per target
     ctr::DevBuf rhs;         // double [2M]
     ctr::DevBuf charges;     // double [4][nc]: x, y, z, q

@@ -69,9 +69,9 @@ int reaction_potential(ctr_ibim* s, const double* d_psi, const double* d_dpsi, i
     rxn_partial_kernel<<<grid, kThreads, 0, s->stream>>>(s->na, s->M, d_psi, d_dpsi, d_xyz, npts,
                                                         s->h * s->h * s->h, s->kappa, s->eps_out / s->eps_in, chunk,
                                                         part.as<double>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     rxn_final_kernel<<<grid_for(npts, 128), 128, 0, s->stream>>>(part.as<double>(), nb, npts, d_out);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return CTR_OK;
 }

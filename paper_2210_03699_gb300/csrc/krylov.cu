@@ -196,9 +196,9 @@ int dots(ctr_ibim* s, const double* A, int64_t lda, int count, const double* w, 
     Krylov& k = s->kr;
     const int64_t chunk = (n + k.nblk - 1) / k.nblk;
     dots_partial_kernel<<<k.nblk, kRedThreads, 0, s->stream>>>(A, lda, count, w, n, chunk, k.part.as<double>(), k.nblk);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     dots_final_kernel<<<count, kRedThreads, 0, s->stream>>>(k.part.as<double>(), k.nblk, out, accumulate);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 
@@ -239,32 +239,32 @@ int gmres(ctr_ibim* s, int precision, const double* b, double* x, double tol_rel
     while (budget > 0) {
         // V[0] = start / beta
         axpby_kernel<<<gb, 256, 0, st>>>(1.0 / beta, start, 0.0, start, V, n);
-        CTR_CUDA_TRY(cudaGetLastError());
+        CTR_LAUNCHED();
         init_rhs_kernel<<<1, 1024, 0, st>>>(k.s.as<double>(), m, beta);
-        CTR_CUDA_TRY(cudaGetLastError());
+        CTR_LAUNCHED();
         int kdone = 0;
         double hsc[4] = {0, 0, 0, 0};
         for (int j = 0; j < m && budget > 0; ++j) {
             double* w = V + (size_t)(j + 1) * n;   // build the next vector in place
             diag_inv_kernel<<<gb, 256, 0, st>>>(V + (size_t)j * n, v.w, s->M, il1, il2);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             CTR_TRY(apply_operator(s, v.w, w, precision));
             if (precision == CTR_FP32_REFINE) info->matvecs_fp32++; else info->matvecs_fp64++;
             // CGS2
             CTR_TRY(dots(s, V, n, j + 1, w, n, c, 0));
             sub_multi_kernel<<<gb, 256, 0, st>>>(V, n, j + 1, c, w, n);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             CTR_TRY(dots(s, V, n, j + 1, w, n, nrm + 1, 0));   // second pass coefficients in nrm[1..]
             sub_multi_kernel<<<gb, 256, 0, st>>>(V, n, j + 1, nrm + 1, w, n);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             axpby_kernel<<<grid_for(j + 1, 128), 128, 0, st>>>(1.0, c, 1.0, nrm + 1, c, j + 1);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             CTR_TRY(dots(s, w, n, 1, w, n, nrm, 0));
             givens_kernel<<<1, 1, 0, st>>>(H, m + 1, j, c, nrm, k.cs.as<double>(), k.sn.as<double>(),
                                            k.s.as<double>(), sc, tol_abs);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             scale_kernel<<<gb, 256, 0, st>>>(w, sc, 1, w, n);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             CTR_TRY(read_scalars(s, hsc, 4));
             kdone = j + 1;
             --budget;
@@ -273,9 +273,9 @@ int gmres(ctr_ibim* s, int precision, const double* b, double* x, double tol_rel
             if (hsc[2] != 0.0 || hsc[3] != 0.0) break;
         }
         upper_solve_kernel<<<1, 1, 0, st>>>(H, m + 1, kdone, k.s.as<double>(), k.y.as<double>());
-        CTR_CUDA_TRY(cudaGetLastError());
+        CTR_LAUNCHED();
         add_multi_prec_kernel<<<gb, 256, 0, st>>>(V, n, kdone, k.y.as<double>(), x, s->M, il1, il2);
-        CTR_CUDA_TRY(cudaGetLastError());
+        CTR_LAUNCHED();
         if (hsc[2] != 0.0 || hsc[3] != 0.0) {
             converged = true;
             break;
@@ -285,7 +285,7 @@ int gmres(ctr_ibim* s, int precision, const double* b, double* x, double tol_rel
         CTR_TRY(apply_operator(s, x, v.u, precision));
         if (precision == CTR_FP32_REFINE) info->matvecs_fp32++; else info->matvecs_fp64++;
         axpby_kernel<<<gb, 256, 0, st>>>(1.0, b, -1.0, v.u, v.t, n);
-        CTR_CUDA_TRY(cudaGetLastError());
+        CTR_LAUNCHED();
         double rn = 0.0;
         CTR_TRY(device_dot(s, v.t, v.t, n, &rn));
         beta = std::sqrt(rn);
@@ -326,7 +326,7 @@ int solve_system(ctr_ibim* s, double* d_psi, double* d_dpsi, ctr_solve_info* inf
         CTR_TRY(apply_operator(s, v.x, v.u, s->opt.precision));
         info->matvecs_fp64++;
         axpby_kernel<<<gb, 256, 0, st>>>(1.0, g, -1.0, v.u, v.r, n);
-        CTR_CUDA_TRY(cudaGetLastError());
+        CTR_LAUNCHED();
     } else {
         CTR_CUDA_TRY(cudaMemsetAsync(v.x, 0, sizeof(double) * n, st));
         CTR_CUDA_TRY(cudaMemcpyAsync(v.r, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -338,12 +338,12 @@ int solve_system(ctr_ibim* s, double* d_psi, double* d_dpsi, ctr_solve_info* inf
             bool inner = false;
             CTR_TRY(gmres(s, CTR_FP32_REFINE, v.r, v.d, s->opt.inner_tol, budget, info, inner));
             axpby_kernel<<<gb, 256, 0, st>>>(1.0, v.x, 1.0, v.d, v.x, n);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
             CTR_TRY(apply_operator(s, v.x, v.u, s->opt.residual));
             info->matvecs_fp64++;
             info->refinements++;
             axpby_kernel<<<gb, 256, 0, st>>>(1.0, g, -1.0, v.u, v.r, n);
-            CTR_CUDA_TRY(cudaGetLastError());
+            CTR_LAUNCHED();
         }
     }
     double rn2 = 0.0;

@@ -480,7 +480,7 @@ __global__ void pack_kernel(const double* __restrict__ x, const double* __restri
 __global__ void finish_kernel(int64_t M, int S, const double* __restrict__ partial, const double* __restrict__ x,
                               double* __restrict__ y, const double* __restrict__ W, const int32_t* __restrict__ ptr,
                               const int32_t* __restrict__ node, const double* __restrict__ w, int64_t E,
-                              double lam1, double lam2, double h2, double h3w12) {
+                              double lam1, double lam2, double h2, double h3) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     double s1 = 0.0, s2 = 0.0;
@@ -492,7 +492,7 @@ __global__ void finish_kernel(int64_t M, int S, const double* __restrict__ parti
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
         const int m = node[e];
         const double Wm = W[m], r1 = x[m], r2 = x[M + m];
-        c1 += Wm * (h2 * w[e] * r1 - h3w12 * r2);
+        c1 += Wm * (h2 * w[e] * r1 - h3 * w[3 * E + e] * r2);
         c2 += Wm * (h2 * w[E + e] * r1 - h2 * w[2 * E + e] * r2);
     }
     y[i] = lam1 * x[i] + s1 + c1;
@@ -507,7 +507,7 @@ int launch_pairs(ctr_ibim* s, const typename Policy::Src* src, const PairPlan& p
     pair_kernel<Policy, R><<<grid, kThreads, smem, s->stream>>>(src, (int)s->M, s->corr_ptr.as<int32_t>(),
                                                                s->excl.as<int32_t>(), p.src_per_split,
                                                                s->partial.as<double>(), kc, s->err.as<int>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 
@@ -575,7 +575,7 @@ int plan_pairs(ctr_ibim* s) {
     CTR_TRY(s->partial.alloc(sizeof(double) * 2 * (size_t)S * s->M));
     CTR_TRY(s->srcdf.alloc(sizeof(float4) * 4 * (size_t)s->M));
     df_static_kernel<<<grid_for(s->M, 256), 256, 0, s->stream>>>(s->na, s->M, s->srcdf.as<float4>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 
@@ -587,7 +587,7 @@ int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision) {
     double4* s64 = (precision == CTR_FP64) ? s->src64.as<double4>() : nullptr;
     float4* sdf = (precision == CTR_DF64) ? s->srcdf.as<float4>() : nullptr;
     pack_kernel<<<grid_for(M, 256), 256, 0, st>>>(d_x, s->na.W, M, scale, s32, s64, sdf);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     PairConsts kc;
     kc.c1 = s->eps_out / s->eps_in;
     kc.c2 = s->eps_in / s->eps_out;
@@ -617,13 +617,13 @@ int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision) {
         CTR_TRY((launch_pairs<Fp64Policy, 1>(s, s64, *p, kc)));
     }
     const double h2 = s->h * s->h;
-    const double h3w12 = s->h * s->h * s->h * s->kappa / (4.0 * kPi);
+    const double h3 = s->h * s->h * s->h;
     finish_kernel<<<grid_for(M, 256), 256, 0, st>>>(M, p->splits, s->partial.as<double>(), d_x, d_y, s->na.W,
                                                    s->corr_ptr.as<int32_t>(), s->corr_node.as<int32_t>(),
                                                    s->corr_w.as<double>(), s->E,
                                                    0.5 * (1.0 + s->eps_out / s->eps_in),
-                                                   0.5 * (1.0 + s->eps_in / s->eps_out), h2, h3w12);
-    CTR_CUDA_TRY(cudaGetLastError());
+                                                   0.5 * (1.0 + s->eps_in / s->eps_out), h2, h3);
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 
@@ -661,7 +661,7 @@ int launch_fp32_pairs_external(const float4* src, int64_t M, const int32_t* eptr
     dim3 grid(p.target_blocks, p.splits);
     pair_kernel<Fp32Policy, 2><<<grid, kThreads, smem, st>>>(src, (int)M, eptr, excl, p.src_per_split, partial, kc,
                                                              err);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     *splits_out = p.splits;
     return CTR_OK;
 }

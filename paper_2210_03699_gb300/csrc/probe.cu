@@ -115,12 +115,12 @@ extern "C" int ctr_probe_rate(int kind, int64_t iters, double* ops_per_s, double
     if (kind < CTR_PROBE_FFMA || kind > CTR_PROBE_DFMA) return fail(CTR_ERR_INVALID, "unknown probe kind");
     if (kind == CTR_PROBE_FFMA2) per_thread_iter = 2 * kChains;
     launch(iters / 10 + 1);   // warm-up
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     CTR_CUDA_TRY(cudaEventRecord(e0));
     launch(iters);
     CTR_CUDA_TRY(cudaEventRecord(e1));
     CTR_CUDA_TRY(cudaEventSynchronize(e1));
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     float ms = 0.f;
     CTR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);

@@ -102,8 +102,8 @@ __device__ __forceinline__ double phi_avg(double x) {
 
 __global__ void geometry_kernel(const double* __restrict__ sd, const int64_t* __restrict__ lin, int64_t M,
                                 int64_t nx, int64_t ny, int64_t nz, double ox, double oy, double oz,
-                                double h, double eps, NodeArrays na, float4* __restrict__ src32,
-                                double4* __restrict__ src64, int* __restrict__ err) {
+                                double h, double eps, int kreg_all, NodeArrays na, uint8_t* __restrict__ bad,
+                                float4* __restrict__ src32, double4* __restrict__ src64, int* __restrict__ err) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const int64_t g = lin[m];
@@ -167,11 +167,16 @@ __global__ void geometry_kernel(const double* __restrict__ sd, const int64_t* __
     const double t2[3] = {ct * e1[0] + st * e2[0], ct * e1[1] + st * e2[1], ct * e1[2] + st * e2[2]};
     const double t1[3] = {-st * e1[0] + ct * e2[0], -st * e1[1] + ct * e2[1], -st * e1[2] + ct * e2[2]};
     // Jacobian (Eq. 2.8 with d > 0 outside), surface curvatures and M = diag(-k1, -k2)
-    const double J = (1.0 - dd * kp1) * (1.0 - dd * kp2);
+    double J = (1.0 - dd * kp1) * (1.0 - dd * kp2);
     const double k1 = kp1 / (1.0 - dd * kp1), k2 = kp2 / (1.0 - dd * kp2);
+    // hybrid classification (Sec. 3.2): untrustworthy curvature -> bad node, J = 1 (Eq. 3.2)
+    const bool finite = isfinite(J) && isfinite(k1) && isfinite(k2) && isfinite(t1[0] + t1[1] + t1[2]) &&
+                        isfinite(t2[0] + t2[1] + t2[2]);
+    const bool is_bad = kreg_all || !finite || fmax(fabs(k1), fabs(k2)) * (eps + h) >= 0.8;
+    if (is_bad) J = 1.0;
     const double W = J * phi_avg(dd / eps) / eps;
-    if (!isfinite(W) || !isfinite(k1) || !isfinite(k2) || !isfinite(P0 + P1 + P2) || !(gn > 0.0))
-        atomicOr(err, kErrNumeric);
+    if (!isfinite(W) || !isfinite(P0 + P1 + P2) || !(gn > 0.0)) atomicOr(err, kErrNumeric);
+    bad[m] = is_bad ? 1 : 0;
 
     na.Px[m] = P0; na.Py[m] = P1; na.Pz[m] = P2;
     na.nx[m] = n0; na.ny[m] = n1; na.nz[m] = n2;
@@ -211,7 +216,7 @@ __global__ void rhs_kernel(NodeArrays na, int64_t M, const double* __restrict__ 
 int exclusive_scan_i32(const int32_t* d_counts, int32_t* d_offsets, int64_t n, cudaStream_t st,
                        DevBuf& /*scratch*/) {
     scan_kernel<<<1, 1024, 0, st>>>(d_counts, d_offsets, n);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 
@@ -236,7 +241,7 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
     CTR_TRY(counts.alloc(sizeof(int32_t) * nchunks));
     CTR_TRY(offsets.alloc(sizeof(int32_t) * (nchunks + 1)));
     tube_count_kernel<<<(unsigned)nchunks, kScanThreads, 0, st>>>(d_sdist, total, s->eps, counts.as<int32_t>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     CTR_TRY(exclusive_scan_i32(counts.as<int32_t>(), offsets.as<int32_t>(), nchunks, st, scratch));
     int32_t Mh = 0;
     CTR_CUDA_TRY(cudaMemcpyAsync(&Mh, offsets.as<int32_t>() + nchunks, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -249,7 +254,7 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
     CTR_CUDA_TRY(cudaMemsetAsync(node_of.p, 0xff, sizeof(int32_t) * total, st));
     tube_compact_kernel<<<(unsigned)nchunks, kScanThreads, 0, st>>>(d_sdist, total, s->eps, offsets.as<int32_t>(),
                                                                     s->lin.as<int64_t>(), node_of.as<int32_t>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
 
     CTR_TRY(s->nodes.alloc(sizeof(double) * NodeArrays::kCount * M));
     double* b = s->nodes.as<double>();
@@ -259,10 +264,13 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
     for (int q = 0; q < NodeArrays::kCount; ++q) *f[q] = b + (size_t)q * M;
     CTR_TRY(s->src32.alloc(sizeof(float4) * 2 * M));
     CTR_TRY(s->src64.alloc(sizeof(double4) * 2 * M));
+    CTR_TRY(s->bad.alloc(M));
     geometry_kernel<<<grid_for(M, 128), 128, 0, st>>>(d_sdist, s->lin.as<int64_t>(), M, s->n[0], s->n[1], s->n[2],
-                                                     s->origin[0], s->origin[1], s->origin[2], s->h, s->eps, s->na,
-                                                     s->src32.as<float4>(), s->src64.as<double4>(), s->err.as<int>());
-    CTR_CUDA_TRY(cudaGetLastError());
+                                                     s->origin[0], s->origin[1], s->origin[2], s->h, s->eps,
+                                                     s->opt.method == CTR_METHOD_KREG ? 1 : 0, s->na,
+                                                     s->bad.as<uint8_t>(), s->src32.as<float4>(),
+                                                     s->src64.as<double4>(), s->err.as<int>());
+    CTR_LAUNCHED();
     CTR_TRY(check_device_error(s, "geometry"));
 
     // correction-weight tables (Ewald), then the correction matrix
@@ -277,7 +285,7 @@ int setup_rhs(ctr_ibim* s) {
     CTR_TRY(s->rhs.alloc(sizeof(double) * 2 * s->M));
     rhs_kernel<<<grid_for(s->M, 128), 128, 0, s->stream>>>(s->na, s->M, s->charges.as<double>(), s->nc, s->eps_in,
                                                           s->rhs.as<double>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 

@@ -80,7 +80,7 @@ extern "C" int ctr_pair_sum_fp32_static(int64_t M, const float* src, const int32
     CTR_TRY(launch_fp32_pairs_external(reinterpret_cast<const float4*>(src), M, row_ptr, excluded, eps_ratio, kappa,
                                        kScratchDoubles, p.scratch, p.flag, st, &splits));
     sum_splits_kernel<<<grid_for(2 * M, 256), 256, 0, st>>>(p.scratch, splits, M, out);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     int flag = 0;
     CTR_CUDA_TRY(cudaMemcpyAsync(&flag, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     CTR_CUDA_TRY(cudaStreamSynchronize(st));

@@ -17,6 +17,13 @@
 // Both routes give the same numbers (to ~1e-14); refinement needs ~10^5
 // lattice points per value, Ewald a few hundred.
 //
+// K-reg rows (Sec. 2.3) replace CTR2 at targets the hybrid classification
+// marks bad (Sec. 3.2): every tube node y in the cylinder around the normal
+// line of radius tau = 2h (distance of the tangent-plane projections of y and
+// x, computed unfused as v = y - P, s = (v0 n0 + v1 n1) + v2 n2,
+// t = v - s n, (t0 t0 + t1 t1) + t2 t2 < tau^2), in ascending node order, with
+// weights C11 = C21 = C22 = 0 and C12 = (e^{-kappa tau} - 1 + kappa tau)/(2 pi kappa tau^2).
+//
 // Correction matrix (per target node y_i, Sec. 2.4): the planes t_k of the
 // dominant axis, the singular line of Eq. (2.19), the nearest node and shift
 // (alpha, beta), the angular functions of the theorem in Sec. 2.4.1 (Eq. 2.28,
@@ -126,8 +133,37 @@ struct PlaneCtx {
     int64_t nx, ny, nz;
     double origin[3];
     double h, eps;
-    int K;
+    int K;       // planes on each side
+    int Kc;      // K-reg cylinder search half-width (grid nodes)
+    double tau;  // K-reg radius
 };
+
+// Visits the K-reg cylinder nodes of target i in ascending node order.
+template <typename F>
+__device__ void visit_cylinder(const PlaneCtx& c, const NodeArrays& na, const int64_t* lin,
+                               const int32_t* node_of, int64_t i, F&& fn) {
+    const double P[3] = {na.Px[i], na.Py[i], na.Pz[i]};
+    const double n[3] = {na.nx[i], na.ny[i], na.nz[i]};
+    const int64_t g = lin[i];
+    const int64_t ci = g % c.nx, cj = (g / c.nx) % c.ny, ck = g / (c.nx * c.ny);
+    const double tau2 = __dmul_rn(c.tau, c.tau);
+    for (int64_t k = max((int64_t)0, ck - c.Kc); k <= min(c.nz - 1, ck + c.Kc); ++k)
+        for (int64_t j = max((int64_t)0, cj - c.Kc); j <= min(c.ny - 1, cj + c.Kc); ++j)
+            for (int64_t q = max((int64_t)0, ci - c.Kc); q <= min(c.nx - 1, ci + c.Kc); ++q) {
+                const int32_t m = node_of[q + c.nx * (j + c.ny * k)];
+                if (m < 0) continue;
+                const double y0 = __dadd_rn(c.origin[0], __dmul_rn(c.h, (double)q));
+                const double y1 = __dadd_rn(c.origin[1], __dmul_rn(c.h, (double)j));
+                const double y2 = __dadd_rn(c.origin[2], __dmul_rn(c.h, (double)k));
+                const double v0 = __dsub_rn(y0, P[0]), v1 = __dsub_rn(y1, P[1]), v2 = __dsub_rn(y2, P[2]);
+                const double sdot = __dadd_rn(__dadd_rn(__dmul_rn(v0, n[0]), __dmul_rn(v1, n[1])), __dmul_rn(v2, n[2]));
+                const double t0 = __dsub_rn(v0, __dmul_rn(sdot, n[0]));
+                const double t1 = __dsub_rn(v1, __dmul_rn(sdot, n[1]));
+                const double t2 = __dsub_rn(v2, __dmul_rn(sdot, n[2]));
+                const double q2 = __dadd_rn(__dadd_rn(__dmul_rn(t0, t0), __dmul_rn(t1, t1)), __dmul_rn(t2, t2));
+                if (q2 < tau2) fn(m, 0.0, 0.0, 0.0);
+            }
+}
 
 // Visits the correction nodes of target i in ascending plane order.
 // fn(m, alpha, beta, eta) is called for each tube node found.
@@ -169,29 +205,34 @@ __device__ void visit_planes(const PlaneCtx& c, const NodeArrays& na, const int6
 }
 
 __global__ void corr_count_kernel(PlaneCtx c, NodeArrays na, const int64_t* __restrict__ lin,
-                                  const int32_t* __restrict__ node_of, int64_t M, int32_t* __restrict__ counts) {
+                                  const int32_t* __restrict__ node_of, const uint8_t* __restrict__ bad, int64_t M,
+                                  int32_t* __restrict__ counts) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     int cnt = 0;
-    visit_planes(c, na, lin, node_of, i, [&](int32_t, double, double, double) { ++cnt; });
+    auto inc = [&](int32_t, double, double, double) { ++cnt; };
+    if (bad[i]) visit_cylinder(c, na, lin, node_of, i, inc);
+    else visit_planes(c, na, lin, node_of, i, inc);
     counts[i] = cnt;
 }
 
 __global__ void corr_fill_kernel(PlaneCtx c, NodeArrays na, const int64_t* __restrict__ lin,
-                                 const int32_t* __restrict__ node_of, int64_t M, const int32_t* __restrict__ ptr,
-                                 int32_t* __restrict__ node, double* __restrict__ ab_eta, int64_t E,
-                                 int32_t* __restrict__ excl) {
+                                 const int32_t* __restrict__ node_of, const uint8_t* __restrict__ bad, int64_t M,
+                                 const int32_t* __restrict__ ptr, int32_t* __restrict__ node,
+                                 double* __restrict__ ab_eta, int64_t E, int32_t* __restrict__ excl) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     int e = ptr[i];
     const int e0 = e;
-    visit_planes(c, na, lin, node_of, i, [&](int32_t m, double alpha, double beta, double eta) {
+    auto put = [&](int32_t m, double alpha, double beta, double eta) {
         node[e] = m;
         ab_eta[e] = alpha;
         ab_eta[E + e] = beta;
         ab_eta[2 * E + e] = eta;
         ++e;
-    });
+    };
+    if (bad[i]) visit_cylinder(c, na, lin, node_of, i, put);
+    else visit_planes(c, na, lin, node_of, i, put);
     // sorted copy (insertion sort; at most a few entries) for the dense-sum exclusion
     for (int p = e0; p < e; ++p) {
         int32_t v = node[p];
@@ -217,10 +258,10 @@ __device__ void lagrange6(double x, int& i0, double cw[6]) {
     }
 }
 
-__global__ void corr_weight_kernel(NodeArrays na, const int32_t* __restrict__ ptr, int64_t M,
-                                   const double* __restrict__ ab_eta, int64_t E, const double* __restrict__ T,
-                                   double c11, double c22, double kappa2, double* __restrict__ w,
-                                   int* __restrict__ err) {
+__global__ void corr_weight_kernel(NodeArrays na, const uint8_t* __restrict__ bad, const int32_t* __restrict__ ptr,
+                                   int64_t M, const double* __restrict__ ab_eta, int64_t E,
+                                   const double* __restrict__ T, double c11, double c22, double kappa2,
+                                   double w12_ctr, double w12_kreg, double* __restrict__ w, int* __restrict__ err) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     // target of entry e: binary search in ptr
@@ -230,6 +271,12 @@ __global__ void corr_weight_kernel(NodeArrays na, const int32_t* __restrict__ pt
         if (ptr[mid] <= e) lo = mid; else hi = mid;
     }
     const int64_t i = lo;
+    if (bad[i]) {   // K-reg row: only the constant C12 (Sec. 2.3)
+        w[e] = w[E + e] = w[2 * E + e] = 0.0;
+        w[3 * E + e] = w12_kreg;
+        return;
+    }
+    w[3 * E + e] = w12_ctr;
     const double alpha = ab_eta[e], beta = ab_eta[E + e], eta = ab_eta[2 * E + e];
     const double n[3] = {na.nx[i], na.ny[i], na.nz[i]};
     int a = 0;
@@ -270,7 +317,7 @@ __global__ void corr_weight_kernel(NodeArrays na, const int32_t* __restrict__ pt
     lagrange6(beta, j0, cb);
     if (i0 + kTabHalf < 0 || j0 + kTabHalf < 0 || i0 + 5 + kTabHalf >= kTabN || j0 + 5 + kTabHalf >= kTabN) {
         atomicOr(err, kErrCapacity);   // shift outside the tabulated range (cannot happen for |alpha| <= 1/2)
-        w[e] = w[E + e] = w[2 * E + e] = 0.0;
+        w[e] = w[E + e] = w[2 * E + e] = w[3 * E + e] = 0.0;
         return;
     }
     double wA = 0.0, wB = 0.0;
@@ -312,7 +359,7 @@ int upload_trig(int device) {
 int weight_tables_device(double* d_tables, cudaStream_t st) {
     const int n = kModes * kTabN * kTabN;
     ewald_tables_kernel<<<grid_for(n, 128), 128, 0, st>>>(d_tables);
-    CTR_CUDA_TRY(cudaGetLastError());
+    CTR_LAUNCHED();
     return CTR_OK;
 }
 
@@ -326,12 +373,14 @@ int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node
     c.h = s->h;
     c.eps = s->eps;
     c.K = (int)ceil(2.0 * s->eps / s->h) + 2;
+    c.tau = 2.0 * s->h;
+    c.Kc = (int)ceil((s->eps + c.tau) / s->h) + 1;
     DevBuf counts, scratch, abeta;
     CTR_TRY(counts.alloc(sizeof(int32_t) * M));
     CTR_TRY(s->corr_ptr.alloc(sizeof(int32_t) * (M + 1)));
-    corr_count_kernel<<<grid_for(M, 128), 128, 0, st>>>(c, s->na, s->lin.as<int64_t>(), d_node_of, M,
-                                                       counts.as<int32_t>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    corr_count_kernel<<<grid_for(M, 128), 128, 0, st>>>(c, s->na, s->lin.as<int64_t>(), d_node_of,
+                                                       s->bad.as<uint8_t>(), M, counts.as<int32_t>());
+    CTR_LAUNCHED();
     CTR_TRY(exclusive_scan_i32(counts.as<int32_t>(), s->corr_ptr.as<int32_t>(), M, st, scratch));
     int32_t Eh = 0;
     CTR_CUDA_TRY(cudaMemcpyAsync(&Eh, s->corr_ptr.as<int32_t>() + M, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -340,19 +389,24 @@ int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node
     s->E = E;
     CTR_TRY(s->corr_node.alloc(sizeof(int32_t) * (E > 0 ? E : 1)));
     CTR_TRY(s->excl.alloc(sizeof(int32_t) * (E > 0 ? E : 1)));
-    CTR_TRY(s->corr_w.alloc(sizeof(double) * 3 * (E > 0 ? E : 1)));
+    CTR_TRY(s->corr_w.alloc(sizeof(double) * 4 * (E > 0 ? E : 1)));
     CTR_TRY(abeta.alloc(sizeof(double) * 3 * (E > 0 ? E : 1)));
-    corr_fill_kernel<<<grid_for(M, 128), 128, 0, st>>>(c, s->na, s->lin.as<int64_t>(), d_node_of, M,
-                                                      s->corr_ptr.as<int32_t>(), s->corr_node.as<int32_t>(),
-                                                      abeta.as<double>(), E, s->excl.as<int32_t>());
-    CTR_CUDA_TRY(cudaGetLastError());
+    corr_fill_kernel<<<grid_for(M, 128), 128, 0, st>>>(c, s->na, s->lin.as<int64_t>(), d_node_of,
+                                                      s->bad.as<uint8_t>(), M, s->corr_ptr.as<int32_t>(),
+                                                      s->corr_node.as<int32_t>(), abeta.as<double>(), E,
+                                                      s->excl.as<int32_t>());
+    CTR_LAUNCHED();
     if (E > 0) {
         const double c11 = 1.0 - s->eps_out / s->eps_in;
         const double c22 = 1.0 - s->eps_in / s->eps_out;
-        corr_weight_kernel<<<grid_for(E, 128), 128, 0, st>>>(s->na, s->corr_ptr.as<int32_t>(), M, abeta.as<double>(), E,
-                                                            d_tables, c11, c22, s->kappa * s->kappa,
-                                                            s->corr_w.as<double>(), s->err.as<int>());
-        CTR_CUDA_TRY(cudaGetLastError());
+        const double tau = 2.0 * s->h;
+        const double k = s->kappa;
+        const double w12_kreg = (k == 0.0) ? 0.0 : (exp(-k * tau) - 1.0 + k * tau) / (2.0 * kPi * k * tau * tau);
+        corr_weight_kernel<<<grid_for(E, 128), 128, 0, st>>>(s->na, s->bad.as<uint8_t>(), s->corr_ptr.as<int32_t>(), M,
+                                                            abeta.as<double>(), E, d_tables, c11, c22, k * k,
+                                                            k / (4.0 * kPi), w12_kreg, s->corr_w.as<double>(),
+                                                            s->err.as<int>());
+        CTR_LAUNCHED();
     }
     CTR_CUDA_TRY(cudaStreamSynchronize(st));
     return CTR_OK;

@@ -58,7 +58,27 @@ def test_weight_tables_match_oracle(ctr, oracle_tables):
     assert np.max(np.abs(T - oracle_tables)) < 1e-11
 
 
-@pytest.mark.parametrize("which", ["sphere", "ellipsoid"])
+@pytest.fixture(scope="module")
+def molecule(ctr, oracle_tables):
+    """60-atom synthetic molecule, SES at h = 0.5: HYB-IBIM with many bad nodes."""
+    prob = syn.molecule_problem(n_atoms=60, seed=0, h=0.5)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables)
+    G = ctr.CtrIbim.from_problem(prob)
+    yield prob, S, G
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def sphere_kreg(ctr, oracle_tables):
+    """The K-reg method (Sec. 2.3) everywhere on the sphere."""
+    prob = syn.sphere_problem(h=0.25)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables, method="kreg")
+    G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, method=ctr.METHOD_KREG))
+    yield prob, S, G
+    G.close()
+
+
+@pytest.mark.parametrize("which", ["sphere", "ellipsoid", "molecule", "sphere_kreg"])
 def test_setup_parity(which, request):
     prob, S, G = request.getfixturevalue(which)
     assert G.M == S.M
@@ -67,17 +87,19 @@ def test_setup_parity(which, request):
     assert np.array_equal(P, S.geo.P)
     assert np.array_equal(n, S.geo.n)
     assert _rel(W, S.geo.W) < 1e-12
+    assert np.array_equal(G.bad_nodes(), S.geo.bad)
     ptr, node, w = G.corrections()
     assert np.array_equal(ptr, S.corr.ptr)
     assert np.array_equal(node, S.corr.node)
     assert _rel(w[0], S.omega11) < 1e-10
     assert _rel(w[1], S.omega21) < 1e-10
     assert _rel(w[2], S.omega22) < 1e-10
+    assert _rel(w[3], S.omega12) < 1e-14
     assert _rel(G.rhs(), S.rhs()) < 1e-12
     assert abs(G.area() / S.area() - 1) < 1e-12
 
 
-@pytest.mark.parametrize("which", ["sphere", "ellipsoid"])
+@pytest.mark.parametrize("which", ["sphere", "ellipsoid", "molecule", "sphere_kreg"])
 def test_operator_parity(which, request, ctr):
     prob, S, G = request.getfixturevalue(which)
     p = syn.random_density(S.M, seed=11, smooth_points=S.geo.P)
@@ -147,6 +169,36 @@ def test_solve_fp32_refine_parity(ellipsoid, ctr):
     assert info.converged
     assert _rel(psid, psi_o) < 1e-10 and _rel(dpsid, dpsi_o) < 1e-10
     Gdf.close()
+
+
+def test_solve_molecule_hyb_parity(molecule, ctr):
+    prob, S, G = molecule
+    assert 0 < S.geo.bad.sum() < S.M
+    psi_o, dpsi_o, info_o = S.solve(tol=1e-12, max_iter=400)
+    assert info_o["converged"]
+    Go, _ = oenergy.polarization_energy(S, psi_o, dpsi_o)
+    G32 = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE,
+                                                               tol=1e-11))
+    psi, dpsi, info = G32.solve()
+    assert info.converged
+    assert _rel(psi, psi_o) < 1e-6 and _rel(dpsi, dpsi_o) < 1e-6
+    Gp, _ = G32.energy(psi, dpsi)
+    assert abs(Gp / Go - 1) < 1e-6
+    G32.close()
+
+
+def test_solve_kreg_parity(sphere_kreg, ctr):
+    prob, S, G = sphere_kreg
+    psi_o, dpsi_o, _ = S.solve(tol=1e-13)
+    Gk = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, method=ctr.METHOD_KREG,
+                                                              tol=1e-13))
+    psi, dpsi, info = Gk.solve()
+    assert info.converged
+    assert _rel(psi, psi_o) < 1e-10 and _rel(dpsi, dpsi_o) < 1e-10
+    Gp, _ = Gk.energy(psi, dpsi)
+    # K-reg is first order: a few percent from Kirkwood at h = 0.25 (CTR2: 1e-6)
+    assert 1e-3 < abs(Gp / -0.019695646775266615 - 1) < 0.1
+    Gk.close()
 
 
 def test_solve_on_device_buffers(sphere, ctr):

@@ -299,3 +299,40 @@ def test_kirkwood_energy(sphere_c1):
     assert abs(G / gold["G_pol"] - 1.0) < 5e-4
     assert np.abs(psi / gold["psi_boundary"] - 1.0).max() < 2e-2
     assert np.abs(dpsi / gold["dpsi_boundary"] - 1.0).max() < 2e-2
+
+
+# ---------------------------------------------------------------- K-reg / HYB (Secs. 2.3, 3.2)
+def test_kreg_constant_is_disc_average():
+    """C12 of Sec. 2.3 equals the tangent-disc average of (G0 - Gk) (independent quadrature)."""
+    from oracle.correction import kreg_constant
+    for kappa, tau in [(0.1257, 0.5), (1.0, 0.25), (3.0, 0.1)]:
+        x, w = np.polynomial.legendre.leggauss(200)
+        r = 0.5 * tau * (x + 1)
+        wr = 0.5 * tau * w
+        avg = np.sum(wr * 2 * np.pi * r * (1 - np.exp(-kappa * r)) / (4 * np.pi * r)) / (np.pi * tau * tau)
+        assert abs(kreg_constant(kappa, tau) - avg) < 1e-13
+    assert kreg_constant(0.0, 0.5) == 0.0
+
+
+def test_kreg_is_first_order_and_worse_than_ctr2(oracle_tables):
+    """Paper Sec. 2.6: K-reg has order 1 and an error constant far above CTR2's."""
+    gold = json.load(open(os.path.join(GOLDEN, "kirkwood_sphere_R2.json")))
+    prob = syn.sphere_problem(h=0.25)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables, method="kreg")
+    assert S.geo.bad.all() and np.allclose(S.geo.J, 1.0)
+    psi, dpsi, info = S.solve(tol=1e-11)
+    G, _ = energy.polarization_energy(S, psi, dpsi)
+    err_kreg = abs(G / gold["G_pol"] - 1)
+    assert 1e-2 < err_kreg < 0.1
+    # every K-reg row corrects the nodes of its tangent cylinder (tens of nodes at tau = 2h)
+    assert 30 < np.diff(S.corr.ptr).mean() < 70 and np.all(S.corr.kreg)
+
+
+def test_hybrid_classification_on_smooth_and_kinked_surfaces(oracle_tables):
+    prob = syn.ellipsoid_problem(h=0.2)
+    geo = geometry.tube_geometry(prob.grid.n, prob.grid.origin, prob.grid.h, prob.sdist, prob.tube)
+    assert not geo.bad.any()                 # smooth, resolved: HYB is plain CTR2
+    mol = syn.molecule_problem(n_atoms=30, seed=1, h=0.5)
+    geo = geometry.tube_geometry(mol.grid.n, mol.grid.origin, mol.grid.h, mol.sdist, mol.tube)
+    assert geo.bad.any() and not geo.bad.all()
+    assert np.all(geo.J[geo.bad] == 1.0) and np.all(np.isfinite(geo.W)) and np.all(geo.W >= 0)

@@ -29,7 +29,7 @@ def _pair_part_from_matvec(G, ctr, x, h, kappa, eps_in, eps_out):
     lam2 = 0.5 * (1 + eps_in / eps_out)
     rows = np.repeat(np.arange(M), np.diff(ptr))
     Wm = W[node]
-    c1 = Wm * (h * h * w[0] * x[node] - h ** 3 * kappa / (4 * math.pi) * x[M + node])
+    c1 = Wm * (h * h * w[0] * x[node] - h ** 3 * w[3] * x[M + node])
     c2 = Wm * (h * h * w[1] * x[node] - h * h * w[2] * x[M + node])
     corr1 = np.bincount(rows, weights=c1, minlength=M)
     corr2 = np.bincount(rows, weights=c2, minlength=M)
