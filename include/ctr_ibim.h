@@ -197,6 +197,22 @@ int ctr_ibim_matvec(ctr_ibim* sys, const double* x, double* y, int precision, in
 int ctr_ibim_solve(ctr_ibim* sys, double* psi, double* dpsi_n, int on_device, ctr_solve_info* info);
 
 /*
+ * Solves n systems together (Sec. 2.5 solver, as ctr_ibim_solve, for each):
+ * one multi-slot engine advances all of them in lockstep steps, each step one
+ * Arnoldi iteration for every system still iterating and one true-residual
+ * evaluation for every system at the end of a cycle; the dense pair sums of
+ * all systems run in shared persistent launches, and the step's kernel
+ * sequence is replayed as one CUDA graph.  Every system's arithmetic is the
+ * same as when it is solved alone, so its result is bitwise identical.
+ *   systems   n distinct handles on one device (any sizes, any options).
+ *   psi, dpsi_n  n output pointers each, M_i doubles, host or device (on_device).
+ *   infos     n entries, or NULL.
+ * Returns CTR_NOT_CONVERGED when any system stopped at its limits.
+ */
+int ctr_ibim_batch_solve(ctr_ibim* const* systems, int64_t n, double* const* psi, double* const* dpsi_n,
+                         int on_device, ctr_solve_info* infos);
+
+/*
  * Reaction potential at every charge (Eq. 2.31, trapezoidal rule on the
  * tube) and the polarization energy G_pol = 1/2 sum_k q_k psi_rxn(z_k)
  * (Eq. 3.3).  psi, dpsi_n: M doubles each (host or device, on_device);

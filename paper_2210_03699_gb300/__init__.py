@@ -18,7 +18,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "kernel_launches", "library_path", "lib",
+__all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "kernel_launches", "batch_solve",
+           "library_path", "lib",
            "FP64", "FP32_REFINE", "DF64", "METHOD_HYB", "METHOD_KREG"]
 
 FP64 = 0
@@ -109,6 +110,8 @@ def _load():
         "ctr_ibim_area": (ctypes.c_int, [P, _D]),
         "ctr_ibim_matvec": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int]),
         "ctr_ibim_solve": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.POINTER(_Info)]),
+        "ctr_ibim_batch_solve": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int64, ctypes.POINTER(P),
+                                                ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(_Info)]),
         "ctr_ibim_energy": (ctypes.c_int, [P, P, P, ctypes.c_int, _D, P]),
         "ctr_ibim_reaction_potential": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int64, P, P]),
         "ctr_weight_tables": (ctypes.c_int, [P]),
@@ -310,6 +313,35 @@ class CtrIbim:
         _check(lib.ctr_ibim_reaction_potential(self._h, pp, dd, dev, z.shape[0], z.ctypes.data_as(ctypes.c_void_p),
                                                out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+
+def batch_solve(systems, device: bool = False):
+    """Solve several CtrIbim systems together in one multi-slot engine (see ctr_ibim_batch_solve).
+
+    Returns a list of (psi, dpsi, SolveInfo), one per system.
+    """
+    n = len(systems)
+    if n == 0:
+        return []
+    handles = (ctypes.c_void_p * n)(*[s._h for s in systems])
+    outs = []
+    if device:
+        import torch
+        for s in systems:
+            outs.append((torch.empty(s.M, dtype=torch.float64, device="cuda"),
+                         torch.empty(s.M, dtype=torch.float64, device="cuda")))
+        pp = (ctypes.c_void_p * n)(*[ctypes.c_void_p(o[0].data_ptr()) for o in outs])
+        dp = (ctypes.c_void_p * n)(*[ctypes.c_void_p(o[1].data_ptr()) for o in outs])
+    else:
+        for s in systems:
+            outs.append((np.empty(s.M), np.empty(s.M)))
+        pp = (ctypes.c_void_p * n)(*[o[0].ctypes.data_as(ctypes.c_void_p) for o in outs])
+        dp = (ctypes.c_void_p * n)(*[o[1].ctypes.data_as(ctypes.c_void_p) for o in outs])
+    infos = (_Info * n)()
+    st = lib.ctr_ibim_batch_solve(handles, n, pp, dp, 1 if device else 0, infos)
+    _check(st, allow=(0, 1))
+    return [(o[0], o[1], SolveInfo(i.iterations, i.refinements, i.matvecs_fp32, i.matvecs_fp64, i.residual,
+                                   bool(i.converged), st)) for o, i in zip(outs, infos)]
 
 
 def kernel_launches() -> int:

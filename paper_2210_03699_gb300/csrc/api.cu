@@ -6,6 +6,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "engine.cuh"
 
 namespace ctr {
 
@@ -21,6 +22,7 @@ int fail(int status, const std::string& msg) {
 static std::atomic<int64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 }  // namespace ctr
 
@@ -315,27 +317,43 @@ int ctr_ibim_matvec(ctr_ibim* s, const double* x, double* y, int precision, int 
 
 int ctr_ibim_solve(ctr_ibim* s, double* psi, double* dpsi_n, int on_device, ctr_solve_info* info) {
     if (!s || !psi || !dpsi_n) return fail(CTR_ERR_INVALID, "NULL argument");
+    ctr_ibim* hs[1] = {s};
+    double* p[1] = {psi};
+    double* d[1] = {dpsi_n};
+    return ctr_ibim_batch_solve(hs, 1, p, d, on_device, info);
+}
+
+int ctr_ibim_batch_solve(ctr_ibim* const* systems, int64_t n, double* const* psi, double* const* dpsi_n,
+                         int on_device, ctr_solve_info* infos) {
+    if (n < 0 || (n > 0 && (!systems || !psi || !dpsi_n))) return fail(CTR_ERR_INVALID, "NULL argument");
+    if (n == 0) return CTR_OK;
     return guarded([&]() -> int {
-        CTR_TRY(use_device(s));
-        ctr_solve_info local;
-        std::memset(&local, 0, sizeof(local));
-        const int64_t M = s->M;
-        DevBuf out;
-        double *dp = psi, *dd = dpsi_n;
-        if (!on_device) {
-            CTR_TRY(out.alloc(sizeof(double) * 2 * M));
-            dp = out.as<double>();
-            dd = dp + M;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!systems[i] || !psi[i] || !dpsi_n[i]) return fail(CTR_ERR_INVALID, "NULL system or output");
+            if (systems[i]->device != systems[0]->device)
+                return fail(CTR_ERR_INVALID, "all systems of a batch must be on one device");
+            for (int64_t k = 0; k < i; ++k)
+                if (systems[k] == systems[i]) return fail(CTR_ERR_INVALID, "a system appears twice in the batch");
         }
-        int st = solve_system(s, dp, dd, &local);
-        if (info) *info = local;
+        CTR_TRY(use_device(systems[0]));
+        std::vector<ctr_solve_info> local;
+        int64_t steps = 0;
+        const int st = engine_solve_all(systems, n, 1, &local, &steps);
+        if (infos)
+            for (int64_t i = 0; i < n && i < (int64_t)local.size(); ++i) infos[i] = local[i];
         if (st < 0) return st;
-        if (!on_device) {
-            CTR_CUDA_TRY(cudaMemcpyAsync(psi, dp, sizeof(double) * M, cudaMemcpyDeviceToHost, s->stream));
-            CTR_CUDA_TRY(cudaMemcpyAsync(dpsi_n, dd, sizeof(double) * M, cudaMemcpyDeviceToHost, s->stream));
+        bool all_conv = true;
+        for (int64_t i = 0; i < n; ++i) {
+            ctr_ibim* s = systems[i];
+            const int64_t M = s->M;
+            const double* x = s->vecs.as<double>();
+            const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            CTR_CUDA_TRY(cudaMemcpyAsync(psi[i], x, sizeof(double) * M, kind, s->stream));
+            CTR_CUDA_TRY(cudaMemcpyAsync(dpsi_n[i], x + M, sizeof(double) * M, kind, s->stream));
+            CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+            all_conv &= (local[i].converged != 0);
         }
-        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
-        return st;
+        return all_conv ? CTR_OK : CTR_NOT_CONVERGED;
     });
 }
 

@@ -47,6 +47,7 @@ int fail(int status, const std::string& msg);
 
 // After every kernel launch: count it and surface launch errors.
 void count_launch();
+void count_launches(int64_t n);
 #define CTR_LAUNCHED()                      \
     do {                                    \
         ::ctr::count_launch();              \
@@ -164,8 +165,7 @@ int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node
 // pairsum.cu
 int plan_pairs(ctr_ibim* s);
 int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision);
-// krylov.cu
-int solve_system(ctr_ibim* s, double* d_psi, double* d_dpsi, ctr_solve_info* info);
+// krylov.cu: solver workspace
 // energy.cu
 int reaction_potential(ctr_ibim* s, const double* d_psi, const double* d_dpsi, int64_t npts,
                        const double* d_xyz, double* d_out);

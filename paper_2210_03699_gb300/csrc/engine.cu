@@ -1,0 +1,741 @@
+// Multi-slot solver engine: many CTR-IBIM systems advanced together on one GPU.
+//
+// Each slot holds one system (a ctr_ibim handle) and its solver state on the
+// device.  The solver is right-preconditioned GMRES(m) (CGS2, FP64 Givens) on
+// the operator of Eq. (2.30); every cycle ends by recomputing the true
+// residual r = g - A x with the residual pair arithmetic and starting the next
+// cycle from it.  With FP32 inner pairs and an FP64-accurate residual this is
+// GMRES-based iterative refinement; with the same precision inside and out it
+// is plain restarted GMRES.
+//
+// One engine step, captured once as a CUDA graph and replayed:
+//   inner half   (slots in state INNER)  one Arnoldi iteration:
+//                z = Lambda^-1 V_j, pack, pairs, finish w = A z, CGS2 (two passes
+//                of batched dot products and updates), norm, Givens, scale, advance;
+//   update half  (slots in state UPDATE) x += Lambda^-1 V y, pack, pairs,
+//                finish r = g - A x, norm, decide (done / next cycle), start cycle.
+// The dense pair sums of all slots run in persistent kernels (one per pair
+// arithmetic and half) whose blocks take work items (slot, target block,
+// source split) from a list sorted by cost through an atomic counter; items of
+// slots in another state return at once.  A slot's items, partial-sum layout,
+// reduction chunks and scalar updates are exactly those of the slot alone, so
+// a system's result does not depend on what else the engine holds.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "engine.cuh"
+#include "pairkern.cuh"
+
+namespace ctr {
+
+using namespace pk;
+
+namespace {
+
+constexpr int kVecThreads = 256;
+
+__device__ __forceinline__ double block_sum_d(double v) {
+    __shared__ double sh[kVecThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kVecThreads / 32; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ bool inner_active(const SlotDev& s) { return s.stat.state == kSlotInner; }
+__device__ __forceinline__ bool update_active(const SlotDev& s) { return s.stat.state == kSlotUpdate; }
+
+// ---------------------------------------------------------------- packing
+__device__ __forceinline__ void pack_weights(const SlotDev& s, int prec, int64_t t, double a, double b) {
+    if (prec == CTR_FP32_REFINE) {
+        s.src32[2 * t].w = (float)a;
+        s.src32[2 * t + 1].w = (float)b;
+    } else if (prec == CTR_FP64) {
+        s.src64[2 * t].w = a;
+        s.src64[2 * t + 1].w = b;
+    } else {
+        const float ah = (float)a, bh = (float)b;
+        s.srcdf[4 * t].w = ah;
+        s.srcdf[4 * t + 1].w = (float)(a - (double)ah);
+        s.srcdf[4 * t + 2].w = bh;
+        s.srcdf[4 * t + 3].w = (float)(b - (double)bh);
+    }
+}
+
+// inner: z = Lambda^-1 V_j and the weights of z
+__global__ void k_prep_inner(SlotDev* S) {
+    const SlotDev& s = S[blockIdx.y];
+    if (!inner_active(s)) return;
+    const int64_t M = s.M;
+    const double* v = s.V + (size_t)s.j * s.n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+        const double z1 = v[t] * s.il1, z2 = v[M + t] * s.il2;
+        s.z[t] = z1;
+        s.z[M + t] = z2;
+        pack_weights(s, s.inner_prec, t, s.scale * s.W[t] * z1, s.scale * s.W[t] * z2);
+    }
+}
+
+// update: x += Lambda^-1 V y (k columns) and the weights of x
+__global__ void k_update_x(SlotDev* S) {
+    const SlotDev& s = S[blockIdx.y];
+    if (!update_active(s)) return;
+    const int64_t M = s.M, n = s.n;
+    const int k = s.kdone;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+        double v1 = 0.0, v2 = 0.0;
+        for (int i = 0; i < k; ++i) {
+            v1 += s.V[(size_t)i * n + t] * s.y[i];
+            v2 += s.V[(size_t)i * n + M + t] * s.y[i];
+        }
+        const double x1 = s.x[t] + v1 * s.il1, x2 = s.x[M + t] + v2 * s.il2;
+        s.x[t] = x1;
+        s.x[M + t] = x2;
+        pack_weights(s, s.res_prec, t, s.scale * s.W[t] * x1, s.scale * s.W[t] * x2);
+    }
+}
+
+// ---------------------------------------------------------------- persistent pair kernels
+template <typename Policy, int R>
+__global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int4* __restrict__ items,
+                                                    const int* __restrict__ n_items, int* __restrict__ counter,
+                                                    int half, int prec, const float2* __restrict__ exp_tab,
+                                                    int* __restrict__ err) {
+    using Src = typename Policy::Src;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Src* ring = reinterpret_cast<Src*>(smem_raw);
+    float2* tab = reinterpret_cast<float2*>(smem_raw + 2 * Policy::kTile * Policy::kVec * sizeof(Src));
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int cur;
+    __shared__ PairConsts kc;
+    if (threadIdx.x == 0) kc.exp_tab = exp_tab;   // one table per device, shared by every slot
+    __syncthreads();
+    pair_block_init<Policy>(kc, tab, bar);
+    uint32_t gt = 0;
+    const int total = *n_items;
+    for (;;) {
+        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = cur;
+        __syncthreads();
+        if (it >= total) break;
+        const int4 item = items[it];   // slot, target block, split, unused
+        const SlotDev& s = S[item.x];
+        const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec)
+                                    : (update_active(s) && s.res_prec == prec);
+        if (!want) continue;
+        if (threadIdx.x == 0) kc = s.kc;
+        __syncthreads();
+        const int per = (prec == CTR_FP32_REFINE) ? s.per32 : (prec == CTR_DF64 ? s.perdf : s.per64);
+        const int j_begin = item.z * per;
+        const int j_end = min(s.M, j_begin + per);
+        const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
+                                                      : prec == CTR_DF64 ? (const void*)s.srcdf
+                                                                         : (const void*)s.src64);
+        if (!pair_item<Policy, R>(src, s.M, s.cptr, s.excl, item.y, j_begin, j_end, item.z, s.part, kc, err, ring,
+                                  tab, bar, gt))
+            return;
+        __syncthreads();
+    }
+}
+
+// finish: diag + fixed-order split sum + correction of the applied vector;
+// inner: w = V_{j+1} = A z;   update: r = g - A x
+__global__ void k_finish(SlotDev* S, int half) {
+    const SlotDev& s = S[blockIdx.y];
+    if (half == 0 ? !inner_active(s) : !update_active(s)) return;
+    const int64_t M = s.M, E = s.E;
+    const double* x = (half == 0) ? s.z : s.x;
+    const int prec = (half == 0) ? s.inner_prec : s.res_prec;
+    const int splits = (prec == CTR_FP32_REFINE) ? s.sp32 : (prec == CTR_DF64 ? s.spdf : s.sp64);
+    double* out = (half == 0) ? s.V + (size_t)(s.j + 1) * s.n : s.r;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int q = 0; q < splits; ++q) {
+            s1 += s.part[((size_t)q * 2 + 0) * M + i];
+            s2 += s.part[((size_t)q * 2 + 1) * M + i];
+        }
+        double c1 = 0.0, c2 = 0.0;
+        for (int e = s.cptr[i]; e < s.cptr[i + 1]; ++e) {
+            const int m = s.cnode[e];
+            const double Wm = s.W[m], r1 = x[m], r2 = x[M + m];
+            c1 += Wm * (s.h2 * s.cw[e] * r1 - s.h3 * s.cw[3 * E + e] * r2);
+            c2 += Wm * (s.h2 * s.cw[E + e] * r1 - s.h2 * s.cw[2 * E + e] * r2);
+        }
+        const double y1 = s.lam1 * x[i] + s1 + c1;
+        const double y2 = s.lam2 * x[M + i] + s2 + c2;
+        if (half == 0) {
+            out[i] = y1;
+            out[M + i] = y2;
+        } else {
+            out[i] = s.g[i] - y1;
+            out[M + i] = s.g[M + i] - y2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- batched reductions (same chunking as alone)
+// mode 0/1: c = V[0..j] . w (first / second Gram-Schmidt pass), 2: |w|^2, 3: |r|^2
+__global__ void k_dots_partial(SlotDev* S, int mode) {
+    const SlotDev& s = S[blockIdx.y];
+    const bool act = (mode == 3) ? update_active(s) : inner_active(s);
+    if (!act || (int)blockIdx.x >= s.nblk) return;
+    const int64_t n = s.n;
+    const int64_t chunk = (n + s.nblk - 1) / s.nblk;
+    const int64_t t0 = (int64_t)blockIdx.x * chunk, t1 = min(n, t0 + chunk);
+    const double* w = (mode == 3) ? s.r : s.V + (size_t)(s.j + 1) * n;
+    const int count = (mode <= 1) ? s.j + 1 : 1;
+    for (int i = 0; i < count; ++i) {
+        const double* a = (mode <= 1) ? s.V + (size_t)i * n : w;
+        double v = 0.0;
+        for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) v += a[t] * w[t];
+        v = block_sum_d(v);
+        if (threadIdx.x == 0) s.dpart[(size_t)i * s.nblk + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_dots_final(SlotDev* S, int mode) {
+    const SlotDev& s = S[blockIdx.y];
+    const bool act = (mode == 3) ? update_active(s) : inner_active(s);
+    if (!act) return;
+    const int count = (mode <= 1) ? s.j + 1 : 1;
+    const int i = blockIdx.x;
+    if (i >= count) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < s.nblk; b += blockDim.x) v += s.dpart[(size_t)i * s.nblk + b];
+    v = block_sum_d(v);
+    if (threadIdx.x == 0) {
+        double* out = (mode == 0) ? s.cgs : (mode == 1) ? s.cgs2 : (mode == 2) ? s.scal : s.scal + 1;
+        out[i] = v;
+    }
+}
+
+// w -= V[0..j] c   (pass: 0 first coefficients, 1 second)
+__global__ void k_sub(SlotDev* S, int pass) {
+    const SlotDev& s = S[blockIdx.y];
+    if (!inner_active(s)) return;
+    const int64_t n = s.n;
+    double* w = s.V + (size_t)(s.j + 1) * n;
+    const double* c = pass ? s.cgs2 : s.cgs;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double v = w[t];
+        for (int i = 0; i <= s.j; ++i) v -= s.V[(size_t)i * n + t] * c[i];
+        w[t] = v;
+    }
+}
+
+// Givens update of Hessenberg column j (one thread per slot)
+__global__ void k_givens(SlotDev* S, int cap) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (!inner_active(s)) return;
+    const int j = s.j, ldh = s.m + 1;
+    double* col = s.H + (size_t)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = s.cgs[i] + s.cgs2[i];
+    const double hn = sqrt(s.scal[0]);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = s.cs[i] * col[i] + s.sn[i] * col[i + 1];
+        col[i + 1] = -s.sn[i] * col[i] + s.cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    s.cs[j] = col[j] / den;
+    s.sn[j] = col[j + 1] / den;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    s.sv[j + 1] = -s.sn[j] * s.sv[j];
+    s.sv[j] = s.cs[j] * s.sv[j];
+    s.scal[2] = hn;
+    s.stat.iterations++;
+    if (s.inner_prec == CTR_FP32_REFINE) s.stat.matvecs_fp32++; else s.stat.matvecs_fp64++;
+    s.budget--;
+    const double est = fabs(s.sv[j + 1]);
+    if (!isfinite(est)) s.stat.numeric_error = 1;
+    s.cycle_end = (est <= s.tol_cycle || j + 1 == s.m || s.budget <= 0 || hn == 0.0 || !isfinite(est)) ? 1 : 0;
+}
+
+__global__ void k_scale_next(SlotDev* S) {
+    const SlotDev& s = S[blockIdx.y];
+    if (!inner_active(s)) return;
+    double* w = s.V + (size_t)(s.j + 1) * s.n;
+    const double f = 1.0 / s.scal[2];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < s.n; t += (int64_t)gridDim.x * blockDim.x)
+        w[t] *= f;
+}
+
+// advance (one thread per slot): next Arnoldi index, or end of cycle -> update state
+__global__ void k_advance(SlotDev* S, int cap) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (!inner_active(s)) return;
+    if (s.cycle_end) {
+        s.kdone = s.j + 1;
+        s.stat.state = kSlotUpdate;
+    } else {
+        s.j += 1;
+    }
+}
+
+// back substitution R y = s (one thread per slot in UPDATE)
+__global__ void k_upper_solve(SlotDev* S, int cap) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (!update_active(s)) return;
+    const int k = s.kdone, ldh = s.m + 1;
+    for (int i = k - 1; i >= 0; --i) {
+        double v = s.sv[i];
+        for (int l = i + 1; l < k; ++l) v -= s.H[(size_t)l * ldh + i] * s.y[l];
+        s.y[i] = v / s.H[(size_t)i * ldh + i];
+    }
+}
+
+// after the residual: converged, out of budget, or the next cycle from r
+__global__ void k_decide(SlotDev* S, int cap) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (!update_active(s)) return;
+    s.stat.matvecs_fp64++;
+    s.stat.refinements++;
+    const double rn = sqrt(s.scal[1]);
+    s.stat.residual = (s.gnorm > 0.0) ? rn / s.gnorm : 0.0;
+    if (!isfinite(rn)) {
+        s.stat.numeric_error = 1;
+        s.stat.state = kSlotDone;
+        return;
+    }
+    const bool conv = rn <= s.tol_out * s.gnorm;
+    const bool out = s.budget <= 0 || (s.refine && s.stat.refinements >= s.max_refine);
+    if (conv || out) {
+        s.stat.converged = conv ? 1 : 0;
+        s.stat.state = kSlotDone;
+        return;
+    }
+    s.beta = rn;
+    s.tol_cycle = s.refine ? s.inner_tol * rn : s.tol_out * s.gnorm;
+    s.stat.state = kSlotStart;
+}
+
+// V[0] = r / beta for slots starting a cycle
+__global__ void k_start_vec(SlotDev* S) {
+    const SlotDev& s = S[blockIdx.y];
+    if (s.stat.state != kSlotStart) return;
+    const double f = 1.0 / s.beta;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < s.n; t += (int64_t)gridDim.x * blockDim.x)
+        s.V[t] = s.r[t] * f;
+}
+
+__global__ void k_start_scalars(SlotDev* S, int cap) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (s.stat.state != kSlotStart) return;
+    for (int i = 0; i <= s.m; ++i) s.sv[i] = 0.0;
+    s.sv[0] = s.beta;
+    s.j = 0;
+    s.stat.state = kSlotInner;
+}
+
+__global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < cap) out[q] = S[q].stat;
+}
+
+template <typename Policy, int R>
+int launch_persistent(Engine* e, int pol, int half, int prec) {
+    const size_t smem = pair_smem_bytes<Policy>();
+    k_pairs<Policy, R><<<e->grid[pol], kThreads, smem, e->stream>>>(
+        e->slots.as<SlotDev>(), e->items[pol].as<int4>(), e->n_items.as<int>() + pol,
+        e->counters.as<int>() + 2 * pol + half, half, prec, e->exp_tab, e->err.as<int>());
+    CTR_LAUNCHED();
+    return CTR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+static int policy_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
+
+Engine::~Engine() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (stream) {
+        cudaStreamSynchronize(stream);
+        cudaStreamDestroy(stream);
+    }
+}
+
+int engine_create(int device, int cap, Engine** out) {
+    Engine* e = new Engine();
+    e->device = device;
+    e->cap = cap;
+    if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete e;
+        return fail(CTR_ERR_CUDA, "stream create");
+    }
+    cudaStream_t stream = e->stream;
+    e->host.assign(cap, SlotDev{});
+    e->owner.assign(cap, nullptr);
+    auto bad = [&](int st) {
+        delete e;
+        return st;
+    };
+    int st;
+    if ((st = e->slots.alloc(sizeof(SlotDev) * cap)) < 0) return bad(st);
+    if ((st = e->stats.alloc(sizeof(SlotStat) * cap)) < 0) return bad(st);
+    if ((st = e->n_items.alloc(sizeof(int) * 4)) < 0) return bad(st);
+    if ((st = e->counters.alloc(sizeof(int) * 8)) < 0) return bad(st);
+    if ((st = e->err.alloc(sizeof(int))) < 0) return bad(st);
+    if (cudaMemsetAsync(e->err.p, 0, sizeof(int), stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "memset"));
+    if (cudaMemsetAsync(e->n_items.p, 0, sizeof(int) * 4, stream) != cudaSuccess)
+        return bad(fail(CTR_ERR_CUDA, "memset"));
+    for (int q = 0; q < cap; ++q) e->host[q].stat.state = kSlotEmpty;
+    if (cudaMemcpyAsync(e->slots.p, e->host.data(), sizeof(SlotDev) * cap, cudaMemcpyHostToDevice, stream) !=
+        cudaSuccess)
+        return bad(fail(CTR_ERR_CUDA, "slot upload"));
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bad(fail(CTR_ERR_CUDA, "attribute"));
+    int g32 = 0, gdf = 0;
+    if ((st = resident_slots_fp32(2, sms, &g32)) < 0) return bad(st);
+    if ((st = resident_slots_df64(sms, &gdf)) < 0) return bad(st);
+    e->grid[0] = g32;
+    e->grid[1] = gdf;
+    e->grid[2] = gdf;   // FP64 policy: same launch shape as the float-float one
+    for (int p = 0; p < 3; ++p) e->item_cap[p] = 0;
+    if ((st = exp_table(device, &e->exp_tab)) < 0) return bad(st);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "sync"));
+    *out = e;
+    return CTR_OK;
+}
+
+// Rebuild the three item lists (all occupied slots; each item is filtered by state at run time),
+// sorted by decreasing cost for the atomic-counter scheduler.
+static int rebuild_items(Engine* e) {
+    for (int p = 0; p < 3; ++p) {
+        struct It {
+            int4 v;
+            double cost;
+        };
+        std::vector<It> list;
+        for (int q = 0; q < e->cap; ++q) {
+            if (!e->owner[q]) continue;
+            const SlotDev& s = e->host[q];
+            const bool uses = (policy_index(s.inner_prec) == p) || (policy_index(s.res_prec) == p);
+            if (!uses) continue;
+            const int tb = (p == 0) ? s.tb32 : (p == 1 ? s.tbdf : s.tb64);
+            const int sp = (p == 0) ? s.sp32 : (p == 1 ? s.spdf : s.sp64);
+            const int per = (p == 0) ? s.per32 : (p == 1 ? s.perdf : s.per64);
+            for (int b = 0; b < tb; ++b)
+                for (int k = 0; k < sp; ++k) {
+                    const double src = std::min<double>(per, s.M - (double)k * per);
+                    list.push_back(It{make_int4(q, b, k, 0), src});
+                }
+        }
+        std::stable_sort(list.begin(), list.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+        std::vector<int4> v(list.size());
+        for (size_t i = 0; i < list.size(); ++i) v[i] = list[i].v;
+        if ((int64_t)v.size() > e->item_cap[p]) {
+            const int64_t capn = std::max<int64_t>(1024, (int64_t)v.size() * 2);
+            CTR_TRY(e->items[p].alloc(sizeof(int4) * capn));
+            e->item_cap[p] = capn;
+            e->graph_dirty = true;   // the item buffer moved
+        }
+        if (!v.empty())
+            CTR_CUDA_TRY(cudaMemcpyAsync(e->items[p].p, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice,
+                                         e->stream));
+        const int cnt = (int)v.size();
+        CTR_CUDA_TRY(cudaMemcpyAsync(e->n_items.as<int>() + p, &cnt, sizeof(int), cudaMemcpyHostToDevice, e->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    }
+    return CTR_OK;
+}
+
+// The kernels of one engine step, in stream order (captured into the graph).
+static int enqueue_step(Engine* e) {
+    cudaStream_t st = e->stream;
+    SlotDev* S = e->slots.as<SlotDev>();
+    const int cap = e->cap;
+    const int mx = e->max_nblk;
+    const dim3 vec(e->vec_blocks, cap);
+    const unsigned one = grid_for(cap, 128);
+    // ---- inner half: one Arnoldi iteration
+    k_prep_inner<<<vec, kVecThreads, 0, st>>>(S);
+    CTR_LAUNCHED();
+    CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, st));
+    CTR_TRY((launch_persistent<Fp32Policy, 2>(e, 0, 0, CTR_FP32_REFINE)));
+    CTR_TRY((launch_persistent<Df64Policy, 1>(e, 1, 0, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, 1>(e, 2, 0, CTR_FP64)));
+    k_finish<<<vec, kVecThreads, 0, st>>>(S, 0);
+    CTR_LAUNCHED();
+    for (int pass = 0; pass < 2; ++pass) {
+        k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, pass);
+        CTR_LAUNCHED();
+        k_dots_final<<<dim3(e->max_m + 1, cap), kVecThreads, 0, st>>>(S, pass);
+        CTR_LAUNCHED();
+        k_sub<<<vec, kVecThreads, 0, st>>>(S, pass);
+        CTR_LAUNCHED();
+    }
+    k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, 2);
+    CTR_LAUNCHED();
+    k_dots_final<<<dim3(1, cap), kVecThreads, 0, st>>>(S, 2);
+    CTR_LAUNCHED();
+    k_givens<<<one, 128, 0, st>>>(S, cap);
+    CTR_LAUNCHED();
+    k_scale_next<<<vec, kVecThreads, 0, st>>>(S);
+    CTR_LAUNCHED();
+    k_advance<<<one, 128, 0, st>>>(S, cap);
+    CTR_LAUNCHED();
+    // ---- update half: x, true residual, next cycle
+    k_upper_solve<<<one, 128, 0, st>>>(S, cap);
+    CTR_LAUNCHED();
+    k_update_x<<<vec, kVecThreads, 0, st>>>(S);
+    CTR_LAUNCHED();
+    CTR_TRY((launch_persistent<Fp32Policy, 2>(e, 0, 1, CTR_FP32_REFINE)));
+    CTR_TRY((launch_persistent<Df64Policy, 1>(e, 1, 1, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, 1>(e, 2, 1, CTR_FP64)));
+    k_finish<<<vec, kVecThreads, 0, st>>>(S, 1);
+    CTR_LAUNCHED();
+    k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, 3);
+    CTR_LAUNCHED();
+    k_dots_final<<<dim3(1, cap), kVecThreads, 0, st>>>(S, 3);
+    CTR_LAUNCHED();
+    k_decide<<<one, 128, 0, st>>>(S, cap);
+    CTR_LAUNCHED();
+    k_start_vec<<<vec, kVecThreads, 0, st>>>(S);
+    CTR_LAUNCHED();
+    k_start_scalars<<<one, 128, 0, st>>>(S, cap);
+    CTR_LAUNCHED();
+    k_stats<<<one, 128, 0, st>>>(S, cap, e->stats.as<SlotStat>());
+    CTR_LAUNCHED();
+    return CTR_OK;
+}
+
+static int ensure_graph(Engine* e) {
+    if (e->graph_exec && !e->graph_dirty) return CTR_OK;
+    if (e->graph_exec) {
+        cudaGraphExecDestroy(e->graph_exec);
+        e->graph_exec = nullptr;
+    }
+    if (!e->use_graph) return CTR_OK;
+    cudaGraph_t g = nullptr;
+    const int64_t before = ctr_kernel_launches();
+    CTR_CUDA_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    const int st = enqueue_step(e);
+    e->kernels_per_step = ctr_kernel_launches() - before;
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (st < 0) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return fail(CTR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&e->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(CTR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    e->graph_dirty = false;
+    return CTR_OK;
+}
+
+int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
+    int q = -1;
+    for (int i = 0; i < e->cap; ++i)
+        if (!e->owner[i]) {
+            q = i;
+            break;
+        }
+    if (q < 0) return fail(CTR_ERR_CAPACITY, "no free engine slot");
+    CTR_TRY(engine_prepare_handle(s));
+    SlotDev d{};
+    d.M = (int)s->M;
+    d.n = 2 * s->M;
+    d.E = (int)s->E;
+    d.m = s->kr.m;
+    d.nblk = s->kr.nblk;
+    d.W = s->na.W;
+    d.cptr = s->corr_ptr.as<int32_t>();
+    d.cnode = s->corr_node.as<int32_t>();
+    d.cw = s->corr_w.as<double>();
+    d.excl = s->excl.as<int32_t>();
+    d.src32 = s->src32.as<float4>();
+    d.src64 = s->src64.as<double4>();
+    d.srcdf = s->srcdf.as<float4>();
+    d.part = s->partial.as<double>();
+    d.g = s->rhs.as<double>();
+    d.lam1 = 0.5 * (1.0 + s->eps_out / s->eps_in);
+    d.lam2 = 0.5 * (1.0 + s->eps_in / s->eps_out);
+    d.il1 = 2.0 / (1.0 + s->eps_out / s->eps_in);
+    d.il2 = 2.0 / (1.0 + s->eps_in / s->eps_out);
+    d.h2 = s->h * s->h;
+    d.h3 = s->h * s->h * s->h;
+    d.scale = s->h * s->h * s->h / (4.0 * kPi);
+    d.refine = (s->opt.precision == CTR_FP32_REFINE) ? 1 : 0;
+    d.inner_prec = s->opt.precision;
+    d.res_prec = d.refine ? s->opt.residual : s->opt.precision;
+    CTR_TRY(pair_consts(s, true, &d.kc));
+    d.tb32 = s->plan32.target_blocks;
+    d.sp32 = s->plan32.splits;
+    d.per32 = s->plan32.src_per_split;
+    d.tbdf = s->plandf.target_blocks;
+    d.spdf = s->plandf.splits;
+    d.perdf = s->plandf.src_per_split;
+    d.tb64 = s->plan64.target_blocks;
+    d.sp64 = s->plan64.splits;
+    d.per64 = s->plan64.src_per_split;
+    double* b = s->vecs.as<double>();
+    const int64_t n = d.n;
+    d.x = b;
+    d.r = b + n;
+    d.z = b + 2 * n;
+    d.V = s->kr.V.as<double>();
+    d.H = s->kr.H.as<double>();
+    d.cs = s->kr.cs.as<double>();
+    d.sn = s->kr.sn.as<double>();
+    d.sv = s->kr.s.as<double>();
+    d.y = s->kr.y.as<double>();
+    d.cgs = s->kr.y.as<double>() + (d.m + 1);
+    d.cgs2 = s->kr.y.as<double>() + 2 * (d.m + 1);
+    d.dpart = s->kr.part.as<double>();
+    d.scal = s->kr.scal.as<double>();
+    d.tol_out = s->opt.tol;
+    d.inner_tol = s->opt.inner_tol;
+    d.max_refine = s->opt.max_refine;
+    d.budget = s->opt.max_iter;
+    // initial residual r = g (x = 0) and its norm
+    CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));   // the handle's setup work is complete
+    CTR_CUDA_TRY(cudaMemsetAsync(d.x, 0, sizeof(double) * n, e->stream));
+    CTR_CUDA_TRY(cudaMemcpyAsync(d.r, d.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, e->stream));
+    double gn2 = 0.0;
+    CTR_TRY(device_dot(s, d.g, d.g, n, &gn2));
+    d.gnorm = std::sqrt(gn2);
+    d.beta = d.gnorm;
+    d.tol_cycle = d.refine ? d.inner_tol * d.gnorm : d.tol_out * d.gnorm;
+    d.stat = SlotStat{};
+    if (d.gnorm == 0.0) {
+        d.stat.state = kSlotDone;
+        d.stat.converged = 1;
+    } else {
+        d.stat.state = kSlotStart;
+    }
+    e->host[q] = d;
+    e->owner[q] = s;
+    CTR_CUDA_TRY(cudaMemcpyAsync(e->slots.as<SlotDev>() + q, &d, sizeof(SlotDev), cudaMemcpyHostToDevice, e->stream));
+    CTR_CUDA_TRY(cudaMemcpyAsync(e->stats.as<SlotStat>() + q, &d.stat, sizeof(SlotStat), cudaMemcpyHostToDevice,
+                                 e->stream));
+    if (d.stat.state == kSlotStart) {
+        k_start_vec<<<dim3(e->vec_blocks, e->cap), kVecThreads, 0, e->stream>>>(e->slots.as<SlotDev>());
+        CTR_LAUNCHED();
+        k_start_scalars<<<grid_for(e->cap, 128), 128, 0, e->stream>>>(e->slots.as<SlotDev>(), e->cap);
+        CTR_LAUNCHED();
+    }
+    if (d.nblk > e->max_nblk) {   // launch shapes of the captured step change
+        e->max_nblk = d.nblk;
+        e->graph_dirty = true;
+    }
+    if (d.m > e->max_m) {
+        e->max_m = d.m;
+        e->graph_dirty = true;
+    }
+    const int vb = (int)std::min<int64_t>(grid_for(s->M, kVecThreads), 1024);
+    if (vb > e->vec_blocks) {
+        e->vec_blocks = vb;
+        e->graph_dirty = true;
+    }
+    CTR_TRY(rebuild_items(e));
+    *slot_out = q;
+    return CTR_OK;
+}
+
+int engine_retire(Engine* e, int q, ctr_solve_info* info) {
+    if (q < 0 || q >= e->cap || !e->owner[q]) return fail(CTR_ERR_INVALID, "bad slot");
+    SlotStat st;
+    CTR_CUDA_TRY(cudaMemcpyAsync(&st, e->stats.as<SlotStat>() + q, sizeof(SlotStat), cudaMemcpyDeviceToHost, e->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (info) {
+        info->iterations = st.iterations;
+        info->refinements = st.refinements;
+        info->matvecs_fp32 = st.matvecs_fp32;
+        info->matvecs_fp64 = st.matvecs_fp64;
+        info->residual = st.residual;
+        info->converged = st.converged;
+    }
+    SlotDev empty{};
+    empty.stat.state = kSlotEmpty;
+    e->host[q] = empty;
+    e->owner[q] = nullptr;
+    CTR_CUDA_TRY(cudaMemcpyAsync(e->slots.as<SlotDev>() + q, &empty, sizeof(SlotDev), cudaMemcpyHostToDevice, e->stream));
+    CTR_TRY(rebuild_items(e));
+    return st.numeric_error ? fail(CTR_ERR_NUMERIC, "non-finite residual") : CTR_OK;
+}
+
+int engine_step(Engine* e, std::vector<SlotStat>* stats) {
+    CTR_TRY(ensure_graph(e));
+    if (e->graph_exec) {
+        CTR_CUDA_TRY(cudaGraphLaunch(e->graph_exec, e->stream));
+        count_launches(e->kernels_per_step);   // kernels run by the replay
+    } else {
+        CTR_TRY(enqueue_step(e));
+    }
+    stats->resize(e->cap);
+    CTR_CUDA_TRY(cudaMemcpyAsync(stats->data(), e->stats.p, sizeof(SlotStat) * e->cap, cudaMemcpyDeviceToHost, e->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    int herr = 0;
+    CTR_CUDA_TRY(cudaMemcpyAsync(&herr, e->err.p, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (herr) return fail(CTR_ERR_DEVICE_WAIT, "engine: a bounded device wait expired");
+    e->steps++;
+    return CTR_OK;
+}
+
+// The handle's solver workspace, sized for the engine (Krylov basis, vectors, split partials).
+int engine_prepare_handle(ctr_ibim* s) {
+    CTR_TRY(ensure_krylov_public(s));
+    return CTR_OK;
+}
+
+// Solve every handle to completion in one engine (all slots admitted at once).
+int engine_solve_all(ctr_ibim* const* hs, int64_t n, int use_graph, std::vector<ctr_solve_info>* infos,
+                     int64_t* steps) {
+    if (n <= 0) return CTR_OK;
+    Engine* e = nullptr;
+    CTR_TRY(engine_create(hs[0]->device, (int)n, &e));
+    std::unique_ptr<Engine> guard(e);
+    e->use_graph = use_graph != 0;
+    e->vec_blocks = 1;
+    for (int64_t i = 0; i < n; ++i)
+        e->vec_blocks = std::max<int>(e->vec_blocks, (int)std::min<int64_t>(grid_for(hs[i]->M, kVecThreads), 1024));
+    std::vector<int> slot(n);
+    for (int64_t i = 0; i < n; ++i) CTR_TRY(engine_admit(e, hs[i], &slot[i]));
+    infos->assign(n, ctr_solve_info{});
+    std::vector<int> state(n);
+    for (int64_t i = 0; i < n; ++i) state[i] = e->host[slot[i]].stat.state == kSlotDone ? kSlotDone : kSlotInner;
+    std::vector<char> done(n, 0);
+    std::vector<SlotStat> st;
+    int first_error = CTR_OK;
+    for (;;) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (!done[i] && state[i] == kSlotDone) {
+                const int r = engine_retire(e, slot[i], &(*infos)[i]);
+                if (r < 0 && first_error == CTR_OK) first_error = r;
+                done[i] = 1;
+            }
+        }
+        bool left = false;
+        for (int64_t i = 0; i < n; ++i) left |= !done[i];
+        if (!left) break;
+        CTR_TRY(engine_step(e, &st));
+        for (int64_t i = 0; i < n; ++i)
+            if (!done[i]) state[i] = st[slot[i]].state;
+    }
+    if (steps) *steps = e->steps;
+    return first_error;
+}
+
+}  // namespace ctr

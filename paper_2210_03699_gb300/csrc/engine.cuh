@@ -1,0 +1,81 @@
+// Multi-slot solver engine (engine.cu): device-side state of every slot and the host object.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+#include "pairkern.cuh"
+
+namespace ctr {
+
+enum : int { kSlotEmpty = 0, kSlotInner = 1, kSlotUpdate = 2, kSlotDone = 3, kSlotStart = 4 };
+
+// Per-slot counters and state, read back by the host after every step.
+struct SlotStat {
+    int state;
+    int converged;
+    int numeric_error;
+    int pad;
+    int64_t iterations, refinements, matvecs_fp32, matvecs_fp64;
+    double residual;
+};
+
+// Everything the step kernels need about one slot (device copy; the host mirror is Engine::host).
+struct SlotDev {
+    SlotStat stat;
+    int j, m, kdone, cycle_end;
+    int M, E, nblk;
+    int64_t n;
+    int refine, inner_prec, res_prec, max_refine;
+    int64_t budget;
+    // system (owned by the handle)
+    const double* W;
+    const int32_t* cptr;
+    const int32_t* cnode;
+    const double* cw;
+    const int32_t* excl;
+    float4* src32;
+    double4* src64;
+    float4* srcdf;
+    double* part;
+    const double* g;
+    double lam1, lam2, il1, il2, h2, h3, scale;
+    pk::PairConsts kc;
+    int tb32, sp32, per32, tbdf, spdf, perdf, tb64, sp64, per64;
+    // solver workspace (owned by the handle)
+    double *x, *r, *z, *V, *H, *cs, *sn, *sv, *y, *cgs, *cgs2, *dpart, *scal;
+    double gnorm, beta, tol_out, inner_tol, tol_cycle;
+};
+
+struct Engine {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int cap = 0;
+    bool use_graph = true;
+    bool graph_dirty = true;
+    int vec_blocks = 1;
+    int max_nblk = 1;
+    int max_m = 1;
+    int grid[3] = {0, 0, 0};
+    int64_t item_cap[3] = {0, 0, 0};
+    int64_t steps = 0;
+    int64_t kernels_per_step = 0;
+    const float2* exp_tab = nullptr;
+    std::vector<SlotDev> host;
+    std::vector<ctr_ibim*> owner;
+    DevBuf slots, stats, items[3], n_items, counters, err;
+    cudaGraphExec_t graph_exec = nullptr;
+    ~Engine();
+};
+
+int engine_create(int device, int cap, Engine** out);
+int engine_admit(Engine* e, ctr_ibim* s, int* slot);
+int engine_retire(Engine* e, int slot, ctr_solve_info* info);
+int engine_step(Engine* e, std::vector<SlotStat>* stats);
+int engine_prepare_handle(ctr_ibim* s);
+int engine_solve_all(ctr_ibim* const* hs, int64_t n, int use_graph, std::vector<ctr_solve_info>* infos,
+                     int64_t* steps);
+int ensure_krylov_public(ctr_ibim* s);
+
+}  // namespace ctr

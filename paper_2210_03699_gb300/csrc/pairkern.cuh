@@ -1,0 +1,468 @@
+// Dense pair-sum core shared by the single-system operator (pairsum.cu) and
+// the multi-slot engine (engine.cu): kernel constants, bulk-copy/mbarrier
+// helpers, float-float arithmetic, the three pair policies and one work item
+// of the tiled pair sum.  Internal to the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace ctr {
+namespace pk {
+
+constexpr int kThreads = 256;
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kExpHi = 64;      // e^{-k}, k = 0..63
+constexpr int kExpLo = 1024;    // e^{-k/1024}, k = 0..1023
+
+struct PairConsts {
+    float c1f, c2f, kappaf, kl2f;    // eps_E/eps_I, eps_I/eps_E, kappa, -kappa log2(e)
+    double c1, c2, kappa;
+    float2 c1d, c2d, kappad;         // float-float copies
+    const float2* exp_tab;           // [kExpHi + kExpLo] float-float, global
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false after kWaitLimit polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_sfu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------------ float-float arithmetic
+// A value is hi + lo with |lo| <= ulp(hi)/2.  Error-free transformations use
+// explicitly rounded intrinsics so that nothing is fused or reassociated.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2(float2 v) { return F2{v.x, v.y}; }
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return F2{s, e};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {   // |a| >= |b|, or a == 0
+    const float s = __fadd_rn(a, b);
+    return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return F2{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ F2 neg(F2 a) { return F2{-a.hi, -a.lo}; }
+__device__ __forceinline__ F2 add(F2 a, F2 b) {
+    const F2 s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ F2 sub(F2 a, F2 b) { return add(a, neg(b)); }
+__device__ __forceinline__ F2 add_f(F2 a, float b) {
+    const F2 s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ F2 mul(F2 a, F2 b) {
+    const F2 p = two_prod(a.hi, b.hi);
+    return fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+// a0 b0 + a1 b1 + a2 b2
+__device__ __forceinline__ F2 dot3(F2 a0, F2 a1, F2 a2, F2 b0, F2 b1, F2 b2) {
+    const F2 p0 = two_prod(a0.hi, b0.hi), p1 = two_prod(a1.hi, b1.hi), p2 = two_prod(a2.hi, b2.hi);
+    const F2 s = two_sum(p0.hi, p1.hi);
+    const F2 t = two_sum(s.hi, p2.hi);
+    float e = __fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, __fadd_rn(s.lo, t.lo)));
+    e = __fmaf_rn(a0.hi, b0.lo, __fmaf_rn(a0.lo, b0.hi, e));
+    e = __fmaf_rn(a1.hi, b1.lo, __fmaf_rn(a1.lo, b1.hi, e));
+    e = __fmaf_rn(a2.hi, b2.lo, __fmaf_rn(a2.lo, b2.hi, e));
+    return fast_two_sum(t.hi, e);
+}
+// 1/sqrt(x): SFU seed y0 (rel. err < 2^-22), one Newton step y0 + y0 (1 - x y0^2)/2 in float-float
+__device__ __forceinline__ F2 rsqrt_ff(F2 x) {
+    const float y0 = rsqrt_sfu(x.hi);
+    const F2 t = mul(x, two_prod(y0, y0));
+    const float e = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    return fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), e));
+}
+// e^{-x}, x >= 0: x = k/1024 + f (k nearest), e^{-x} = e^{-(k>>10)} e^{-(k&1023)/1024} e^{-f},
+// e^{-f} = 1 - f + f^2 (1/2 - f/6 + f^2/24) for |f| <= 1/2048 (truncation < 3e-19)
+__device__ __forceinline__ F2 exp_neg_ff(F2 x, const float2* tab) {
+    float xh = x.hi, xl = x.lo;
+    if (xh > 63.9f) {
+        xh = 63.9f;
+        xl = 0.f;
+    }
+    const float t = __fmaf_rn(xh, 1024.f, 12582912.f);   // 1.5 * 2^23: round(x * 1024) in the mantissa
+    const int k = min(max(__float_as_int(t) - 0x4B400000, 0), kExpHi * kExpLo - 1);   // in range for any input
+    const float kf = __fsub_rn(t, 12582912.f);
+    const F2 f = two_sum(__fmaf_rn(kf, -1.0f / 1024.f, xh), xl);   // the first term is exact
+    const float fh = f.hi;
+    const float poly = __fmaf_rn(__fmaf_rn(fh, 1.0f / 24.0f, -1.0f / 6.0f), fh, 0.5f);
+    const float q = __fmul_rn(__fmul_rn(fh, fh), poly);
+    const F2 omf = fast_two_sum(1.0f, -fh);
+    const F2 ef = fast_two_sum(omf.hi, __fadd_rn(__fsub_rn(omf.lo, f.lo), q));
+    return mul(mul(f2(tab[k >> 10]), f2(tab[kExpHi + (k & 1023)])), ef);
+}
+
+// ------------------------------------------------------------------ pair policies
+// Fp32: 4 pi K terms, d = x - y, s = 1/r^3, E = e^{-kappa r}, E1 = E (1 + kappa r):
+//   4pi K11 = (d.n_y) s (1 - (eps_E/eps_I) E1)
+//   4pi K12 = (1 - E)/r
+//   4pi K22 = -(d.n_x) s (1 - (eps_I/eps_E) E1)
+//   4pi K21 = s [ (1 - E1) n_x.n_y - (3 - E (3 + 3 kappa r + kappa^2 r^2)) (d.n_x)(d.n_y)/r^2 ]
+// and acc1 += a K11 - b K12, acc2 += a K21 - b K22.
+struct Fp32Policy {
+    using Src = float4;
+    static constexpr int kVec = 2;    // Src per node
+    static constexpr int kTile = 256; // nodes per tile (8 KB)
+    static constexpr bool kTables = false;
+    struct Tgt {
+        float px, py, pz, qx, qy, qz;
+    };
+    struct Acc {
+        float a1, a2;
+    };
+    __device__ static Tgt load(const Src* src, int t) {
+        const float4 a = src[2 * t], b = src[2 * t + 1];
+        return Tgt{a.x, a.y, a.z, b.x, b.y, b.z};
+    }
+    __device__ static void zero(Acc& c) { c.a1 = c.a2 = 0.f; }
+    __device__ static void fold(const Acc& c, double& s1, double& s2) {
+        s1 += (double)c.a1;
+        s2 += (double)c.a2;
+    }
+    template <bool kMask>
+    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, bool ex) {
+        float4 pa = S[0], nb = S[1];
+        if (kMask && ex) {   // excluded correction pair: a zero-weight source at distance 1
+            pa = make_float4(T.px + 1.f, T.py, T.pz, 0.f);
+            nb.w = 0.f;
+        }
+        const float dx = T.px - pa.x, dy = T.py - pa.y, dz = T.pz - pa.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float rinv = rsqrt_sfu(r2);
+        const float r = r2 * rinv;
+        const float E = ex2_sfu(k.kl2f * r);
+        const float kr = k.kappaf * r;
+        const float E1 = fmaf(E, kr, E);
+        const float dny = fmaf(dz, nb.z, fmaf(dy, nb.y, dx * nb.x));
+        const float dnx = fmaf(dz, T.qz, fmaf(dy, T.qy, dx * T.qx));
+        const float nn = fmaf(T.qz, nb.z, fmaf(T.qy, nb.y, T.qx * nb.x));
+        const float rinv2 = rinv * rinv;
+        const float s = rinv2 * rinv;
+        const float as = pa.w * s, bs = nb.w * s;
+        const float t1 = fmaf(-k.c1f, E1, 1.f);
+        acc.a1 = fmaf(as, dny * t1, acc.a1);
+        const float om = fmaf(-rinv, E, rinv);
+        acc.a1 = fmaf(-nb.w, om, acc.a1);
+        const float t2 = fmaf(-k.c2f, E1, 1.f);
+        acc.a2 = fmaf(bs, dnx * t2, acc.a2);
+        const float u = 1.f - E1;
+        const float q = fmaf(kr, kr + 3.f, 3.f);
+        const float t3 = fmaf(-E, q, 3.f);
+        const float B = t3 * dnx * dny * rinv2;
+        acc.a2 = fmaf(as, fmaf(u, nn, -B), acc.a2);
+    }
+};
+
+struct Fp64Policy {
+    using Src = double4;
+    static constexpr int kVec = 2;
+    static constexpr int kTile = 128;   // 8 KB
+    static constexpr bool kTables = false;
+    struct Tgt {
+        double px, py, pz, qx, qy, qz;
+    };
+    struct Acc {
+        double a1, a2;
+    };
+    __device__ static Tgt load(const Src* src, int t) {
+        const double4 a = src[2 * t], b = src[2 * t + 1];
+        return Tgt{a.x, a.y, a.z, b.x, b.y, b.z};
+    }
+    __device__ static void zero(Acc& c) { c.a1 = c.a2 = 0.0; }
+    __device__ static void fold(const Acc& c, double& s1, double& s2) {
+        s1 += c.a1;
+        s2 += c.a2;
+    }
+    template <bool kMask>
+    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, bool ex) {
+        double4 pa = S[0], nb = S[1];
+        if (kMask && ex) {
+            pa = make_double4(T.px + 1.0, T.py, T.pz, 0.0);
+            nb.w = 0.0;
+        }
+        const double dx = T.px - pa.x, dy = T.py - pa.y, dz = T.pz - pa.z;
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double rinv = rsqrt(r2);
+        const double r = r2 * rinv;
+        const double E = exp(-k.kappa * r);
+        const double kr = k.kappa * r;
+        const double E1 = fma(E, kr, E);
+        const double dny = fma(dz, nb.z, fma(dy, nb.y, dx * nb.x));
+        const double dnx = fma(dz, T.qz, fma(dy, T.qy, dx * T.qx));
+        const double nn = fma(T.qz, nb.z, fma(T.qy, nb.y, T.qx * nb.x));
+        const double rinv2 = rinv * rinv;
+        const double s = rinv2 * rinv;
+        const double as = pa.w * s, bs = nb.w * s;
+        const double t1 = fma(-k.c1, E1, 1.0);
+        acc.a1 = fma(as, dny * t1, acc.a1);
+        const double om = fma(-rinv, E, rinv);
+        acc.a1 = fma(-nb.w, om, acc.a1);
+        const double t2 = fma(-k.c2, E1, 1.0);
+        acc.a2 = fma(bs, dnx * t2, acc.a2);
+        const double u = 1.0 - E1;
+        const double q = fma(kr, kr + 3.0, 3.0);
+        const double t3 = fma(-E, q, 3.0);
+        const double B = t3 * dnx * dny * rinv2;
+        acc.a2 = fma(as, fma(u, nn, -B), acc.a2);
+    }
+};
+
+// Source node = 4 float4: {P.hi, a.hi} {P.lo, a.lo} {n.hi, b.hi} {n.lo, b.lo}.
+struct Df64Policy {
+    using Src = float4;
+    static constexpr int kVec = 4;
+    static constexpr int kTile = 128;   // 8 KB
+    static constexpr bool kTables = true;
+    struct Tgt {
+        F2 px, py, pz, qx, qy, qz;
+    };
+    struct Acc {
+        F2 a1, a2;
+    };
+    __device__ static Tgt load(const Src* src, int t) {
+        const float4 a = src[4 * t], b = src[4 * t + 1], c = src[4 * t + 2], d = src[4 * t + 3];
+        return Tgt{F2{a.x, b.x}, F2{a.y, b.y}, F2{a.z, b.z}, F2{c.x, d.x}, F2{c.y, d.y}, F2{c.z, d.z}};
+    }
+    __device__ static void zero(Acc& c) { c.a1 = c.a2 = F2{0.f, 0.f}; }
+    __device__ static void fold(const Acc& c, double& s1, double& s2) {
+        s1 += (double)c.a1.hi + (double)c.a1.lo;
+        s2 += (double)c.a2.hi + (double)c.a2.lo;
+    }
+    template <bool kMask>
+    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2* tab, Acc& acc,
+                                bool ex) {
+        const float4 s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3];
+        F2 Px{s0.x, s1.x}, Py{s0.y, s1.y}, Pz{s0.z, s1.z}, A{s0.w, s1.w};
+        const F2 Nx{s2.x, s3.x}, Ny{s2.y, s3.y}, Nz{s2.z, s3.z};
+        F2 Bw{s2.w, s3.w};
+        if (kMask && ex) {
+            Px = F2{T.px.hi + 1.f, T.px.lo};
+            Py = T.py;
+            Pz = T.pz;
+            A = Bw = F2{0.f, 0.f};
+        }
+        const F2 dx = sub(T.px, Px), dy = sub(T.py, Py), dz = sub(T.pz, Pz);
+        const F2 r2 = dot3(dx, dy, dz, dx, dy, dz);
+        const F2 rinv = rsqrt_ff(r2);
+        const F2 r = mul(r2, rinv);
+        const F2 kr = mul(f2(k.kappad), r);
+        const F2 E = exp_neg_ff(kr, tab);
+        const F2 E1 = mul(E, add_f(kr, 1.f));
+        const F2 dny = dot3(dx, dy, dz, Nx, Ny, Nz);
+        const F2 dnx = dot3(dx, dy, dz, T.qx, T.qy, T.qz);
+        const F2 nn = dot3(T.qx, T.qy, T.qz, Nx, Ny, Nz);
+        const F2 rinv2 = mul(rinv, rinv);
+        const F2 s = mul(rinv2, rinv);
+        const F2 as = mul(A, s), bs = mul(Bw, s);
+        const F2 t1 = add_f(neg(mul(E1, f2(k.c1d))), 1.f);
+        acc.a1 = add(acc.a1, mul(as, mul(dny, t1)));
+        const F2 om = mul(rinv, add_f(neg(E), 1.f));
+        acc.a1 = sub(acc.a1, mul(Bw, om));
+        const F2 t2 = add_f(neg(mul(E1, f2(k.c2d))), 1.f);
+        acc.a2 = add(acc.a2, mul(bs, mul(dnx, t2)));
+        const F2 u = add_f(neg(E1), 1.f);
+        const F2 q = add_f(mul(kr, add_f(kr, 3.f)), 3.f);
+        const F2 t3 = add_f(neg(mul(E, q)), 3.f);
+        const F2 Bt = mul(mul(t3, mul(dnx, dny)), rinv2);
+        acc.a2 = add(acc.a2, mul(as, sub(mul(u, nn), Bt)));
+    }
+};
+
+// One work item of the dense pair sum: target block `tblock` (kThreads * R
+// targets) against sources [j_begin, j_end), partial sums written to
+// partial[(slot * 2 + c) * M + i].  Shared memory (ring, tables, barriers) is
+// set up by the caller; `gt` counts the tiles this block has consumed so far
+// (it fixes the mbarrier phase parity across items).  Returns false when a
+// bounded wait expired (the error word is set; the caller must return).
+template <typename Policy, int R>
+__device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict__ src, int M,
+                                          const int32_t* __restrict__ eptr, const int32_t* __restrict__ excl,
+                                          int tblock, int j_begin, int j_end, int slot,
+                                          double* __restrict__ partial, const PairConsts& kc,
+                                          int* __restrict__ err, typename Policy::Src* ring, const float2* tab,
+                                          uint64_t* bar, uint32_t& gt) {
+    using Src = typename Policy::Src;
+    constexpr int TILE = Policy::kTile;
+    constexpr int VEC = Policy::kVec;
+    const int tid = threadIdx.x;
+    const int ntiles = (j_end > j_begin) ? (j_end - j_begin + TILE - 1) / TILE : 0;
+
+    typename Policy::Tgt tg[R];
+    double s1[R], s2[R];
+    int ti[R], epos[R], eend[R], enext[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ti[r] = tblock * (kThreads * R) + r * kThreads + tid;
+        const int t = min(ti[r], M - 1);
+        tg[r] = Policy::load(src, t);
+        s1[r] = 0.0;
+        s2[r] = 0.0;
+        int e = eptr[t], ee = eptr[t + 1];
+        while (e < ee && excl[e] < j_begin) ++e;
+        epos[r] = e;
+        eend[r] = ee;
+        enext[r] = (e < ee) ? excl[e] : INT_MAX;
+    }
+    auto issue = [&](int k) {
+        const uint32_t g = gt + (uint32_t)k;
+        const int j0 = j_begin + k * TILE;
+        const int n = min(TILE, j_end - j0);
+        const uint32_t bytes = (uint32_t)(n * VEC * sizeof(Src));
+        Src* dst = ring + (g & 1) * TILE * VEC;
+        fence_proxy_async();
+        mbar_expect_tx(&bar[g & 1], bytes);
+        bulk_load(dst, src + (size_t)VEC * j0, bytes, &bar[g & 1]);
+    };
+    if (tid == 0 && ntiles > 0) issue(0);
+
+    for (int k = 0; k < ntiles; ++k) {
+        const uint32_t g = gt + (uint32_t)k;
+        if (tid == 0 && k + 1 < ntiles) issue(k + 1);
+        const bool ok = mbar_wait(&bar[g & 1], (g >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            // give up: flag it, let the copy that may still be in flight land, return
+            if (tid == 0) {
+                atomicOr(err, kErrWait);
+                if (k + 1 < ntiles) (void)mbar_wait(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
+            }
+            return false;
+        }
+        const Src* tile = ring + (g & 1) * TILE * VEC;
+        const int j0 = j_begin + k * TILE;
+        const int n = min(TILE, j_end - j0);
+        bool need = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) need |= (enext[r] < j0 + n);
+        typename Policy::Acc acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) Policy::zero(acc[r]);
+        if (!__any_sync(0xffffffffu, need)) {
+#pragma unroll 2
+            for (int q = 0; q < n; ++q) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    Policy::template pair<false>(tg[r], tile + q * VEC, kc, tab, acc[r], false);
+            }
+        } else {
+            for (int q = 0; q < n; ++q) {
+                const int j = j0 + q;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const bool ex = (j == enext[r]);
+                    if (ex) {
+                        ++epos[r];
+                        enext[r] = (epos[r] < eend[r]) ? excl[epos[r]] : INT_MAX;
+                    }
+                    Policy::template pair<true>(tg[r], tile + q * VEC, kc, tab, acc[r], ex);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) Policy::fold(acc[r], s1[r], s2[r]);
+        __syncthreads();   // the buffer of this tile is free for the tile after next
+    }
+    gt += (uint32_t)ntiles;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (ti[r] < M) {
+            partial[((size_t)slot * 2 + 0) * M + ti[r]] = s1[r];
+            partial[((size_t)slot * 2 + 1) * M + ti[r]] = s2[r];
+        }
+    }
+    return true;
+}
+
+// Shared-memory bytes of a pair block: the two-stage source ring and, for the
+// float-float policy, the exponential tables.
+template <typename Policy>
+constexpr size_t pair_smem_bytes() {
+    return 2 * Policy::kTile * Policy::kVec * sizeof(typename Policy::Src) +
+           (Policy::kTables ? (kExpHi + kExpLo) * sizeof(float2) : 0);
+}
+
+// Per-block setup shared by every pair kernel: exponential tables and the two mbarriers.
+template <typename Policy>
+__device__ __forceinline__ void pair_block_init(const PairConsts& kc, float2* tab, uint64_t* bar) {
+    if constexpr (Policy::kTables) {
+        for (int q = threadIdx.x; q < kExpHi + kExpLo; q += kThreads) tab[q] = kc.exp_tab[q];
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+inline float2 split_ff(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+}  // namespace pk
+
+// float-float table of e^{-k} (k < 64) and e^{-k/1024} (k < 1024) on a device
+int exp_table(int device, const float2** out);
+// Splits of the source range for equal-work items filling whole waves of `slots` resident blocks
+PairPlan make_plan(int64_t M, int R, int tile, int slots);
+// Resident blocks of the pair kernels on the whole device
+int resident_slots_fp32(int R, int sms, int* slots);
+int resident_slots_df64(int sms, int* slots);
+// Pair constants of a handle (kernel-ratio terms, kappa, tables when needed)
+int pair_consts(ctr_ibim* s, bool tables, pk::PairConsts* out);
+
+}  // namespace ctr

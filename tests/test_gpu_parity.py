@@ -281,3 +281,37 @@ def test_full_size_sampled_rows(ctr, oracle_tables, tile_targets):
     assert _rel(y32[sel], ref) < 2e-5
     assert np.all(np.isfinite(y32)) and np.all(np.isfinite(y64))
     G.close()
+
+
+# ---------------------------------------------------------------- batched engine (many systems, one engine)
+def test_batch_matches_alone_bitwise(ctr, oracle_tables):
+    """Each system's result is the same alone and in a mixed batch (sizes, methods, precisions)."""
+    probs = [
+        (syn.sphere_problem(h=0.25), ctr.Options(tube_halfwidth=0.5, precision=ctr.FP32_REFINE)),
+        (syn.ellipsoid_problem(h=0.2), ctr.Options(tube_halfwidth=0.4, precision=ctr.FP32_REFINE)),
+        (syn.molecule_problem(n_atoms=40, seed=3, h=0.5), ctr.Options(tube_halfwidth=1.0,
+                                                                      precision=ctr.FP32_REFINE)),
+        (syn.sphere_problem(h=0.25, R=1.5, half_box=2.5), ctr.Options(tube_halfwidth=0.5, precision=ctr.FP64)),
+        (syn.sphere_problem(h=0.25, kappa=1.0), ctr.Options(tube_halfwidth=0.5, precision=ctr.DF64,
+                                                            method=ctr.METHOD_KREG)),
+    ]
+    alone = []
+    for prob, opt in probs:
+        G = ctr.CtrIbim.from_problem(prob, options=opt)
+        psi, dpsi, info = G.solve()
+        assert info.converged
+        alone.append((psi, dpsi, info))
+        G.close()
+    systems = [ctr.CtrIbim.from_problem(prob, options=opt) for prob, opt in probs]
+    batch = ctr.batch_solve(systems)
+    for (psi, dpsi, info), (bpsi, bdpsi, binfo) in zip(alone, batch):
+        assert binfo.converged
+        assert np.array_equal(psi, bpsi) and np.array_equal(dpsi, bdpsi)
+        assert (info.iterations, info.refinements, info.matvecs_fp32, info.matvecs_fp64) == \
+               (binfo.iterations, binfo.refinements, binfo.matvecs_fp32, binfo.matvecs_fp64)
+    # a second batch in another order gives the same results again
+    batch2 = ctr.batch_solve(list(reversed(systems)))
+    for (psi, dpsi, _), (bpsi, bdpsi, _) in zip(alone, reversed(batch2)):
+        assert np.array_equal(psi, bpsi) and np.array_equal(dpsi, bdpsi)
+    for G in systems:
+        G.close()
