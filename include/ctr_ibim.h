@@ -212,6 +212,56 @@ int ctr_ibim_solve(ctr_ibim* sys, double* psi, double* dpsi_n, int on_device, ct
 int ctr_ibim_batch_solve(ctr_ibim* const* systems, int64_t n, double* const* psi, double* const* dpsi_n,
                          int on_device, ctr_solve_info* infos);
 
+/* ---------------------------------------------------------------- serving
+ * A server solves requests (one surface + charges each) as they arrive, with
+ * continuous batching: a host thread admits waiting requests into free slots
+ * of one multi-slot engine while the device-memory budget allows (first come,
+ * first served), advances every admitted system one engine step at a time,
+ * and retires finished ones (their result and polarization energy kept until
+ * released).  Requests that arrive while others run share the same launches.
+ * Every system's arithmetic is the same as when it is solved alone.  The
+ * server uses the device current at ctr_server_create.
+ */
+typedef struct ctr_server ctr_server;
+
+typedef struct {
+    int max_slots;             /* systems resident at once, 1..4096 (default 16) */
+    int64_t hbm_budget_bytes;  /* device memory the resident systems may hold; <= 0: 80% of free memory */
+} ctr_server_options;
+
+typedef struct {
+    int status;                /* CTR_OK, CTR_NOT_CONVERGED, or a negative status of setup/solve */
+    int64_t M;                 /* tube nodes of the request */
+    double G_pol;              /* polarization energy, Eq. (3.3) */
+    ctr_solve_info info;
+    double t_submit, t_admit, t_done;   /* seconds on the server's steady clock */
+} ctr_request_result;
+
+typedef struct {
+    int64_t budget_bytes, used_bytes, peak_used_bytes;
+    int peak_slots, running, waiting;
+    int64_t steps;
+} ctr_server_stats_t;
+
+void ctr_default_server_options(ctr_server_options* opt);
+/* Starts a server (and its worker thread) on the current device. */
+int ctr_server_create(const ctr_server_options* opt, ctr_server** out);
+/* Queues a request; all inputs are host memory and are copied (same meaning as ctr_ibim_setup). */
+int ctr_server_submit(ctr_server* sv, const ctr_grid* grid, const double* sdist, double eps_in, double eps_out,
+                      double kappa, int64_t n_charges, const double* charge_xyz, const double* charge_q,
+                      const ctr_options* opt, uint64_t* ticket);
+/* Non-blocking: *done = 1 and *res filled once the request has finished. */
+int ctr_server_poll(ctr_server* sv, uint64_t ticket, int* done, ctr_request_result* res);
+/* Blocks until the request has finished (timeout_s <= 0: no limit; else CTR_ERR_DEVICE_WAIT on timeout). */
+int ctr_server_wait(ctr_server* sv, uint64_t ticket, double timeout_s, ctr_request_result* res);
+/* Copies a finished request's psi and dpsi_n (M doubles each, host; capacity >= M). */
+int ctr_server_fetch(ctr_server* sv, uint64_t ticket, double* psi, double* dpsi_n, int64_t capacity);
+/* Forgets a finished request and its stored result. */
+int ctr_server_release(ctr_server* sv, uint64_t ticket);
+int ctr_server_stats(ctr_server* sv, ctr_server_stats_t* out);
+/* Stops the worker (waiting requests are dropped) and frees everything. */
+void ctr_server_destroy(ctr_server* sv);
+
 /*
  * Reaction potential at every charge (Eq. 2.31, trapezoidal rule on the
  * tube) and the polarization energy G_pol = 1/2 sum_k q_k psi_rxn(z_k)

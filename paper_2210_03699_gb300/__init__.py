@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "kernel_launches", "batch_solve",
+           "Server", "RequestResult",
            "library_path", "lib",
            "FP64", "FP32_REFINE", "DF64", "METHOD_HYB", "METHOD_KREG"]
 
@@ -53,6 +54,21 @@ class _Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("refinements", ctypes.c_int64),
                 ("matvecs_fp32", ctypes.c_int64), ("matvecs_fp64", ctypes.c_int64),
                 ("residual", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class _RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("M", ctypes.c_int64), ("G_pol", ctypes.c_double), ("info", _Info),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("used_bytes", ctypes.c_int64),
+                ("peak_used_bytes", ctypes.c_int64), ("peak_slots", ctypes.c_int), ("running", ctypes.c_int),
+                ("waiting", ctypes.c_int), ("steps", ctypes.c_int64)]
 
 
 @dataclasses.dataclass
@@ -115,6 +131,18 @@ def _load():
         "ctr_ibim_energy": (ctypes.c_int, [P, P, P, ctypes.c_int, _D, P]),
         "ctr_ibim_reaction_potential": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int64, P, P]),
         "ctr_weight_tables": (ctypes.c_int, [P]),
+        "ctr_default_server_options": (None, [ctypes.POINTER(_ServerOptions)]),
+        "ctr_server_create": (ctypes.c_int, [ctypes.POINTER(_ServerOptions), ctypes.POINTER(P)]),
+        "ctr_server_submit": (ctypes.c_int, [P, ctypes.POINTER(_Grid), P, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int64, P, P, ctypes.POINTER(_Options),
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+        "ctr_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(_RequestResult)]),
+        "ctr_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_RequestResult)]),
+        "ctr_server_fetch": (ctypes.c_int, [P, ctypes.c_uint64, P, P, ctypes.c_int64]),
+        "ctr_server_release": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "ctr_server_stats": (ctypes.c_int, [P, ctypes.POINTER(_ServerStats)]),
+        "ctr_server_destroy": (None, [P]),
         "ctr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "ctr_last_error": (ctypes.c_char_p, []),
         "ctr_kernel_launches": (ctypes.c_int64, []),
@@ -313,6 +341,100 @@ class CtrIbim:
         _check(lib.ctr_ibim_reaction_potential(self._h, pp, dd, dev, z.shape[0], z.ctypes.data_as(ctypes.c_void_p),
                                                out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+
+@dataclasses.dataclass
+class RequestResult:
+    status: int
+    M: int
+    G_pol: float
+    info: SolveInfo
+    t_submit: float
+    t_admit: float
+    t_done: float
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+class Server:
+    """Continuous-batching request server (ctr_server_*): submit problems, poll or wait for results."""
+
+    def __init__(self, max_slots: int = 16, hbm_budget_bytes: int = 0):
+        o = _ServerOptions(int(max_slots), int(hbm_budget_bytes))
+        h = ctypes.c_void_p()
+        _check(lib.ctr_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, grid_n, origin, h, sdist, eps_in, eps_out, kappa, charge_xyz, charge_q,
+               options: Options | None = None) -> int:
+        g = _Grid((ctypes.c_int64 * 3)(*[int(v) for v in grid_n]),
+                  (ctypes.c_double * 3)(*[float(v) for v in origin]), float(h))
+        sd = np.ascontiguousarray(sdist, dtype=np.float64)
+        xyz = np.ascontiguousarray(charge_xyz, dtype=np.float64).reshape(-1, 3)
+        q = np.ascontiguousarray(charge_q, dtype=np.float64).ravel()
+        opt = (options or Options())._c()
+        t = ctypes.c_uint64()
+        _check(lib.ctr_server_submit(self._h, ctypes.byref(g), sd.ctypes.data_as(ctypes.c_void_p), float(eps_in),
+                                     float(eps_out), float(kappa), q.size, xyz.ctypes.data_as(ctypes.c_void_p),
+                                     q.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt), ctypes.byref(t)))
+        return int(t.value)
+
+    def submit_problem(self, prob, options: Options | None = None) -> int:
+        g = prob.grid
+        return self.submit(g.n, g.origin, g.h, prob.sdist, prob.eps_in, prob.eps_out, prob.kappa,
+                           prob.charge_xyz, prob.charge_q, options or Options(tube_halfwidth=prob.tube))
+
+    @staticmethod
+    def _result(r: _RequestResult) -> RequestResult:
+        i = r.info
+        return RequestResult(r.status, int(r.M), float(r.G_pol),
+                             SolveInfo(i.iterations, i.refinements, i.matvecs_fp32, i.matvecs_fp64, i.residual,
+                                       bool(i.converged), r.status), r.t_submit, r.t_admit, r.t_done)
+
+    def poll(self, ticket: int):
+        done = ctypes.c_int()
+        r = _RequestResult()
+        _check(lib.ctr_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(r)))
+        return self._result(r) if done.value else None
+
+    def wait(self, ticket: int, timeout: float = 0.0) -> RequestResult:
+        r = _RequestResult()
+        _check(lib.ctr_server_wait(self._h, ticket, float(timeout), ctypes.byref(r)))
+        return self._result(r)
+
+    def fetch(self, ticket: int, M: int):
+        psi = np.empty(M)
+        dpsi = np.empty(M)
+        _check(lib.ctr_server_fetch(self._h, ticket, psi.ctypes.data_as(ctypes.c_void_p),
+                                    dpsi.ctypes.data_as(ctypes.c_void_p), M))
+        return psi, dpsi
+
+    def release(self, ticket: int):
+        _check(lib.ctr_server_release(self._h, ticket))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib.ctr_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.ctr_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 def batch_solve(systems, device: bool = False):

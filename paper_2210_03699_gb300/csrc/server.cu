@@ -1,0 +1,385 @@
+// Request server with continuous batching over the multi-slot engine.
+//
+// A host thread owns one engine (fixed slot capacity) and loops:
+//   1. admit: while a slot is free and the oldest waiting request fits the
+//      device-memory budget, set it up on the GPU (tube, geometry,
+//      corrections, right-hand side) and put it in a slot;
+//   2. step: one engine step advances every admitted system (an Arnoldi
+//      iteration, or a true-residual evaluation at a cycle end), so requests
+//      that arrive while others run share the same launches;
+//   3. retire: finished systems get their reaction potentials and energy,
+//      their results are kept for the caller, their device memory is freed.
+// Admission is first-come first-served: a request that does not fit waits
+// for memory to free up (requests behind it wait too, so none starves).  The
+// footprint estimate counts the tube nodes on the host (|d| < eps) and charges
+// the per-node cost of geometry, packed sources, split partials, solver
+// vectors and the Krylov basis; after setup the handle's real allocation is
+// charged instead.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+namespace ctr {
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    ctr_grid grid{};
+    std::vector<double> sdist;
+    double eps_in = 1, eps_out = 80, kappa = 0;
+    std::vector<double> xyz, q;
+    ctr_options opt{};
+    ctr_request_result res{};
+    std::vector<double> psi, dpsi;
+    ctr_ibim* sys = nullptr;
+    int slot = -1;
+    int64_t charged = 0;
+    bool done = false;
+};
+
+size_t handle_bytes(const ctr_ibim* s) {
+    const DevBuf* bufs[] = {&s->lin, &s->nodes, &s->src32, &s->src64, &s->srcdf, &s->corr_ptr, &s->corr_node,
+                            &s->corr_w, &s->bad, &s->excl, &s->rhs, &s->charges, &s->partial, &s->err, &s->vecs,
+                            &s->red, &s->kr.V, &s->kr.H, &s->kr.cs, &s->kr.sn, &s->kr.s, &s->kr.y,
+                            &s->kr.part, &s->kr.scal};
+    size_t b = 0;
+    for (const DevBuf* d : bufs) b += d->bytes;
+    return b;
+}
+
+}  // namespace
+
+}  // namespace ctr
+
+struct ctr_server {
+    int device = 0;
+    int cap = 1;
+    int64_t budget = 0;
+    int64_t used = 0;
+    int64_t peak_used = 0;
+    int peak_slots = 0;
+    ctr::Engine* engine = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ctr::Request*> waiting;
+    std::map<uint64_t, ctr::Request*> all;
+    std::vector<ctr::Request*> running;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int fatal = 0;
+    std::string fatal_msg;
+    std::thread worker;
+    int64_t steps = 0;
+};
+
+namespace ctr {
+namespace {
+
+int64_t estimate_bytes(const Request& r) {
+    const double eps = r.opt.tube_halfwidth > 0 ? r.opt.tube_halfwidth : 2.0 * r.grid.h;
+    int64_t M = 0;
+    for (double d : r.sdist) M += (std::fabs(d) < eps) ? 1 : 0;
+    const int m = r.opt.restart > 0 ? r.opt.restart : 64;
+    // per node: geometry 16 doubles, packed sources 32 + 64 + 64 bytes, corrections (~50 entries
+    // worst case, K-reg) 36 bytes each, solver vectors 12 doubles, Krylov (m + 1) x 2 doubles,
+    // split partials up to 16 x 2 doubles
+    const int64_t per_node = 16 * 8 + 160 + 50 * 36 + 12 * 8 + (int64_t)(m + 1) * 16 + 16 * 16;
+    const int64_t grid_bytes = (int64_t)r.sdist.size() * (8 + 4);   // staging copy + node map during setup
+    return M * per_node + grid_bytes;
+}
+
+void finish_request(ctr_server* sv, Request* r, int status) {
+    r->res.status = status;
+    r->res.t_done = now_s();
+    r->done = true;
+    sv->cv_done.notify_all();
+}
+
+// Retire the slots the last step finished (called with the lock released).
+int retire_done(ctr_server* sv, const std::vector<SlotStat>& st, std::vector<Request*>& finished) {
+    for (Request* r : sv->running) {
+        if (st[r->slot].state != kSlotDone) continue;
+        ctr_solve_info info{};
+        const int rs = engine_retire(sv->engine, r->slot, &info);
+        r->res.info = info;
+        int status = rs < 0 ? rs : (info.converged ? CTR_OK : CTR_NOT_CONVERGED);
+        const int64_t M = r->sys->M;
+        r->res.M = M;
+        if (status >= 0) {
+            const double* x = r->sys->vecs.as<double>();
+            r->psi.resize(M);
+            r->dpsi.resize(M);
+            if (cudaMemcpy(r->psi.data(), x, sizeof(double) * M, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(r->dpsi.data(), x + M, sizeof(double) * M, cudaMemcpyDeviceToHost) != cudaSuccess)
+                status = fail(CTR_ERR_CUDA, "result copy");
+        }
+        if (status >= 0) {
+            double G = 0.0;
+            const int es = ctr_ibim_energy(r->sys, r->psi.data(), r->dpsi.data(), 0, &G, nullptr);
+            if (es < 0) status = es;
+            r->res.G_pol = G;
+        }
+        ctr_ibim_destroy(r->sys);
+        r->sys = nullptr;
+        r->slot = -1;
+        finished.push_back(r);
+        r->res.status = status;
+    }
+    return CTR_OK;
+}
+
+void worker_loop(ctr_server* sv) {
+    cudaSetDevice(sv->device);
+    std::vector<SlotStat> st;
+    for (;;) {
+        // ---- admission (under the lock: pick; setup outside the lock)
+        Request* admit = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            if (sv->stop) break;
+            if (sv->running.empty() && sv->waiting.empty()) {
+                sv->cv_work.wait(lk, [&] { return sv->stop || !sv->waiting.empty(); });
+                if (sv->stop) break;
+            }
+            if (!sv->waiting.empty() && (int)sv->running.size() < sv->cap) {
+                Request* head = sv->waiting.front();
+                const int64_t need = estimate_bytes(*head);
+                if (sv->used + need <= sv->budget || sv->running.empty()) {
+                    sv->waiting.pop_front();
+                    head->charged = need;
+                    sv->used += need;
+                    admit = head;
+                }
+            }
+        }
+        if (admit) {
+            admit->res.t_admit = now_s();
+            ctr_ibim* sys = nullptr;
+            int s1 = ctr_ibim_setup(&admit->grid, admit->sdist.data(), 0, admit->eps_in, admit->eps_out, admit->kappa,
+                                    (int64_t)admit->q.size(), admit->xyz.data(), admit->q.data(), &admit->opt,
+                                    nullptr, &sys);
+            int slot = -1;
+            if (s1 >= 0) s1 = engine_admit(sv->engine, sys, &slot);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            admit->sdist.clear();
+            admit->sdist.shrink_to_fit();
+            if (s1 < 0) {
+                if (sys) ctr_ibim_destroy(sys);
+                sv->used -= admit->charged;
+                admit->res.status = s1;
+                finish_request(sv, admit, s1);
+            } else {
+                // charge the real allocation instead of the estimate
+                const int64_t real = (int64_t)handle_bytes(sys);
+                sv->used += real - admit->charged;
+                admit->charged = real;
+                admit->sys = sys;
+                admit->slot = slot;
+                sv->running.push_back(admit);
+                sv->peak_used = std::max(sv->peak_used, sv->used);
+                sv->peak_slots = std::max(sv->peak_slots, (int)sv->running.size());
+            }
+            continue;   // admit as many as fit before the next step
+        }
+        // ---- one engine step for every admitted system
+        bool any;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            any = !sv->running.empty();
+        }
+        if (!any) continue;
+        const int rs = engine_step(sv->engine, &st);
+        std::vector<Request*> finished;
+        if (rs < 0) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->fatal = rs;
+            sv->fatal_msg = ctr_last_error();
+            for (Request* r : sv->running) finish_request(sv, r, rs);
+            sv->running.clear();
+            for (Request* r : sv->waiting) finish_request(sv, r, rs);
+            sv->waiting.clear();
+            break;
+        }
+        retire_done(sv, st, finished);
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->steps++;
+        for (Request* r : finished) {
+            sv->running.erase(std::find(sv->running.begin(), sv->running.end(), r));
+            sv->used -= r->charged;
+            finish_request(sv, r, r->res.status);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace ctr
+
+using namespace ctr;
+
+extern "C" {
+
+void ctr_default_server_options(ctr_server_options* o) {
+    if (!o) return;
+    o->max_slots = 16;
+    o->hbm_budget_bytes = 0;
+}
+
+int ctr_server_create(const ctr_server_options* opt, ctr_server** out) {
+    if (!out) return fail(CTR_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    ctr_server_options o;
+    ctr_default_server_options(&o);
+    if (opt) o = *opt;
+    if (o.max_slots <= 0 || o.max_slots > 4096) return fail(CTR_ERR_INVALID, "max_slots must be in [1, 4096]");
+    ctr_server* sv = new ctr_server();
+    if (cudaGetDevice(&sv->device) != cudaSuccess) {
+        delete sv;
+        return fail(CTR_ERR_CUDA, "cudaGetDevice");
+    }
+    sv->cap = o.max_slots;
+    if (o.hbm_budget_bytes > 0) {
+        sv->budget = o.hbm_budget_bytes;
+    } else {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            delete sv;
+            return fail(CTR_ERR_CUDA, "cudaMemGetInfo");
+        }
+        sv->budget = (int64_t)(0.8 * (double)fr);
+    }
+    const int st = engine_create(sv->device, sv->cap, &sv->engine);
+    if (st < 0) {
+        delete sv;
+        return st;
+    }
+    sv->engine->vec_blocks = 1;
+    sv->worker = std::thread(worker_loop, sv);
+    *out = sv;
+    return CTR_OK;
+}
+
+int ctr_server_submit(ctr_server* sv, const ctr_grid* grid, const double* sdist, double eps_in, double eps_out,
+                      double kappa, int64_t n_charges, const double* charge_xyz, const double* charge_q,
+                      const ctr_options* opt, uint64_t* ticket) {
+    if (!sv || !grid || !sdist || !ticket || n_charges < 0 || (n_charges > 0 && (!charge_xyz || !charge_q)))
+        return fail(CTR_ERR_INVALID, "bad argument");
+    const int64_t total = grid->n[0] * grid->n[1] * grid->n[2];
+    if (total <= 0) return fail(CTR_ERR_INVALID, "empty grid");
+    Request* r = new Request();
+    r->grid = *grid;
+    r->sdist.assign(sdist, sdist + total);
+    r->eps_in = eps_in;
+    r->eps_out = eps_out;
+    r->kappa = kappa;
+    r->xyz.assign(charge_xyz ? charge_xyz : nullptr, charge_xyz ? charge_xyz + 3 * n_charges : nullptr);
+    r->q.assign(charge_q ? charge_q : nullptr, charge_q ? charge_q + n_charges : nullptr);
+    ctr_default_options(&r->opt);
+    if (opt) r->opt = *opt;
+    r->res.t_submit = now_s();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->fatal) {
+        delete r;
+        return fail(sv->fatal, "server stopped: " + sv->fatal_msg);
+    }
+    r->ticket = sv->next_ticket++;
+    sv->all[r->ticket] = r;
+    sv->waiting.push_back(r);
+    *ticket = r->ticket;
+    sv->cv_work.notify_one();
+    return CTR_OK;
+}
+
+int ctr_server_poll(ctr_server* sv, uint64_t ticket, int* done, ctr_request_result* res) {
+    if (!sv || !done) return fail(CTR_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(CTR_ERR_INVALID, "unknown ticket");
+    *done = it->second->done ? 1 : 0;
+    if (*done && res) *res = it->second->res;
+    return CTR_OK;
+}
+
+int ctr_server_wait(ctr_server* sv, uint64_t ticket, double timeout_s, ctr_request_result* res) {
+    if (!sv) return fail(CTR_ERR_INVALID, "bad argument");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(CTR_ERR_INVALID, "unknown ticket");
+    Request* r = it->second;
+    auto pred = [&] { return r->done; };
+    if (timeout_s > 0) {
+        if (!sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+            return fail(CTR_ERR_DEVICE_WAIT, "timed out waiting for the request");
+    } else {
+        sv->cv_done.wait(lk, pred);
+    }
+    if (res) *res = r->res;
+    return CTR_OK;
+}
+
+int ctr_server_fetch(ctr_server* sv, uint64_t ticket, double* psi, double* dpsi_n, int64_t capacity) {
+    if (!sv) return fail(CTR_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(CTR_ERR_INVALID, "unknown ticket");
+    Request* r = it->second;
+    if (!r->done) return fail(CTR_ERR_INVALID, "request not finished");
+    const int64_t M = (int64_t)r->psi.size();
+    if (capacity < M) return fail(CTR_ERR_CAPACITY, "output buffers too small");
+    if (psi) std::memcpy(psi, r->psi.data(), sizeof(double) * M);
+    if (dpsi_n) std::memcpy(dpsi_n, r->dpsi.data(), sizeof(double) * M);
+    return CTR_OK;
+}
+
+int ctr_server_release(ctr_server* sv, uint64_t ticket) {
+    if (!sv) return fail(CTR_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(CTR_ERR_INVALID, "unknown ticket");
+    if (!it->second->done) return fail(CTR_ERR_INVALID, "request not finished");
+    delete it->second;
+    sv->all.erase(it);
+    return CTR_OK;
+}
+
+int ctr_server_stats(ctr_server* sv, ctr_server_stats_t* out) {
+    if (!sv || !out) return fail(CTR_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    out->budget_bytes = sv->budget;
+    out->used_bytes = sv->used;
+    out->peak_used_bytes = sv->peak_used;
+    out->peak_slots = sv->peak_slots;
+    out->running = (int)sv->running.size();
+    out->waiting = (int)sv->waiting.size();
+    out->steps = sv->steps;
+    return CTR_OK;
+}
+
+void ctr_server_destroy(ctr_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (Request* r : sv->running)
+        if (r->sys) ctr_ibim_destroy(r->sys);
+    for (auto& kv : sv->all) delete kv.second;
+    delete sv->engine;
+    delete sv;
+}
+
+}  // extern "C"

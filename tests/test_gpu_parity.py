@@ -315,3 +315,51 @@ def test_batch_matches_alone_bitwise(ctr, oracle_tables):
         assert np.array_equal(psi, bpsi) and np.array_equal(dpsi, bdpsi)
     for G in systems:
         G.close()
+
+
+# ---------------------------------------------------------------- serving (continuous batching)
+def test_server_results_equal_alone_under_staggered_arrivals(ctr):
+    """Requests submitted while others run are admitted as slots free up; each result is the
+    same as the system solved alone (bitwise), and the memory budget is respected."""
+    import time
+    probs = [syn.sphere_problem(h=0.25), syn.ellipsoid_problem(h=0.2),
+             syn.molecule_problem(n_atoms=40, seed=5, h=0.5), syn.sphere_problem(h=0.25, R=1.5, half_box=2.5),
+             syn.ellipsoid_problem(h=0.2, seed=1), syn.sphere_problem(h=0.25, kappa=0.5)]
+    opts = [ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP32_REFINE) for p in probs]
+    alone = []
+    for p, o in zip(probs, opts):
+        G = ctr.CtrIbim.from_problem(p, options=o)
+        psi, dpsi, info = G.solve()
+        Gp, _ = G.energy(psi, dpsi)
+        alone.append((psi, dpsi, Gp, info))
+        G.close()
+    with ctr.Server(max_slots=3, hbm_budget_bytes=int(1.5e9)) as sv:
+        tickets = []
+        for k, (p, o) in enumerate(zip(probs, opts)):
+            tickets.append(sv.submit_problem(p, o))
+            time.sleep(0.01 * k)                      # staggered arrivals
+        results = [sv.wait(t, timeout=300) for t in tickets]
+        st = sv.stats()
+        assert st["peak_slots"] <= 3 and st["peak_used_bytes"] <= st["budget_bytes"]
+        assert st["running"] == 0 and st["waiting"] == 0
+        for t, r, (psi, dpsi, Gp, info) in zip(tickets, results, alone):
+            assert r.status == 0 and r.info.converged
+            assert r.t_submit <= r.t_admit <= r.t_done
+            bpsi, bdpsi = sv.fetch(t, r.M)
+            assert np.array_equal(bpsi, psi) and np.array_equal(bdpsi, dpsi)
+            assert r.G_pol == Gp
+            assert r.info.iterations == info.iterations
+            sv.release(t)
+
+
+def test_server_isolates_failed_requests(ctr):
+    """A request whose setup fails (empty tube) reports its status; the others complete."""
+    good = syn.sphere_problem(h=0.25)
+    with ctr.Server(max_slots=2) as sv:
+        t1 = sv.submit_problem(good)
+        t_bad = sv.submit(good.grid.n, good.grid.origin, good.grid.h, np.full(good.grid.size, 9.0), 1.0, 80.0, 0.1,
+                          np.zeros((1, 3)), np.ones(1))
+        t2 = sv.submit_problem(good)
+        r1, rb, r2 = sv.wait(t1, 120), sv.wait(t_bad, 120), sv.wait(t2, 120)
+        assert r1.status == 0 and r2.status == 0 and rb.status == -2
+        assert r1.G_pol == r2.G_pol
