@@ -45,6 +45,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the baseline sample")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
+                    help="solve: the default single-system line; batch: many molecules in one engine; "
+                         "serve: continuous-batching server under Poisson arrivals")
+    ap.add_argument("--molecules", type=int, default=64, help="batch mode: molecules in the batch")
+    ap.add_argument("--max-atoms", type=int, default=2000, help="batch/serve: largest molecule")
+    ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per load level")
+    ap.add_argument("--loads", default="0.5,0.8,0.95", help="serve mode: offered load / measured capacity")
+    ap.add_argument("--pool", type=int, default=12, help="serve mode: distinct problems requests draw from")
+    ap.add_argument("--slots", type=int, default=16, help="serve mode: server slots")
     return ap.parse_args()
 
 
@@ -213,11 +222,150 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, ctr):
+    """Batched workload: molecules with log-uniform atom counts, h in {0.5, 0.35}, one engine."""
+    import torch
+    import synthetic as syn
+    t0 = time.perf_counter()
+    specs = syn.batch_specs(args.molecules, seed=0, max_atoms=args.max_atoms)
+    probs = syn.molecules_parallel(specs)
+    t_gen = time.perf_counter() - t0
+    opts = [ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP32_REFINE, tol=1e-10) for p in probs]
+
+    def make():
+        return [ctr.CtrIbim.from_problem(p, options=o) for p, o in zip(probs, opts)]
+
+    systems = make()
+    Ms = np.array([g.M for g in systems], dtype=np.float64)
+    ctr.batch_solve(systems)                        # warm-up (and autotuning)
+    torch.cuda.synchronize()
+    launches0 = ctr.kernel_launches()
+    t0 = time.perf_counter()
+    out = ctr.batch_solve(systems)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    launches = ctr.kernel_launches() - launches0
+    pairs = float(np.sum(Ms ** 2 * np.array([i.matvecs_fp32 + i.matvecs_fp64 for _, _, i in out])))
+    # the same systems one after another (engine of one slot each)
+    t0 = time.perf_counter()
+    for g in systems:
+        g.solve(device=True)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    R, U = ctr.tuning_info()
+    line = {"metric": "CTR-IBIM batched pair-interactions/s", "value": pairs / t_batch, "unit": "pair-interactions/s",
+            "n_gpus": 1, "steps": 1, "higher_is_better": True, "dtype": "f32 pairs + f64", "data": "synthetic",
+            "config": {"workload": f"{len(probs)} random-walk SES molecules, atoms log-uniform in 20-{args.max_atoms}, "
+                                   f"h in {{0.5, 0.35}}, tube 2h, FP32 pairs + float-float refinement, tol 1e-10",
+                       "M_min": int(Ms.min()), "M_median": int(np.median(Ms)), "M_max": int(Ms.max()),
+                       "sum_M2": float(np.sum(Ms ** 2)), "generation_s": t_gen},
+            "batch_s": t_batch, "solves_per_s": len(probs) / t_batch, "sequential_s": t_seq,
+            "speedup_vs_sequential": t_seq / t_batch, "all_converged": all(i.converged for _, _, i in out),
+            "max_iterations": int(max(i.iterations for _, _, i in out)),
+            "autotuned_fp32_variant": {"targets_per_thread": R, "unroll": U}, "gpu_launches": int(launches)}
+    for g in systems:
+        g.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args, ctr):
+    """Serving: Poisson arrivals at fractions of the measured capacity; latency and throughput."""
+    import threading as th
+    import torch
+    import synthetic as syn
+    rng = np.random.Generator(np.random.PCG64(0))
+    n_mol = max(1, args.pool // 3)
+    mol_specs = syn.batch_specs(n_mol, seed=100, max_atoms=min(args.max_atoms, 600))
+    pool = list(syn.molecules_parallel(mol_specs))
+    for k in range(max(1, args.pool // 3)):
+        pool.append(syn.sphere_with_nodes(int(np.exp(rng.uniform(np.log(5e3), np.log(4e5)))),
+                                          q=float(rng.choice([-1.0, 1.0]))))
+    for k, hh in enumerate([0.2, 0.1, 0.05][:max(1, args.pool - len(pool))]):
+        pool.append(syn.ellipsoid_problem(h=hh, seed=k))
+    opts = ctr.Options(precision=ctr.FP32_REFINE, tol=1e-10)
+
+    def run_load(rate, n, seed):
+        arrivals = None
+        if rate is not None:
+            gaps = np.random.Generator(np.random.PCG64(seed)).exponential(1.0 / rate, size=n)
+            arrivals = np.cumsum(gaps) - gaps[0]
+        picks = np.random.Generator(np.random.PCG64(seed + 1)).integers(0, len(pool), size=n)
+        with ctr.Server(max_slots=args.slots) as sv:
+            tickets = [None] * n
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i in range(n):
+                    if arrivals is not None:
+                        dt = arrivals[i] - (time.perf_counter() - t0)
+                        if dt > 0:
+                            time.sleep(dt)
+                    p = pool[picks[i]]
+                    tickets[i] = sv.submit_problem(p, ctr.Options(tube_halfwidth=p.tube, precision=opts.precision,
+                                                                  tol=opts.tol))
+
+            thr = th.Thread(target=submitter)
+            thr.start()
+            thr.join()
+            res = [sv.wait(t, timeout=3600) for t in tickets]
+            st = sv.stats()
+        lat = np.array([r.latency for r in res])
+        t_first = min(r.t_submit for r in res)
+        t_last = max(r.t_done for r in res)
+        ok = all(r.status == 0 for r in res)
+        return {"solves_per_s": n / (t_last - t_first), "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+                "all_ok": ok, "peak_slots": st["peak_slots"], "peak_used_GB": st["peak_used_bytes"] / 1e9,
+                "steps": st["steps"], "G": {int(picks[i]): res[i].G_pol for i in range(n)}}
+
+    warm = run_load(None, min(len(pool), 4), 7)      # warm-up (autotuning, first-touch)
+    cap = run_load(None, args.requests, 11)          # saturated: everything submitted at once
+    capacity = cap["solves_per_s"]
+    levels = {}
+    for f in [float(v) for v in args.loads.split(",") if v]:
+        levels[str(f)] = run_load(f * capacity, args.requests, 13)
+    # the plain FP64 one-at-a-time GPU path on the same pool (energies for the error check)
+    t0 = time.perf_counter()
+    G64 = {}
+    for k, p in enumerate(pool):
+        with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP64,
+                                                               tol=1e-10)) as G:
+            psi, dpsi, _ = G.solve(device=True)
+            G64[k] = G.energy(psi, dpsi)[0]
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    errs = [abs(levels[str(f)]["G"][k] / G64[k] - 1) for f in levels for k in levels[str(f)]["G"]]
+    Ms = []
+    for p in pool:
+        with ctr.CtrIbim.from_problem(p) as G:
+            Ms.append(G.M)
+    for lv in list(levels.values()) + [cap]:
+        lv.pop("G", None)
+    line = {"metric": "CTR-IBIM served solves/s", "value": levels[max(levels, key=float)]["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 pairs + f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.requests} requests per load level, Poisson arrivals, drawn from a pool of "
+                                   f"{len(pool)} problems (SES molecules, spheres, ellipsoids), FP32 pairs + "
+                                   f"float-float refinement to 1e-10", "M_min": int(min(Ms)), "M_max": int(max(Ms)),
+                       "slots": args.slots},
+            "capacity_solves_per_s": capacity, "saturated": cap, "levels": levels,
+            "fp64_one_at_a_time_solves_per_s": len(pool) / t64,
+            "max_rel_energy_error_vs_fp64_path": float(max(errs)) if errs else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.mode in ("batch", "serve"):
+        import torch
+        torch.cuda.set_device(local)
+        import paper_2210_03699_gb300 as ctr
+        if rank == 0:
+            (run_batch if args.mode == "batch" else run_serve)(args, ctr)
         return
     import torch
     torch.cuda.set_device(local)

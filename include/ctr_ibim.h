@@ -330,6 +330,15 @@ const char* ctr_last_error(void);
 /* Kernels this library has launched in this process so far (all devices and handles). */
 int64_t ctr_kernel_launches(void);
 
+/*
+ * The FP32 pair-kernel variant the solver's autotuner chose most recently on
+ * the current device: targets per thread (1, 2 or 4) and unroll of the source
+ * loop (1, 2 or 4); 0 and 0 before the first tuned solve.  The tuner times
+ * each variant once on a solve's real work items at its first step (cached per
+ * device and problem-size bucket); variants never change the results.
+ */
+int ctr_tuning_info(int* targets_per_thread, int* unroll);
+
 #ifdef __cplusplus
 }
 #endif

@@ -146,6 +146,7 @@ def _load():
         "ctr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "ctr_last_error": (ctypes.c_char_p, []),
         "ctr_kernel_launches": (ctypes.c_int64, []),
+        "ctr_tuning_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -464,6 +465,13 @@ def batch_solve(systems, device: bool = False):
     _check(st, allow=(0, 1))
     return [(o[0], o[1], SolveInfo(i.iterations, i.refinements, i.matvecs_fp32, i.matvecs_fp64, i.residual,
                                    bool(i.converged), st)) for o, i in zip(outs, infos)]
+
+
+def tuning_info():
+    """(targets per thread, unroll) the autotuner last chose for the FP32 pair kernel (0, 0 if none)."""
+    R, U = ctypes.c_int(), ctypes.c_int()
+    _check(lib.ctr_tuning_info(ctypes.byref(R), ctypes.byref(U)))
+    return int(R.value), int(U.value)
 
 
 def kernel_launches() -> int:

@@ -97,6 +97,12 @@ const char* ctr_last_error(void) { return t_last_error.c_str(); }
 
 int64_t ctr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int ctr_tuning_info(int* targets_per_thread, int* unroll) {
+    if (!targets_per_thread || !unroll) return fail(CTR_ERR_INVALID, "NULL argument");
+    last_tuning(targets_per_thread, unroll);
+    return CTR_OK;
+}
+
 void ctr_ibim_destroy(ctr_ibim* s) {
     if (!s) return;
     int cur = -1;

@@ -21,7 +21,9 @@
 // reduction chunks and scalar updates are exactly those of the slot alone, so
 // a system's result does not depend on what else the engine holds.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <map>
 #include <mutex>
 
 #include "engine.cuh"
@@ -101,7 +103,7 @@ __global__ void k_update_x(SlotDev* S) {
 }
 
 // ---------------------------------------------------------------- persistent pair kernels
-template <typename Policy, int R>
+template <typename Policy, int R, int U>
 __global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int4* __restrict__ items,
                                                     const int* __restrict__ n_items, int* __restrict__ counter,
                                                     int half, int prec, const float2* __restrict__ exp_tab,
@@ -137,8 +139,10 @@ __global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int4* __re
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
-        if (!pair_item<Policy, R>(src, s.M, s.cptr, s.excl, item.y, j_begin, j_end, item.z, s.part, kc, err, ring,
-                                  tab, bar, gt))
+        // the target block index is in units of kThreads * R_slot targets: the slot's plan fixes
+        // the blocks; variants with another R cover the same targets with more or fewer blocks
+        if (!pair_item<Policy, R, U>(src, s.M, s.cptr, s.excl, item.y, j_begin, j_end, item.z, s.part, kc, err,
+                                     ring, tab, bar, gt))
             return;
         __syncthreads();
     }
@@ -350,20 +354,56 @@ __global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
     if (q < cap) out[q] = S[q].stat;
 }
 
-template <typename Policy, int R>
+template <typename Policy, int R, int U>
 int launch_persistent(Engine* e, int pol, int half, int prec) {
     const size_t smem = pair_smem_bytes<Policy>();
-    k_pairs<Policy, R><<<e->grid[pol], kThreads, smem, e->stream>>>(
+    static int per_sm = 0;   // resident blocks of this instantiation (same on every GB300)
+    if (per_sm == 0) {
+        int b = 0;
+        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs<Policy, R, U>, kThreads, smem));
+        per_sm = std::max(1, b);
+    }
+    k_pairs<Policy, R, U><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
         e->slots.as<SlotDev>(), e->items[pol].as<int4>(), e->n_items.as<int>() + pol,
         e->counters.as<int>() + 2 * pol + half, half, prec, e->exp_tab, e->err.as<int>());
     CTR_LAUNCHED();
     return CTR_OK;
 }
 
+// FP32 variants the autotuner chooses from: (targets per thread, unroll of the source loop)
+constexpr int kVariants32[9][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}, {4, 4}};
+
+int launch_fp32(Engine* e, int half) {
+    switch (e->var32) {
+        case 0: return launch_persistent<Fp32Policy, 1, 1>(e, 0, half, CTR_FP32_REFINE);
+        case 1: return launch_persistent<Fp32Policy, 1, 2>(e, 0, half, CTR_FP32_REFINE);
+        case 2: return launch_persistent<Fp32Policy, 1, 4>(e, 0, half, CTR_FP32_REFINE);
+        case 3: return launch_persistent<Fp32Policy, 2, 1>(e, 0, half, CTR_FP32_REFINE);
+        case 5: return launch_persistent<Fp32Policy, 2, 4>(e, 0, half, CTR_FP32_REFINE);
+        case 6: return launch_persistent<Fp32Policy, 4, 1>(e, 0, half, CTR_FP32_REFINE);
+        case 7: return launch_persistent<Fp32Policy, 4, 2>(e, 0, half, CTR_FP32_REFINE);
+        case 8: return launch_persistent<Fp32Policy, 4, 4>(e, 0, half, CTR_FP32_REFINE);
+        default: return launch_persistent<Fp32Policy, 2, 2>(e, 0, half, CTR_FP32_REFINE);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 static int policy_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
+
+static std::atomic<int> g_last_R{0}, g_last_U{0};
+
+void last_tuning(int* R, int* unroll) {
+    *R = g_last_R.load();
+    *unroll = g_last_U.load();
+}
+
+int engine_fp32_variant(const Engine* e, int* R, int* unroll) {
+    *R = kVariants32[e->var32][0];
+    *unroll = kVariants32[e->var32][1];
+    return CTR_OK;
+}
 
 Engine::~Engine() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -404,6 +444,7 @@ int engine_create(int device, int cap, Engine** out) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "attribute"));
+    e->sms = sms;
     int g32 = 0, gdf = 0;
     if ((st = resident_slots_fp32(2, sms, &g32)) < 0) return bad(st);
     if ((st = resident_slots_df64(sms, &gdf)) < 0) return bad(st);
@@ -431,7 +472,9 @@ static int rebuild_items(Engine* e) {
             const SlotDev& s = e->host[q];
             const bool uses = (policy_index(s.inner_prec) == p) || (policy_index(s.res_prec) == p);
             if (!uses) continue;
-            const int tb = (p == 0) ? s.tb32 : (p == 1 ? s.tbdf : s.tb64);
+            const int R32 = kVariants32[e->var32][0];
+            const int tb = (p == 0) ? (int)((s.M + (int64_t)kThreads * R32 - 1) / ((int64_t)kThreads * R32))
+                                    : (p == 1 ? s.tbdf : s.tb64);
             const int sp = (p == 0) ? s.sp32 : (p == 1 ? s.spdf : s.sp64);
             const int per = (p == 0) ? s.per32 : (p == 1 ? s.perdf : s.per64);
             for (int b = 0; b < tb; ++b)
@@ -471,9 +514,9 @@ static int enqueue_step(Engine* e) {
     k_prep_inner<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
     CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, st));
-    CTR_TRY((launch_persistent<Fp32Policy, 2>(e, 0, 0, CTR_FP32_REFINE)));
-    CTR_TRY((launch_persistent<Df64Policy, 1>(e, 1, 0, CTR_DF64)));
-    CTR_TRY((launch_persistent<Fp64Policy, 1>(e, 2, 0, CTR_FP64)));
+    CTR_TRY(launch_fp32(e, 0));
+    CTR_TRY((launch_persistent<Df64Policy, 1, 2>(e, 1, 0, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, 1, 2>(e, 2, 0, CTR_FP64)));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 0);
     CTR_LAUNCHED();
     for (int pass = 0; pass < 2; ++pass) {
@@ -499,9 +542,9 @@ static int enqueue_step(Engine* e) {
     CTR_LAUNCHED();
     k_update_x<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
-    CTR_TRY((launch_persistent<Fp32Policy, 2>(e, 0, 1, CTR_FP32_REFINE)));
-    CTR_TRY((launch_persistent<Df64Policy, 1>(e, 1, 1, CTR_DF64)));
-    CTR_TRY((launch_persistent<Fp64Policy, 1>(e, 2, 1, CTR_FP64)));
+    CTR_TRY(launch_fp32(e, 1));
+    CTR_TRY((launch_persistent<Df64Policy, 1, 2>(e, 1, 1, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, 1, 2>(e, 2, 1, CTR_FP64)));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 1);
     CTR_LAUNCHED();
     k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, 3);
@@ -675,7 +718,72 @@ int engine_retire(Engine* e, int q, ctr_solve_info* info) {
     return st.numeric_error ? fail(CTR_ERR_NUMERIC, "non-finite residual") : CTR_OK;
 }
 
+// Time one FP32 persistent launch per variant over the current work items and keep the fastest.
+// Variants differ only in targets per thread and loop unrolling: every target's sums are formed in
+// the same order, so results are identical whichever is chosen.  Cached per device and size bucket.
+static int engine_autotune(Engine* e) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    double pairs = 0.0;
+    bool fp32 = false;
+    for (int q = 0; q < e->cap; ++q)
+        if (e->owner[q] && e->host[q].inner_prec == CTR_FP32_REFINE) {
+            pairs += (double)e->host[q].M * (double)e->host[q].M;
+            fp32 = true;
+        }
+    e->tuned = true;
+    if (!fp32) return CTR_OK;
+    const int bucket = (int)std::floor(std::log2(std::max(pairs, 1.0)));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({e->device, bucket});
+        if (it != cache.end()) {
+            g_last_R = kVariants32[it->second][0];
+            g_last_U = kVariants32[it->second][1];
+            if (it->second != e->var32) {
+                e->var32 = it->second;
+                CTR_TRY(rebuild_items(e));
+                e->graph_dirty = true;
+            }
+            return CTR_OK;
+        }
+    }
+    cudaEvent_t a, b;
+    CTR_CUDA_TRY(cudaEventCreate(&a));
+    CTR_CUDA_TRY(cudaEventCreate(&b));
+    int best = e->var32;
+    float best_ms = 1e30f;
+    for (int v = 0; v < 9; ++v) {
+        e->var32 = v;
+        CTR_TRY(rebuild_items(e));
+        for (int rep = 0; rep < 2; ++rep) {   // first launch warms up, second is timed
+            CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, e->stream));
+            CTR_CUDA_TRY(cudaEventRecord(a, e->stream));
+            CTR_TRY(launch_fp32(e, 0));
+            CTR_CUDA_TRY(cudaEventRecord(b, e->stream));
+        }
+        CTR_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CTR_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->var32 = best;
+    CTR_TRY(rebuild_items(e));
+    e->graph_dirty = true;
+    g_last_R = kVariants32[best][0];
+    g_last_U = kVariants32[best][1];
+    std::lock_guard<std::mutex> lk(mu);
+    cache[{e->device, bucket}] = best;
+    return CTR_OK;
+}
+
 int engine_step(Engine* e, std::vector<SlotStat>* stats) {
+    if (!e->tuned && e->autotune) CTR_TRY(engine_autotune(e));
     CTR_TRY(ensure_graph(e));
     if (e->graph_exec) {
         CTR_CUDA_TRY(cudaGraphLaunch(e->graph_exec, e->stream));

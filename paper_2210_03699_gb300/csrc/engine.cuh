@@ -58,9 +58,13 @@ struct Engine {
     int max_nblk = 1;
     int max_m = 1;
     int grid[3] = {0, 0, 0};
+    int sms = 1;
     int64_t item_cap[3] = {0, 0, 0};
     int64_t steps = 0;
     int64_t kernels_per_step = 0;
+    int var32 = 4;            // FP32 persistent variant (index into the autotuner's table): R = 2, unroll 2
+    bool autotune = true;     // choose var32 by timing at the first step
+    bool tuned = false;
     const float2* exp_tab = nullptr;
     std::vector<SlotDev> host;
     std::vector<ctr_ibim*> owner;
@@ -77,5 +81,8 @@ int engine_prepare_handle(ctr_ibim* s);
 int engine_solve_all(ctr_ibim* const* hs, int64_t n, int use_graph, std::vector<ctr_solve_info>* infos,
                      int64_t* steps);
 int ensure_krylov_public(ctr_ibim* s);
+int engine_fp32_variant(const Engine* e, int* R, int* unroll);
+// Last variant the autotuner chose on the current device (R = 0 if none yet).
+void last_tuning(int* R, int* unroll);
 
 }  // namespace ctr

@@ -328,7 +328,7 @@ struct Df64Policy {
 // set up by the caller; `gt` counts the tiles this block has consumed so far
 // (it fixes the mbarrier phase parity across items).  Returns false when a
 // bounded wait expired (the error word is set; the caller must return).
-template <typename Policy, int R>
+template <typename Policy, int R, int U = 2>
 __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict__ src, int M,
                                           const int32_t* __restrict__ eptr, const int32_t* __restrict__ excl,
                                           int tblock, int j_begin, int j_end, int slot,
@@ -391,7 +391,7 @@ __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict
 #pragma unroll
         for (int r = 0; r < R; ++r) Policy::zero(acc[r]);
         if (!__any_sync(0xffffffffu, need)) {
-#pragma unroll 2
+#pragma unroll U
             for (int q = 0; q < n; ++q) {
 #pragma unroll
                 for (int r = 0; r < R; ++r)

@@ -292,6 +292,47 @@ def molecule_problem(n_atoms: int = 500, seed: int = 0, h: float = 0.5, probe: f
                    info={"n_atoms": n_atoms, "seed": seed, "probe": probe, "radii": radii})
 
 
+# ---------------------------------------------------------------- batches and request streams
+def batch_specs(n: int, seed: int = 0, min_atoms: int = 20, max_atoms: int = 2000, spacings=(0.5, 0.35)):
+    """Molecule specs of the batched workload: atom counts log-uniform in [min, max], h from `spacings`.
+
+    Returns [(n_atoms, molecule seed, h)]; molecule k uses seed `seed + k`.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    atoms = np.rint(np.exp(rng.uniform(np.log(min_atoms), np.log(max_atoms), size=n))).astype(int)
+    hs = rng.choice(np.asarray(spacings, dtype=np.float64), size=n)
+    return [(int(a), int(seed + k), float(hh)) for k, (a, hh) in enumerate(zip(atoms, hs))]
+
+
+def _molecule_from_spec(spec):
+    n_atoms, seed, h = spec
+    return molecule_problem(n_atoms=n_atoms, seed=seed, h=h)
+
+
+def molecules_parallel(specs, workers: int | None = None):
+    """Generate molecule problems in a spawn-started process pool (safe after CUDA initialisation)."""
+    import multiprocessing as mp
+    import os
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    if workers <= 1 or len(specs) <= 1:
+        return [_molecule_from_spec(s) for s in specs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_molecule_from_spec, specs, chunksize=1)
+
+
+def request_stream(n: int, rate: float, seed: int = 0):
+    """Poisson arrival times (seconds from 0) of n requests at `rate` per second, and pool indices."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    return np.cumsum(gaps) - gaps[0], rng
+
+
+def sphere_with_nodes(target_M: int, h: float = 0.25, q: float = 1.0) -> Problem:
+    """Sphere whose tube holds about target_M nodes (M ~ 4 pi R^2 * 2 eps / h^3 with eps = 2h)."""
+    R = float(np.sqrt(target_M * h * h / (16.0 * np.pi)))
+    return sphere_problem(h=h, R=R, half_box=R + 2 * h + 3 * h + h, q=q)
+
+
 # ---------------------------------------------------------------- densities
 def random_density(M: int, seed: int, smooth_points=None) -> np.ndarray:
     """Seeded test density p = (rho1, rho2), length 2M, values in [-1, 1].
