@@ -7,16 +7,17 @@ E = the component of the complement of U that reaches the box boundary
 Sec. 3.1 step 3).  The SES is {x : dist(x, E) = p}, the molecule is
 {dist(x, E) > p}, and with d > 0 outside:
 
-  * x in E:      d(x) = p + dist(x, U) = p + min_k (|x - z_k| - R_k);
-  * x in U:      d(x) = p - dist(x, E) = p - dist(x, dE).
+  * x in E:                d(x) = p + dist(x, U) = p + min_k (|x - z_k| - R_k);
+  * x in U or a cavity:    d(x) = p - dist(x, E) = p - dist(x, dE).
 
 dist(x, dE) is evaluated exactly against the pieces of the boundary of the
 union of balls: spherical faces (the projection of x onto sphere k, if it is
 covered by no other ball), circular edges of intersecting sphere pairs (the
 nearest point of the full circle, if uncovered) and vertices of sphere
 triples (if uncovered); the nearest boundary point is always one of these.
-Pieces that bound a cavity instead of E are dropped (the grid node one step
-beyond the piece, away from x, is looked up in the flood-filled grid).
+Pieces that bound a cavity instead of E are dropped (the grid cells one to
+three steps beyond the piece along its own outward direction are looked up in
+the flood-filled grid).
 Nodes farther than `band` from the SES get a clamped value of the right sign.
 """
 from __future__ import annotations
@@ -26,8 +27,9 @@ from scipy import ndimage
 from scipy.spatial import cKDTree
 
 
-def _flood_outside(free: np.ndarray) -> np.ndarray:
-    lab, _ = ndimage.label(free)
+def _flood_outside(conn: np.ndarray) -> np.ndarray:
+    """Components of `conn` (26-connected) that touch the box boundary."""
+    lab, _ = ndimage.label(conn, structure=np.ones((3, 3, 3), dtype=bool))
     border = np.unique(np.concatenate([lab[0].ravel(), lab[-1].ravel(), lab[:, 0].ravel(), lab[:, -1].ravel(),
                                        lab[:, :, 0].ravel(), lab[:, :, -1].ravel()]))
     border = border[border > 0]
@@ -109,7 +111,6 @@ def ses_distance(grid, z, r, probe, band):
     X, Y, Zc = grid.points()
     P = np.stack([X, Y, Zc], axis=1)
     tree, circles, verts, vtrip = _boundary_pieces(z, R)
-    rmax = R.max()
     # distance to U (outside) and membership
     dmin = np.full(P.shape[0], np.inf)
     for s in range(0, P.shape[0], 200_000):
@@ -119,30 +120,58 @@ def ses_distance(grid, z, r, probe, band):
         idx = np.atleast_2d(idx)
         dmin[s:s + 200_000] = np.min(dd - R[idx], axis=1)
     shape = (grid.n[2], grid.n[1], grid.n[0])
-    free = (dmin >= 0).reshape(shape)
-    outer = _flood_outside(free).ravel()
+    # E on the grid: every point of E lies within half a cell diagonal of a node with dmin >= -sqrt(3) h / 2,
+    # and a path in E visits 26-adjacent such nodes, so the components of that set that reach the box boundary
+    # hold all of E (walls thinner than sqrt(3) h merge a cavity into E).
+    outer = _flood_outside((dmin >= -0.5 * np.sqrt(3.0) * h).reshape(shape)).ravel() & (dmin >= 0)
     d = np.empty(P.shape[0])
     big = band + 4 * h
     # x in E
-    inE = outer & (dmin >= 0)
-    d[inE] = probe + dmin[inE]
-    # cavity probe positions: part of the molecule, deep
-    cav = (~outer) & (dmin >= 0)
-    d[cav] = -big
-    # x in U: p - dist(x, dE), needed only within the band
-    inU = dmin < 0
-    need = inU & (dmin > -(probe + big))
-    d[inU & ~need] = -big
+    d[outer] = probe + dmin[outer]
+    # x in U or in a cavity (filled, Sec. 3.1): p - dist(x, dE), needed only within the band
+    inside = ~outer
+    need = inside & (dmin > -(probe + big))
+    d[inside & ~need] = -big
     idxs = np.nonzero(need)[0]
     origin = np.array(grid.origin)
     dims = np.array(grid.n)
 
-    def outer_at(pts):
-        ijk = np.rint((pts - origin) / h).astype(np.int64)
-        ijk = np.clip(ijk, 0, dims - 1)
-        lin = ijk[:, 0] + dims[0] * (ijk[:, 1] + dims[1] * ijk[:, 2])
-        return outer[lin]
+    free_flat = (dmin >= 0)
+    corners = np.array([(a, b, c) for c in (0, 1) for b in (0, 1) for a in (0, 1)], dtype=np.int64)
 
+    def outer_side(pts, u):
+        """Whether the free space just beyond boundary points `pts` (outward unit directions `u`) is E.
+
+        Steps h, 2h, 3h outward; at each step the 8 grid nodes of the enclosing cell are looked up and the
+        first step that reaches a free (probe-centre) node decides: outer if any free node there is in E.
+        A piece with no free node within 3h is kept (cavities that small do not occur at these spacings).
+        """
+        res = np.ones(len(pts), dtype=bool)
+        open_ = np.ones(len(pts), dtype=bool)
+        for step in (1.0, 2.0, 3.0):
+            q = pts + (step * h) * u
+            base = np.clip(np.floor((q - origin) / h).astype(np.int64), 0, dims - 2)
+            any_free = np.zeros(len(pts), dtype=bool)
+            any_outer = np.zeros(len(pts), dtype=bool)
+            for c in corners:
+                ijk = base + c
+                lin = ijk[:, 0] + dims[0] * (ijk[:, 1] + dims[1] * ijk[:, 2])
+                any_free |= free_flat[lin]
+                any_outer |= outer[lin]
+            decide = open_ & any_free
+            res[decide] = any_outer[decide]
+            open_ &= ~any_free
+        return res
+
+    def unit(v):
+        return v / np.maximum(np.linalg.norm(v, axis=1), 1e-12)[:, None]
+
+    # which pieces bound E: decided once per piece from its own outward direction (radial for a face,
+    # the sum of the two radial directions for an edge, of the three for a vertex)
+    if len(verts):
+        vdir = unit(sum((verts - z[vtrip[:, c]]) / R[vtrip[:, c], None] for c in range(3)))
+        keepv = outer_side(verts, vdir)
+        verts, vtrip = verts[keepv], vtrip[keepv]
     vtree = cKDTree(verts) if len(verts) else None
     if len(circles):
         ccen, cu, crho, cab = circles
@@ -155,10 +184,10 @@ def ses_distance(grid, z, r, probe, band):
         dd, ii = tree.query(pts, k=kz)
         dd = np.atleast_2d(dd).reshape(len(pts), -1)
         ii = np.atleast_2d(ii).reshape(len(pts), -1)
-        inside = dd < R[ii] - 1e-9
+        inside_ = dd < R[ii] - 1e-9
         for c in range(own.shape[1]):
-            inside &= ii != own[:, c:c + 1]
-        return ~inside.any(axis=1)
+            inside_ &= ii != own[:, c:c + 1]
+        return ~inside_.any(axis=1)
 
     reach = probe + big + 2 * h
     for s in range(0, idxs.size, 50_000):
@@ -166,26 +195,14 @@ def ses_distance(grid, z, r, probe, band):
         Q = P[ids]
         n = ids.size
         best = np.full(n, np.inf)
-        # spherical faces: the projection of x onto each nearby sphere
-        ka = min(24, len(z))
-        dd, ii = tree.query(Q, k=ka)
-        dd = dd.reshape(n, -1)
-        ii = ii.reshape(n, -1)
-        t_idx = np.repeat(np.arange(n), dd.shape[1])
-        a_idx = ii.ravel()
-        L = dd.ravel()
-        keep = (L > 1e-12) & (np.abs(L - R[a_idx]) < reach)
-        t_idx, a_idx, L = t_idx[keep], a_idx[keep], L[keep]
-        cpts = z[a_idx] + (R[a_idx] / L)[:, None] * (Q[t_idx] - z[a_idx])
-        dist = np.abs(L - R[a_idx])
-        ok = uncovered(cpts, a_idx[:, None])
-        dirs = cpts - Q[t_idx]
-        nrm = np.maximum(np.linalg.norm(dirs, axis=1), 1e-12)
-        ok &= outer_at(cpts + h * dirs / nrm[:, None])
-        np.minimum.at(best, t_idx[ok], dist[ok])
+        # vertices (already restricted to those that bound E): an upper bound that prunes the rest
+        if vtree is not None:
+            kv = min(16, len(verts))
+            dv, _ = vtree.query(Q, k=kv)
+            best = np.minimum(best, dv.reshape(n, -1).min(axis=1))
         # circular edges: the nearest point of each nearby intersection circle
         if len(circles):
-            kc = min(24, len(ccen))
+            kc = min(48, len(ccen))
             dd, ii = ctree.query(Q, k=kc)
             dd = dd.reshape(n, -1)
             ii = ii.reshape(n, -1)
@@ -200,23 +217,28 @@ def ses_distance(grid, z, r, probe, band):
             good = Lp > 1e-12
             t_idx, c_idx, wp, Lp = t_idx[good], c_idx[good], wp[good], Lp[good]
             cpts = ccen[c_idx] + (crho[c_idx] / Lp)[:, None] * wp
-            dirs = cpts - Q[t_idx]
-            dist = np.linalg.norm(dirs, axis=1)
+            dist = np.linalg.norm(cpts - Q[t_idx], axis=1)
+            near = dist < best[t_idx]
+            t_idx, c_idx, cpts, dist = t_idx[near], c_idx[near], cpts[near], dist[near]
             ok = uncovered(cpts, cab[c_idx])
-            ok &= outer_at(cpts + h * dirs / np.maximum(dist, 1e-12)[:, None])
+            a, b = cab[c_idx, 0], cab[c_idx, 1]
+            ok &= outer_side(cpts, unit((cpts - z[a]) / R[a, None] + (cpts - z[b]) / R[b, None]))
             np.minimum.at(best, t_idx[ok], dist[ok])
-        # vertices
-        if vtree is not None:
-            kv = min(8, len(verts))
-            dv, iv = vtree.query(Q, k=kv)
-            dv = dv.reshape(n, -1)
-            iv = iv.reshape(n, -1)
-            t_idx = np.repeat(np.arange(n), kv)
-            v_idx = iv.ravel()
-            dist = dv.ravel()
-            cpts = verts[v_idx]
-            ok = outer_at(cpts + h * (cpts - Q[t_idx]) / np.maximum(dist, 1e-12)[:, None])
-            np.minimum.at(best, t_idx[ok], dist[ok])
+        # spherical faces: the projection of x onto each nearby sphere
+        ka = min(32, len(z))
+        dd, ii = tree.query(Q, k=ka)
+        dd = dd.reshape(n, -1)
+        ii = ii.reshape(n, -1)
+        t_idx = np.repeat(np.arange(n), dd.shape[1])
+        a_idx = ii.ravel()
+        L = dd.ravel()
+        dist = np.abs(L - R[a_idx])
+        keep = (L > 1e-12) & (dist < reach) & (dist < best[t_idx])
+        t_idx, a_idx, L, dist = t_idx[keep], a_idx[keep], L[keep], dist[keep]
+        cpts = z[a_idx] + (R[a_idx] / L)[:, None] * (Q[t_idx] - z[a_idx])
+        ok = uncovered(cpts, a_idx[:, None])
+        ok &= outer_side(cpts, (cpts - z[a_idx]) / R[a_idx, None])
+        np.minimum.at(best, t_idx[ok], dist[ok])
         d[ids] = np.where(np.isfinite(best), probe - best, -big)
     d = np.clip(d, -big, big)
     return d
