@@ -30,8 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-OPS_PER_PAIR_FP32 = 44      # FP32-pipe instructions per pair in the FP32 pair kernel (see the design notes)
-SFU_PER_PAIR = 2            # rsqrt + ex2
+# FP32-pipe instructions per pair evaluation, counted from the kernel source (see the design notes):
+# one-sided evaluations (one orientation) and symmetric ones (both orientations, with the share of the
+# in-warp transposed sums), for the FP32 and the float-float pair arithmetics.  SFU work (rsqrt, ex2)
+# and shared-memory loads are not counted.
+OPS_FP32 = {"one": 44, "sym": 54}
+OPS_DF64 = {"one": 507, "sym": 643}
 
 
 def parse():
@@ -252,7 +256,7 @@ def run_batch(args, ctr):
         g.solve(device=True)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    R, U = ctr.tuning_info()
+    R, V, U = ctr.tuning_info()
     line = {"metric": "CTR-IBIM batched pair-interactions/s", "value": pairs / t_batch, "unit": "pair-interactions/s",
             "n_gpus": 1, "steps": 1, "higher_is_better": True, "dtype": "f32 pairs + f64", "data": "synthetic",
             "config": {"workload": f"{len(probs)} random-walk SES molecules, atoms log-uniform in 20-{args.max_atoms}, "
@@ -262,7 +266,7 @@ def run_batch(args, ctr):
             "batch_s": t_batch, "solves_per_s": len(probs) / t_batch, "sequential_s": t_seq,
             "speedup_vs_sequential": t_seq / t_batch, "all_converged": all(i.converged for _, _, i in out),
             "max_iterations": int(max(i.iterations for _, _, i in out)),
-            "autotuned_fp32_variant": {"targets_per_thread": R, "unroll": U}, "gpu_launches": int(launches)}
+            "autotuned_fp32_variant": {"targets_per_thread": R, "chunk": V, "unroll": U}, "gpu_launches": int(launches)}
     for g in systems:
         g.close()
     print(json.dumps(line), flush=True)
@@ -416,33 +420,48 @@ def main():
     pairs_all = sum_over_ranks(pairs, world)
     value = pairs_all / t_max
 
-    # kernel-level roofline: one FP32-pair operator application, timed on the stream
+    # kernel-level rooflines: FP32 and float-float operator applications, timed on the stream
+    t_mv, sched = {}, {}
     with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
         x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, 2 * G.M), device="cuda")
         y = torch.empty_like(x)
-        for _ in range(2):
-            G.matvec(x, ctr.FP32_REFINE, out=y)
-        reps = 5
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            G.matvec(x, ctr.FP32_REFINE, out=y)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_mv32 = e0.elapsed_time(e1) * 1e-3 / reps
-        e0.record(stream)
-        G.matvec(x, ctr.FP64, out=y)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_mv64 = e0.elapsed_time(e1) * 1e-3
+        for pr, reps in ((ctr.FP32_REFINE, 5), (ctr.DF64, 2)):
+            G.matvec(x, pr, out=y)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                G.matvec(x, pr, out=y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_mv[pr] = e0.elapsed_time(e1) * 1e-3 / reps
+            sched[pr] = G.pair_schedule(pr)
         Mk = G.M
-    # peaks from the probes (FP32 pipe)
     rate_ffma = ctypes_probe(ctr, 0)
     rate_ex2 = ctypes_probe(ctr, 2)
     rate_dfma = ctypes_probe(ctr, 4)
-    peak_pairs = rate_ffma / OPS_PER_PAIR_FP32
-    achieved_pairs = Mk * Mk / t_mv32
+
+    def roof(pr, ops, name):
+        sc = sched[pr]
+        n_ops = ops["one"] * sc["one_sided_pairs"] + ops["sym"] * sc["symmetric_pairs"]
+        peak = rate_ffma * Mk * Mk / n_ops
+        ach = Mk * Mk / t_mv[pr]
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "pair-interactions/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_basis": f"measured FFMA rate {rate_ffma:.4g}/s x M^2 / FP32-pipe ops of the schedule "
+                              f"({ops['one']} per one-sided and {ops['sym']} per symmetric pair evaluation)",
+                "t_matvec_ms": t_mv[pr] * 1e3, "one_sided_pairs": sc["one_sided_pairs"],
+                "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"]}
+
+    i_last = infos[-1]
+    r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32Policy> (FP32 pair sum, inner GMRES)")
+    rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)")
+    share32 = i_last.matvecs_fp32 * t_mv[ctr.FP32_REFINE]
+    sharedf = i_last.matvecs_fp64 * t_mv[ctr.DF64]
+    dominant, other = (rdf, r32) if sharedf >= share32 else (r32, rdf)
+    dominant = dict(dominant, ex2_rate=rate_ex2, dfma_rate=rate_dfma,
+                    step_share=max(share32, sharedf) / (t_max / args.steps))
+    other = dict(other, step_share=min(share32, sharedf) / (t_max / args.steps))
 
     # e2e through the public API with host buffers
     e2e = None
@@ -476,12 +495,8 @@ def main():
             "config": dict(cfg, M=int(M), unknowns=int(2 * M), iterations=int(i0.iterations),
                            refinements=int(i0.refinements), matvecs_fp32=int(i0.matvecs_fp32),
                            matvecs_fp64=int(i0.matvecs_fp64), residual=i0.residual, G_pol=Gp),
-            "roofline": {"bound": "alu", "kernel": "pair_kernel<float4> (FP32 pair sum)",
-                         "achieved": achieved_pairs, "peak": peak_pairs, "unit": "pair-interactions/s",
-                         "frac": achieved_pairs / peak_pairs, "traffic": None,
-                         "peak_basis": f"measured FFMA rate {rate_ffma:.4g}/s / {OPS_PER_PAIR_FP32} FP32 ops per pair",
-                         "ex2_rate": rate_ex2, "dfma_rate": rate_dfma,
-                         "t_matvec_fp32_ms": t_mv32 * 1e3, "t_matvec_fp64_ms": t_mv64 * 1e3},
+            "roofline": dominant,
+            "roofline_second": other,
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -88,7 +88,8 @@ typedef struct {
     int max_iter;          /* limit on GMRES iterations (all cycles, all refinements); <= 0: 400 */
     int max_refine;        /* limit on refinement steps (CTR_FP32_REFINE); <= 0 selects 10 */
     double inner_tol;      /* relative tolerance of each FP32 GMRES solve; <= 0 selects 1e-5 */
-    int tile_targets;      /* pair-kernel targets per thread (1, 2 or 4); <= 0: automatic */
+    int tile_targets;      /* reserved, ignored: the pair schedules use 4 targets per thread
+                              (FP32) and 1 (float-float, FP64) */
     int residual;          /* pair arithmetic of the refinement residual r = g - A x:
                               CTR_DF64 (the default of ctr_default_options) or CTR_FP64 */
     int method;            /* CTR_METHOD_HYB (default) or CTR_METHOD_KREG */
@@ -172,6 +173,17 @@ int ctr_ibim_rhs(const ctr_ibim* sys, double* g, int on_device);
 
 /* Surface area by the tube rule, Eq. (2.6) with f = 1: h^3 sum_j W_j. */
 int ctr_ibim_area(const ctr_ibim* sys, double* area);
+
+/*
+ * The pair schedule of one arithmetic (precision CTR_FP32_REFINE, CTR_DF64 or
+ * CTR_FP64) of the dense sum of Eq. (2.30): how many (target, source) pairs
+ * its one-sided items evaluate (the near band, correction pairs masked), how
+ * many its symmetric items evaluate once for both orientations (each counts
+ * once here and stands for two of the M^2 - |N| interactions), its work items
+ * and the bytes of its partial-sum regions.  Any output may be NULL.
+ */
+int ctr_ibim_pair_schedule(const ctr_ibim* sys, int precision, int64_t* one_sided_pairs,
+                           int64_t* symmetric_pairs, int64_t* items, int64_t* partial_bytes);
 
 /*
  * y = A x for the operator of Eq. (2.30) (rows of Eqs. 2.14-2.15): the
@@ -331,13 +343,14 @@ const char* ctr_last_error(void);
 int64_t ctr_kernel_launches(void);
 
 /*
- * The FP32 pair-kernel variant the solver's autotuner chose most recently on
- * the current device: targets per thread (1, 2 or 4) and unroll of the source
- * loop (1, 2 or 4); 0 and 0 before the first tuned solve.  The tuner times
- * each variant once on a solve's real work items at its first step (cached per
- * device and problem-size bucket); variants never change the results.
+ * The FP32 pair-kernel variant the solver's autotuner chose most recently in
+ * this process: targets per thread (fixed, 4), sources per transposed chunk of
+ * the symmetric items (4 or 8) and unroll of the chunk loop (1 or 2); all
+ * 0 before the first tuned solve.  The tuner times each variant once on a
+ * solve's real work items at its first step (cached per device and
+ * problem-size bucket); variants never change the results.
  */
-int ctr_tuning_info(int* targets_per_thread, int* unroll);
+int ctr_tuning_info(int* targets_per_thread, int* chunk, int* unroll);
 
 #ifdef __cplusplus
 }

@@ -146,7 +146,8 @@ def _load():
         "ctr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "ctr_last_error": (ctypes.c_char_p, []),
         "ctr_kernel_launches": (ctypes.c_int64, []),
-        "ctr_tuning_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "ctr_ibim_pair_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 4),
+        "ctr_tuning_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)] * 3),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -282,6 +283,13 @@ class CtrIbim:
         g = np.empty(2 * self.M)
         _check(lib.ctr_ibim_rhs(self._h, g.ctypes.data_as(ctypes.c_void_p), 0))
         return g
+
+    def pair_schedule(self, precision: int = FP32_REFINE) -> dict:
+        """Pair counts of the dense-sum schedule of one arithmetic (see ctr_ibim_pair_schedule)."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib.ctr_ibim_pair_schedule(self._h, int(precision), *[ctypes.byref(x) for x in v]))
+        return {"one_sided_pairs": v[0].value, "symmetric_pairs": v[1].value, "items": v[2].value,
+                "partial_bytes": v[3].value}
 
     def area(self) -> float:
         a = ctypes.c_double()
@@ -468,10 +476,10 @@ def batch_solve(systems, device: bool = False):
 
 
 def tuning_info():
-    """(targets per thread, unroll) the autotuner last chose for the FP32 pair kernel (0, 0 if none)."""
-    R, U = ctypes.c_int(), ctypes.c_int()
-    _check(lib.ctr_tuning_info(ctypes.byref(R), ctypes.byref(U)))
-    return int(R.value), int(U.value)
+    """(targets per thread, sources per chunk, unroll) the autotuner last chose for the FP32 pair kernel."""
+    R, V, U = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.ctr_tuning_info(ctypes.byref(R), ctypes.byref(V), ctypes.byref(U)))
+    return int(R.value), int(V.value), int(U.value)
 
 
 def kernel_launches() -> int:

@@ -97,9 +97,9 @@ const char* ctr_last_error(void) { return t_last_error.c_str(); }
 
 int64_t ctr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-int ctr_tuning_info(int* targets_per_thread, int* unroll) {
-    if (!targets_per_thread || !unroll) return fail(CTR_ERR_INVALID, "NULL argument");
-    last_tuning(targets_per_thread, unroll);
+int ctr_tuning_info(int* targets_per_thread, int* chunk, int* unroll) {
+    if (!targets_per_thread || !chunk || !unroll) return fail(CTR_ERR_INVALID, "NULL argument");
+    last_tuning(targets_per_thread, chunk, unroll);
     return CTR_OK;
 }
 
@@ -282,6 +282,20 @@ int ctr_ibim_rhs(const ctr_ibim* s, double* g, int on_device) {
     CTR_CUDA_TRY(cudaMemcpyAsync(g, s->rhs.p, sizeof(double) * 2 * s->M,
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
     CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return CTR_OK;
+}
+
+int ctr_ibim_pair_schedule(const ctr_ibim* s, int precision, int64_t* one_sided, int64_t* symmetric,
+                           int64_t* items, int64_t* partial_bytes) {
+    if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
+    if (precision != CTR_FP32_REFINE && precision != CTR_DF64 && precision != CTR_FP64)
+        return fail(CTR_ERR_INVALID, "precision");
+    const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
+    const ctr::PairSchedule& p = s->sched[pol];
+    if (one_sided) *one_sided = p.pairs_one;
+    if (symmetric) *symmetric = p.pairs_sym;
+    if (items) *items = (int64_t)p.items.size();
+    if (partial_bytes) *partial_bytes = p.part_doubles * (int64_t)sizeof(double);
     return CTR_OK;
 }
 

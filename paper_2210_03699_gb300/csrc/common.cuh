@@ -99,12 +99,43 @@ struct NodeArrays {
     static constexpr int kCount = 16;
 };
 
-// Pair-kernel launch plan for one precision.
+// Pair-kernel launch plan of the one-sided grid launch (fixed-scratch entry point).
 struct PairPlan {
     int R = 2;          // targets per thread
     int splits = 1;     // source splits (blockIdx.y)
     int src_per_split = 0;
     int target_blocks = 0;
+};
+
+// A work item of a pair schedule: target block I (BS consecutive nodes) against
+// sources [j_begin, j_end); one-sided (sym = 0: correction pairs masked) or
+// symmetric (sym = 1: both orientations of every pair, no correction pair in
+// the item).  Target sums: 2 * BS doubles at ibase of the partial buffer;
+// source sums of a symmetric item: 2 * (j_end - j_begin) doubles at jbase.
+struct PairItem {
+    int32_t I, j_begin, j_end, sym;
+    int64_t ibase, jbase;
+};
+// One partial region as seen by the nodes of a block: node i reads
+// buf[base + c * len + (i - origin)] when 0 <= i - origin < len.
+struct PairRec {
+    int64_t base;
+    int32_t len, origin;
+};
+
+// The pair schedule of one system for one pair arithmetic: items (device list
+// sorted by decreasing cost; host copy and costs kept for the engine) and, per
+// target block, the regions its nodes sum in a fixed order.
+struct PairSchedule {
+    int R = 1;            // targets per thread
+    int BS = 256;         // nodes per target block
+    int tile = 128;       // sources per shared-memory tile
+    int nb = 0;           // target blocks
+    int64_t part_doubles = 0;
+    int64_t pairs_sym = 0, pairs_one = 0;   // evaluated pair orientations of each kind
+    std::vector<PairItem> items;
+    std::vector<double> cost;
+    DevBuf d_items, d_rptr, d_recs;
 };
 
 // Per-handle GMRES workspace.
@@ -150,7 +181,8 @@ struct ctr_ibim {
     ctr::DevBuf err;         // int device error word
     ctr::DevBuf vecs;        // double [6][2M] solver vectors
     ctr::DevBuf red;         // reduction scratch
-    ctr::PairPlan plan32, plan64, plandf;
+    ctr::PairSchedule sched[3];   // pair schedules: [0] FP32, [1] float-float, [2] FP64
+    ctr::DevBuf counter;          // int [4] work counters of the single-system launches
     ctr::Krylov kr;
 };
 
@@ -164,6 +196,8 @@ int weight_tables_device(double* d_tables, cudaStream_t st);
 int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node_of);
 // pairsum.cu
 int plan_pairs(ctr_ibim* s);
+// schedule.cu: symmetric / one-sided pair schedules of a handle
+int build_schedules(ctr_ibim* s, const int slots[3]);
 int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision);
 // krylov.cu: solver workspace
 // energy.cu

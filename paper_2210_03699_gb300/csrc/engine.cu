@@ -103,21 +103,21 @@ __global__ void k_update_x(SlotDev* S) {
 }
 
 // ---------------------------------------------------------------- persistent pair kernels
-template <typename Policy, int R, int U>
-__global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int4* __restrict__ items,
+// Work entries (slot, item of that slot's schedule), sorted by decreasing cost.
+template <typename Policy, int R, int V, int U>
+__global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int2* __restrict__ items,
                                                     const int* __restrict__ n_items, int* __restrict__ counter,
-                                                    int half, int prec, const float2* __restrict__ exp_tab,
+                                                    int half, int prec, int pol, const float2* __restrict__ exp_tab,
                                                     int* __restrict__ err) {
     using Src = typename Policy::Src;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Src* ring = reinterpret_cast<Src*>(smem_raw);
-    float2* tab = reinterpret_cast<float2*>(smem_raw + 2 * Policy::kTile * Policy::kVec * sizeof(Src));
+    PairSmem<Policy> sm(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int cur;
     __shared__ PairConsts kc;
     if (threadIdx.x == 0) kc.exp_tab = exp_tab;   // one table per device, shared by every slot
     __syncthreads();
-    pair_block_init<Policy>(kc, tab, bar);
+    pair_block_init<Policy>(kc, sm.tab, bar);
     uint32_t gt = 0;
     const int total = *n_items;
     for (;;) {
@@ -126,29 +126,28 @@ __global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int4* __re
         const int it = cur;
         __syncthreads();
         if (it >= total) break;
-        const int4 item = items[it];   // slot, target block, split, unused
-        const SlotDev& s = S[item.x];
+        const int2 w = items[it];   // slot, item
+        const SlotDev& s = S[w.x];
         const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec)
                                     : (update_active(s) && s.res_prec == prec);
         if (!want) continue;
-        if (threadIdx.x == 0) kc = s.kc;
+        if (threadIdx.x == 0) {
+            const float2* t = kc.exp_tab;
+            kc = s.kc;
+            kc.exp_tab = t;
+        }
         __syncthreads();
-        const int per = (prec == CTR_FP32_REFINE) ? s.per32 : (prec == CTR_DF64 ? s.perdf : s.per64);
-        const int j_begin = item.z * per;
-        const int j_end = min(s.M, j_begin + per);
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
-        // the target block index is in units of kThreads * R_slot targets: the slot's plan fixes
-        // the blocks; variants with another R cover the same targets with more or fewer blocks
-        if (!pair_item<Policy, R, U>(src, s.M, s.cptr, s.excl, item.y, j_begin, j_end, item.z, s.part, kc, err,
-                                     ring, tab, bar, gt))
+        if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, kc, err, sm.ring,
+                                       sm.jred, sm.tab, bar, gt))
             return;
         __syncthreads();
     }
 }
 
-// finish: diag + fixed-order split sum + correction of the applied vector;
+// finish: diag + fixed-order sum of the schedule's partial regions + correction of the applied vector;
 // inner: w = V_{j+1} = A z;   update: r = g - A x
 __global__ void k_finish(SlotDev* S, int half) {
     const SlotDev& s = S[blockIdx.y];
@@ -156,14 +155,11 @@ __global__ void k_finish(SlotDev* S, int half) {
     const int64_t M = s.M, E = s.E;
     const double* x = (half == 0) ? s.z : s.x;
     const int prec = (half == 0) ? s.inner_prec : s.res_prec;
-    const int splits = (prec == CTR_FP32_REFINE) ? s.sp32 : (prec == CTR_DF64 ? s.spdf : s.sp64);
+    const int pol = (prec == CTR_FP32_REFINE) ? 0 : (prec == CTR_DF64 ? 1 : 2);
     double* out = (half == 0) ? s.V + (size_t)(s.j + 1) * s.n : s.r;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         double s1 = 0.0, s2 = 0.0;
-        for (int q = 0; q < splits; ++q) {
-            s1 += s.part[((size_t)q * 2 + 0) * M + i];
-            s2 += s.part[((size_t)q * 2 + 1) * M + i];
-        }
+        gather_partials(s.recs[pol], s.rptr[pol], s.BS[pol], s.part, i, s1, s2);
         double c1 = 0.0, c2 = 0.0;
         for (int e = s.cptr[i]; e < s.cptr[i + 1]; ++e) {
             const int m = s.cnode[e];
@@ -354,36 +350,28 @@ __global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
     if (q < cap) out[q] = S[q].stat;
 }
 
-template <typename Policy, int R, int U>
+template <typename Policy, int R, int V, int U>
 int launch_persistent(Engine* e, int pol, int half, int prec) {
     const size_t smem = pair_smem_bytes<Policy>();
     static int per_sm = 0;   // resident blocks of this instantiation (same on every GB300)
     if (per_sm == 0) {
         int b = 0;
-        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs<Policy, R, U>, kThreads, smem));
+        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs<Policy, R, V, U>, kThreads, smem));
         per_sm = std::max(1, b);
     }
-    k_pairs<Policy, R, U><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
-        e->slots.as<SlotDev>(), e->items[pol].as<int4>(), e->n_items.as<int>() + pol,
-        e->counters.as<int>() + 2 * pol + half, half, prec, e->exp_tab, e->err.as<int>());
+    k_pairs<Policy, R, V, U><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
+        e->slots.as<SlotDev>(), e->items[pol].as<int2>(), e->n_items.as<int>() + pol,
+        e->counters.as<int>() + 2 * pol + half, half, prec, pol, e->exp_tab, e->err.as<int>());
     CTR_LAUNCHED();
     return CTR_OK;
 }
 
-// FP32 variants the autotuner chooses from: (targets per thread, unroll of the source loop)
-constexpr int kVariants32[9][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}, {4, 4}};
-
 int launch_fp32(Engine* e, int half) {
     switch (e->var32) {
-        case 0: return launch_persistent<Fp32Policy, 1, 1>(e, 0, half, CTR_FP32_REFINE);
-        case 1: return launch_persistent<Fp32Policy, 1, 2>(e, 0, half, CTR_FP32_REFINE);
-        case 2: return launch_persistent<Fp32Policy, 1, 4>(e, 0, half, CTR_FP32_REFINE);
-        case 3: return launch_persistent<Fp32Policy, 2, 1>(e, 0, half, CTR_FP32_REFINE);
-        case 5: return launch_persistent<Fp32Policy, 2, 4>(e, 0, half, CTR_FP32_REFINE);
-        case 6: return launch_persistent<Fp32Policy, 4, 1>(e, 0, half, CTR_FP32_REFINE);
-        case 7: return launch_persistent<Fp32Policy, 4, 2>(e, 0, half, CTR_FP32_REFINE);
-        case 8: return launch_persistent<Fp32Policy, 4, 4>(e, 0, half, CTR_FP32_REFINE);
-        default: return launch_persistent<Fp32Policy, 2, 2>(e, 0, half, CTR_FP32_REFINE);
+        case 1: return launch_persistent<Fp32Policy, kR32, 4, 1>(e, 0, half, CTR_FP32_REFINE);
+        case 2: return launch_persistent<Fp32Policy, kR32, 8, 2>(e, 0, half, CTR_FP32_REFINE);
+        case 3: return launch_persistent<Fp32Policy, kR32, 4, 2>(e, 0, half, CTR_FP32_REFINE);
+        default: return launch_persistent<Fp32Policy, kR32, 8, 1>(e, 0, half, CTR_FP32_REFINE);
     }
 }
 
@@ -392,15 +380,18 @@ int launch_fp32(Engine* e, int half) {
 // ---------------------------------------------------------------- host side
 static int policy_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
 
-static std::atomic<int> g_last_R{0}, g_last_U{0};
+static std::atomic<int> g_last_var{-1};
 
-void last_tuning(int* R, int* unroll) {
-    *R = g_last_R.load();
-    *unroll = g_last_U.load();
+void last_tuning(int* R, int* chunk, int* unroll) {
+    const int v = g_last_var.load();
+    *R = v < 0 ? 0 : kR32;
+    *chunk = v < 0 ? 0 : kVariants32[v][0];
+    *unroll = v < 0 ? 0 : kVariants32[v][1];
 }
 
-int engine_fp32_variant(const Engine* e, int* R, int* unroll) {
-    *R = kVariants32[e->var32][0];
+int engine_fp32_variant(const Engine* e, int* R, int* chunk, int* unroll) {
+    *R = kR32;
+    *chunk = kVariants32[e->var32][0];
     *unroll = kVariants32[e->var32][1];
     return CTR_OK;
 }
@@ -445,12 +436,7 @@ int engine_create(int device, int cap, Engine** out) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "attribute"));
     e->sms = sms;
-    int g32 = 0, gdf = 0;
-    if ((st = resident_slots_fp32(2, sms, &g32)) < 0) return bad(st);
-    if ((st = resident_slots_df64(sms, &gdf)) < 0) return bad(st);
-    e->grid[0] = g32;
-    e->grid[1] = gdf;
-    e->grid[2] = gdf;   // FP64 policy: same launch shape as the float-float one
+    e->var32 = fp32_variant();
     for (int p = 0; p < 3; ++p) e->item_cap[p] = 0;
     if ((st = exp_table(device, &e->exp_tab)) < 0) return bad(st);
     if (cudaStreamSynchronize(stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "sync"));
@@ -458,12 +444,12 @@ int engine_create(int device, int cap, Engine** out) {
     return CTR_OK;
 }
 
-// Rebuild the three item lists (all occupied slots; each item is filtered by state at run time),
-// sorted by decreasing cost for the atomic-counter scheduler.
+// Rebuild the three work lists (every item of every occupied slot's schedule; each entry is filtered
+// by its slot's state at run time), sorted by decreasing cost for the atomic-counter scheduler.
 static int rebuild_items(Engine* e) {
     for (int p = 0; p < 3; ++p) {
         struct It {
-            int4 v;
+            int2 v;
             double cost;
         };
         std::vector<It> list;
@@ -472,28 +458,20 @@ static int rebuild_items(Engine* e) {
             const SlotDev& s = e->host[q];
             const bool uses = (policy_index(s.inner_prec) == p) || (policy_index(s.res_prec) == p);
             if (!uses) continue;
-            const int R32 = kVariants32[e->var32][0];
-            const int tb = (p == 0) ? (int)((s.M + (int64_t)kThreads * R32 - 1) / ((int64_t)kThreads * R32))
-                                    : (p == 1 ? s.tbdf : s.tb64);
-            const int sp = (p == 0) ? s.sp32 : (p == 1 ? s.spdf : s.sp64);
-            const int per = (p == 0) ? s.per32 : (p == 1 ? s.perdf : s.per64);
-            for (int b = 0; b < tb; ++b)
-                for (int k = 0; k < sp; ++k) {
-                    const double src = std::min<double>(per, s.M - (double)k * per);
-                    list.push_back(It{make_int4(q, b, k, 0), src});
-                }
+            const PairSchedule& sc = e->owner[q]->sched[p];
+            for (size_t k = 0; k < sc.items.size(); ++k) list.push_back(It{make_int2(q, (int)k), sc.cost[k]});
         }
         std::stable_sort(list.begin(), list.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
-        std::vector<int4> v(list.size());
+        std::vector<int2> v(list.size());
         for (size_t i = 0; i < list.size(); ++i) v[i] = list[i].v;
         if ((int64_t)v.size() > e->item_cap[p]) {
             const int64_t capn = std::max<int64_t>(1024, (int64_t)v.size() * 2);
-            CTR_TRY(e->items[p].alloc(sizeof(int4) * capn));
+            CTR_TRY(e->items[p].alloc(sizeof(int2) * capn));
             e->item_cap[p] = capn;
             e->graph_dirty = true;   // the item buffer moved
         }
         if (!v.empty())
-            CTR_CUDA_TRY(cudaMemcpyAsync(e->items[p].p, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice,
+            CTR_CUDA_TRY(cudaMemcpyAsync(e->items[p].p, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice,
                                          e->stream));
         const int cnt = (int)v.size();
         CTR_CUDA_TRY(cudaMemcpyAsync(e->n_items.as<int>() + p, &cnt, sizeof(int), cudaMemcpyHostToDevice, e->stream));
@@ -515,8 +493,8 @@ static int enqueue_step(Engine* e) {
     CTR_LAUNCHED();
     CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, st));
     CTR_TRY(launch_fp32(e, 0));
-    CTR_TRY((launch_persistent<Df64Policy, 1, 2>(e, 1, 0, CTR_DF64)));
-    CTR_TRY((launch_persistent<Fp64Policy, 1, 2>(e, 2, 0, CTR_FP64)));
+    CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, CTR_FP64)));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 0);
     CTR_LAUNCHED();
     for (int pass = 0; pass < 2; ++pass) {
@@ -543,8 +521,8 @@ static int enqueue_step(Engine* e) {
     k_update_x<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
     CTR_TRY(launch_fp32(e, 1));
-    CTR_TRY((launch_persistent<Df64Policy, 1, 2>(e, 1, 1, CTR_DF64)));
-    CTR_TRY((launch_persistent<Fp64Policy, 1, 2>(e, 2, 1, CTR_FP64)));
+    CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 1, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 1, CTR_FP64)));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 1);
     CTR_LAUNCHED();
     k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, 3);
@@ -623,15 +601,12 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     d.inner_prec = s->opt.precision;
     d.res_prec = d.refine ? s->opt.residual : s->opt.precision;
     CTR_TRY(pair_consts(s, true, &d.kc));
-    d.tb32 = s->plan32.target_blocks;
-    d.sp32 = s->plan32.splits;
-    d.per32 = s->plan32.src_per_split;
-    d.tbdf = s->plandf.target_blocks;
-    d.spdf = s->plandf.splits;
-    d.perdf = s->plandf.src_per_split;
-    d.tb64 = s->plan64.target_blocks;
-    d.sp64 = s->plan64.splits;
-    d.per64 = s->plan64.src_per_split;
+    for (int p = 0; p < 3; ++p) {
+        d.items[p] = s->sched[p].d_items.as<PairItem>();
+        d.recs[p] = s->sched[p].d_recs.as<PairRec>();
+        d.rptr[p] = s->sched[p].d_rptr.as<int32_t>();
+        d.BS[p] = s->sched[p].BS;
+    }
     double* b = s->vecs.as<double>();
     const int64_t n = d.n;
     d.x = b;
@@ -719,8 +694,9 @@ int engine_retire(Engine* e, int q, ctr_solve_info* info) {
 }
 
 // Time one FP32 persistent launch per variant over the current work items and keep the fastest.
-// Variants differ only in targets per thread and loop unrolling: every target's sums are formed in
-// the same order, so results are identical whichever is chosen.  Cached per device and size bucket.
+// Variants differ only in the source chunk of the transposed sums and in loop unrolling: every
+// sum is formed in the same order, so results are identical whichever is chosen.  Cached per
+// device and size bucket; the choice also serves the single-system launches of the process.
 static int engine_autotune(Engine* e) {
     static std::mutex mu;
     static std::map<std::pair<int, int>, int> cache;
@@ -738,11 +714,10 @@ static int engine_autotune(Engine* e) {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find({e->device, bucket});
         if (it != cache.end()) {
-            g_last_R = kVariants32[it->second][0];
-            g_last_U = kVariants32[it->second][1];
+            g_last_var = it->second;
+            set_fp32_variant(it->second);
             if (it->second != e->var32) {
                 e->var32 = it->second;
-                CTR_TRY(rebuild_items(e));
                 e->graph_dirty = true;
             }
             return CTR_OK;
@@ -753,9 +728,8 @@ static int engine_autotune(Engine* e) {
     CTR_CUDA_TRY(cudaEventCreate(&b));
     int best = e->var32;
     float best_ms = 1e30f;
-    for (int v = 0; v < 9; ++v) {
+    for (int v = 0; v < kNumVariants32; ++v) {
         e->var32 = v;
-        CTR_TRY(rebuild_items(e));
         for (int rep = 0; rep < 2; ++rep) {   // first launch warms up, second is timed
             CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, e->stream));
             CTR_CUDA_TRY(cudaEventRecord(a, e->stream));
@@ -773,10 +747,9 @@ static int engine_autotune(Engine* e) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     e->var32 = best;
-    CTR_TRY(rebuild_items(e));
     e->graph_dirty = true;
-    g_last_R = kVariants32[best][0];
-    g_last_U = kVariants32[best][1];
+    g_last_var = best;
+    set_fp32_variant(best);
     std::lock_guard<std::mutex> lk(mu);
     cache[{e->device, bucket}] = best;
     return CTR_OK;

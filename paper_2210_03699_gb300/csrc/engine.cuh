@@ -42,7 +42,11 @@ struct SlotDev {
     const double* g;
     double lam1, lam2, il1, il2, h2, h3, scale;
     pk::PairConsts kc;
-    int tb32, sp32, per32, tbdf, spdf, perdf, tb64, sp64, per64;
+    // pair schedules of the three arithmetics ([0] FP32, [1] float-float, [2] FP64; owned by the handle)
+    const PairItem* items[3];
+    const PairRec* recs[3];
+    const int32_t* rptr[3];
+    int BS[3];
     // solver workspace (owned by the handle)
     double *x, *r, *z, *V, *H, *cs, *sn, *sv, *y, *cgs, *cgs2, *dpart, *scal;
     double gnorm, beta, tol_out, inner_tol, tol_cycle;
@@ -57,12 +61,11 @@ struct Engine {
     int vec_blocks = 1;
     int max_nblk = 1;
     int max_m = 1;
-    int grid[3] = {0, 0, 0};
     int sms = 1;
     int64_t item_cap[3] = {0, 0, 0};
     int64_t steps = 0;
     int64_t kernels_per_step = 0;
-    int var32 = 4;            // FP32 persistent variant (index into the autotuner's table): R = 2, unroll 2
+    int var32 = 0;            // FP32 persistent variant (index into pk::kVariants32)
     bool autotune = true;     // choose var32 by timing at the first step
     bool tuned = false;
     const float2* exp_tab = nullptr;
@@ -81,8 +84,8 @@ int engine_prepare_handle(ctr_ibim* s);
 int engine_solve_all(ctr_ibim* const* hs, int64_t n, int use_graph, std::vector<ctr_solve_info>* infos,
                      int64_t* steps);
 int ensure_krylov_public(ctr_ibim* s);
-int engine_fp32_variant(const Engine* e, int* R, int* unroll);
-// Last variant the autotuner chose on the current device (R = 0 if none yet).
-void last_tuning(int* R, int* unroll);
+int engine_fp32_variant(const Engine* e, int* R, int* chunk, int* unroll);
+// Last variant the autotuner chose (R = 0 if none yet).
+void last_tuning(int* R, int* chunk, int* unroll);
 
 }  // namespace ctr

@@ -158,20 +158,65 @@ struct Fp32Policy {
     static constexpr int kVec = 2;    // Src per node
     static constexpr int kTile = 256; // nodes per tile (8 KB)
     static constexpr bool kTables = false;
+    static constexpr int kSymStep = 32;   // symmetric chunk fully unrolled
     struct Tgt {
-        float px, py, pz, qx, qy, qz;
+        float px, py, pz, qx, qy, qz, wa, wb;
     };
     struct Acc {
         float a1, a2;
     };
+    using JAcc = Acc;   // source-side (transposed) sums of a symmetric tile
     __device__ static Tgt load(const Src* src, int t) {
         const float4 a = src[2 * t], b = src[2 * t + 1];
-        return Tgt{a.x, a.y, a.z, b.x, b.y, b.z};
+        return Tgt{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
     }
+    __device__ static void clear_w(Tgt& t) { t.wa = t.wb = 0.f; }
     __device__ static void zero(Acc& c) { c.a1 = c.a2 = 0.f; }
     __device__ static void fold(const Acc& c, double& s1, double& s2) {
         s1 += (double)c.a1;
         s2 += (double)c.a2;
+    }
+    __device__ static JAcc jadd(const JAcc& x, const JAcc& y) { return JAcc{x.a1 + y.a1, x.a2 + y.a2}; }
+    __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
+        return JAcc{__shfl_xor_sync(0xffffffffu, x.a1, m), __shfl_xor_sync(0xffffffffu, x.a2, m)};
+    }
+    // Both orientations of one pair: the target's sums (acc) get K(x_i, y_j) applied to source j's
+    // weights and the source's sums (ja) get K(x_j, y_i) applied to target i's weights.  With
+    // d = P_i - P_j the swapped pair has d' = -d, so d'.n_j = -(d.n_j) and d'.n_i = -(d.n_i) swap
+    // roles while r, E, n_i.n_j and the K21 bracket are shared: 8 extra FP32 ops for the second term.
+    __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
+                                    JAcc& ja) {
+        const float4 pa = S[0], nb = S[1];
+        const float dx = T.px - pa.x, dy = T.py - pa.y, dz = T.pz - pa.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float rinv = rsqrt_sfu(r2);
+        const float r = r2 * rinv;
+        const float E = ex2_sfu(k.kl2f * r);
+        const float kr = k.kappaf * r;
+        const float E1 = fmaf(E, kr, E);
+        const float dny = fmaf(dz, nb.z, fmaf(dy, nb.y, dx * nb.x));
+        const float dnx = fmaf(dz, T.qz, fmaf(dy, T.qy, dx * T.qx));
+        const float nn = fmaf(T.qz, nb.z, fmaf(T.qy, nb.y, T.qx * nb.x));
+        const float rinv2 = rinv * rinv;
+        const float s = rinv2 * rinv;
+        const float as = pa.w * s, bs = nb.w * s;
+        const float t1 = fmaf(-k.c1f, E1, 1.f);
+        const float om = fmaf(-rinv, E, rinv);
+        const float t2 = fmaf(-k.c2f, E1, 1.f);
+        const float u = 1.f - E1;
+        const float q = fmaf(kr, kr + 3.f, 3.f);
+        const float t3 = fmaf(-E, q, 3.f);
+        const float B = t3 * dnx * dny * rinv2;
+        const float X = fmaf(u, nn, -B);
+        acc.a1 = fmaf(as, dny * t1, acc.a1);
+        acc.a1 = fmaf(-nb.w, om, acc.a1);
+        acc.a2 = fmaf(bs, dnx * t2, acc.a2);
+        acc.a2 = fmaf(as, X, acc.a2);
+        const float ast = T.wa * s, bst = T.wb * s;
+        ja.a1 = fmaf(-ast, dnx * t1, ja.a1);
+        ja.a1 = fmaf(-T.wb, om, ja.a1);
+        ja.a2 = fmaf(-bst, dny * t2, ja.a2);
+        ja.a2 = fmaf(ast, X, ja.a2);
     }
     template <bool kMask>
     __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, bool ex) {
@@ -212,20 +257,61 @@ struct Fp64Policy {
     static constexpr int kVec = 2;
     static constexpr int kTile = 128;   // 8 KB
     static constexpr bool kTables = false;
+    static constexpr int kSymStep = 4;
     struct Tgt {
-        double px, py, pz, qx, qy, qz;
+        double px, py, pz, qx, qy, qz, wa, wb;
     };
     struct Acc {
         double a1, a2;
     };
+    using JAcc = Acc;
     __device__ static Tgt load(const Src* src, int t) {
         const double4 a = src[2 * t], b = src[2 * t + 1];
-        return Tgt{a.x, a.y, a.z, b.x, b.y, b.z};
+        return Tgt{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
     }
+    __device__ static void clear_w(Tgt& t) { t.wa = t.wb = 0.0; }
     __device__ static void zero(Acc& c) { c.a1 = c.a2 = 0.0; }
     __device__ static void fold(const Acc& c, double& s1, double& s2) {
         s1 += c.a1;
         s2 += c.a2;
+    }
+    __device__ static JAcc jadd(const JAcc& x, const JAcc& y) { return JAcc{x.a1 + y.a1, x.a2 + y.a2}; }
+    __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
+        return JAcc{__shfl_xor_sync(0xffffffffu, x.a1, m), __shfl_xor_sync(0xffffffffu, x.a2, m)};
+    }
+    __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
+                                    JAcc& ja) {
+        const double4 pa = S[0], nb = S[1];
+        const double dx = T.px - pa.x, dy = T.py - pa.y, dz = T.pz - pa.z;
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double rinv = rsqrt(r2);
+        const double r = r2 * rinv;
+        const double E = exp(-k.kappa * r);
+        const double kr = k.kappa * r;
+        const double E1 = fma(E, kr, E);
+        const double dny = fma(dz, nb.z, fma(dy, nb.y, dx * nb.x));
+        const double dnx = fma(dz, T.qz, fma(dy, T.qy, dx * T.qx));
+        const double nn = fma(T.qz, nb.z, fma(T.qy, nb.y, T.qx * nb.x));
+        const double rinv2 = rinv * rinv;
+        const double s = rinv2 * rinv;
+        const double as = pa.w * s, bs = nb.w * s;
+        const double t1 = fma(-k.c1, E1, 1.0);
+        const double om = fma(-rinv, E, rinv);
+        const double t2 = fma(-k.c2, E1, 1.0);
+        const double u = 1.0 - E1;
+        const double q = fma(kr, kr + 3.0, 3.0);
+        const double t3 = fma(-E, q, 3.0);
+        const double B = t3 * dnx * dny * rinv2;
+        const double X = fma(u, nn, -B);
+        acc.a1 = fma(as, dny * t1, acc.a1);
+        acc.a1 = fma(-nb.w, om, acc.a1);
+        acc.a2 = fma(bs, dnx * t2, acc.a2);
+        acc.a2 = fma(as, X, acc.a2);
+        const double ast = T.wa * s, bst = T.wb * s;
+        ja.a1 = fma(-ast, dnx * t1, ja.a1);
+        ja.a1 = fma(-T.wb, om, ja.a1);
+        ja.a2 = fma(-bst, dny * t2, ja.a2);
+        ja.a2 = fma(ast, X, ja.a2);
     }
     template <bool kMask>
     __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, bool ex) {
@@ -267,20 +353,29 @@ struct Df64Policy {
     static constexpr int kVec = 4;
     static constexpr int kTile = 128;   // 8 KB
     static constexpr bool kTables = true;
+    static constexpr int kSymStep = 2;    // ~640 FP32 ops per symmetric pair: two per unrolled step
     struct Tgt {
-        F2 px, py, pz, qx, qy, qz;
+        F2 px, py, pz, qx, qy, qz, wa, wb;
     };
     struct Acc {
         F2 a1, a2;
     };
+    using JAcc = Acc;
     __device__ static Tgt load(const Src* src, int t) {
         const float4 a = src[4 * t], b = src[4 * t + 1], c = src[4 * t + 2], d = src[4 * t + 3];
-        return Tgt{F2{a.x, b.x}, F2{a.y, b.y}, F2{a.z, b.z}, F2{c.x, d.x}, F2{c.y, d.y}, F2{c.z, d.z}};
+        return Tgt{F2{a.x, b.x}, F2{a.y, b.y}, F2{a.z, b.z}, F2{c.x, d.x}, F2{c.y, d.y}, F2{c.z, d.z},
+                   F2{a.w, b.w}, F2{c.w, d.w}};
     }
+    __device__ static void clear_w(Tgt& t) { t.wa = t.wb = F2{0.f, 0.f}; }
     __device__ static void zero(Acc& c) { c.a1 = c.a2 = F2{0.f, 0.f}; }
     __device__ static void fold(const Acc& c, double& s1, double& s2) {
         s1 += (double)c.a1.hi + (double)c.a1.lo;
         s2 += (double)c.a2.hi + (double)c.a2.lo;
+    }
+    __device__ static JAcc jadd(const JAcc& x, const JAcc& y) { return JAcc{add(x.a1, y.a1), add(x.a2, y.a2)}; }
+    __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
+        return JAcc{F2{__shfl_xor_sync(0xffffffffu, x.a1.hi, m), __shfl_xor_sync(0xffffffffu, x.a1.lo, m)},
+                    F2{__shfl_xor_sync(0xffffffffu, x.a2.hi, m), __shfl_xor_sync(0xffffffffu, x.a2.lo, m)}};
     }
     template <bool kMask>
     __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2* tab, Acc& acc,
@@ -320,19 +415,56 @@ struct Df64Policy {
         const F2 Bt = mul(mul(t3, mul(dnx, dny)), rinv2);
         acc.a2 = add(acc.a2, mul(as, sub(mul(u, nn), Bt)));
     }
+    __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2* tab, Acc& acc,
+                                    JAcc& ja) {
+        const float4 s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3];
+        const F2 Px{s0.x, s1.x}, Py{s0.y, s1.y}, Pz{s0.z, s1.z}, A{s0.w, s1.w};
+        const F2 Nx{s2.x, s3.x}, Ny{s2.y, s3.y}, Nz{s2.z, s3.z}, Bw{s2.w, s3.w};
+        const F2 dx = sub(T.px, Px), dy = sub(T.py, Py), dz = sub(T.pz, Pz);
+        const F2 r2 = dot3(dx, dy, dz, dx, dy, dz);
+        const F2 rinv = rsqrt_ff(r2);
+        const F2 r = mul(r2, rinv);
+        const F2 kr = mul(f2(k.kappad), r);
+        const F2 E = exp_neg_ff(kr, tab);
+        const F2 E1 = mul(E, add_f(kr, 1.f));
+        const F2 dny = dot3(dx, dy, dz, Nx, Ny, Nz);
+        const F2 dnx = dot3(dx, dy, dz, T.qx, T.qy, T.qz);
+        const F2 nn = dot3(T.qx, T.qy, T.qz, Nx, Ny, Nz);
+        const F2 rinv2 = mul(rinv, rinv);
+        const F2 s = mul(rinv2, rinv);
+        const F2 t1 = add_f(neg(mul(E1, f2(k.c1d))), 1.f);
+        const F2 om = mul(rinv, add_f(neg(E), 1.f));
+        const F2 t2 = add_f(neg(mul(E1, f2(k.c2d))), 1.f);
+        const F2 u = add_f(neg(E1), 1.f);
+        const F2 q = add_f(mul(kr, add_f(kr, 3.f)), 3.f);
+        const F2 t3 = add_f(neg(mul(E, q)), 3.f);
+        const F2 Bt = mul(mul(t3, mul(dnx, dny)), rinv2);
+        const F2 X = sub(mul(u, nn), Bt);
+        const F2 as = mul(A, s), bs = mul(Bw, s);
+        acc.a1 = add(acc.a1, mul(as, mul(dny, t1)));
+        acc.a1 = sub(acc.a1, mul(Bw, om));
+        acc.a2 = add(acc.a2, mul(bs, mul(dnx, t2)));
+        acc.a2 = add(acc.a2, mul(as, X));
+        const F2 ast = mul(T.wa, s), bst = mul(T.wb, s);
+        ja.a1 = sub(ja.a1, mul(ast, mul(dnx, t1)));
+        ja.a1 = sub(ja.a1, mul(T.wb, om));
+        ja.a2 = sub(ja.a2, mul(bst, mul(dny, t2)));
+        ja.a2 = add(ja.a2, mul(ast, X));
+    }
 };
 
-// One work item of the dense pair sum: target block `tblock` (kThreads * R
-// targets) against sources [j_begin, j_end), partial sums written to
-// partial[(slot * 2 + c) * M + i].  Shared memory (ring, tables, barriers) is
-// set up by the caller; `gt` counts the tiles this block has consumed so far
-// (it fixes the mbarrier phase parity across items).  Returns false when a
-// bounded wait expired (the error word is set; the caller must return).
+// One one-sided work item of the dense pair sum: target block `tblock`
+// (kThreads * R targets) against sources [j_begin, j_end), with the correction
+// pairs masked; the sums of target i go to out[c * cstride + (i - t0)], c = 0, 1.
+// Shared memory (ring, tables, barriers) is set up by the caller; `gt` counts
+// the tiles this block has consumed so far (it fixes the mbarrier phase parity
+// across items).  Returns false when a bounded wait expired (the error word is
+// set; the caller must return).
 template <typename Policy, int R, int U = 2>
 __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict__ src, int M,
                                           const int32_t* __restrict__ eptr, const int32_t* __restrict__ excl,
-                                          int tblock, int j_begin, int j_end, int slot,
-                                          double* __restrict__ partial, const PairConsts& kc,
+                                          int tblock, int j_begin, int j_end, double* __restrict__ out,
+                                          int64_t cstride, int64_t t0, const PairConsts& kc,
                                           int* __restrict__ err, typename Policy::Src* ring, const float2* tab,
                                           uint64_t* bar, uint32_t& gt) {
     using Src = typename Policy::Src;
@@ -419,20 +551,253 @@ __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (ti[r] < M) {
-            partial[((size_t)slot * 2 + 0) * M + ti[r]] = s1[r];
-            partial[((size_t)slot * 2 + 1) * M + ti[r]] = s2[r];
+            out[ti[r] - t0] = s1[r];
+            out[cstride + ti[r] - t0] = s2[r];
         }
     }
     return true;
 }
 
-// Shared-memory bytes of a pair block: the two-stage source ring and, for the
-// float-float policy, the exponential tables.
+// In-warp transpose-and-sum of V per-lane values v[0..V) (V a power of two <= 32):
+// afterwards every lane holds, in v[0], the sum over all 32 lanes of entry
+// lane >> (5 - log2 V).  Each exchange stage halves the entries a lane keeps
+// (it sends the half its partner keeps); the remaining stages are a plain
+// butterfly.  The summation tree is the hypercube order 16, 8, 4, 2, 1 for any V.
+template <typename Policy, int V>
+__device__ __forceinline__ void transpose_sum(typename Policy::JAcc (&v)[V], int lane) {
+    using J = typename Policy::JAcc;
+    int cnt = V;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        if (cnt > 1) {
+            const bool upper = (lane & m) != 0;
+            const int h = cnt / 2;
+#pragma unroll
+            for (int i = 0; i < V / 2; ++i) {
+                if (i < h) {
+                    const J send = upper ? v[i] : v[i + h];
+                    const J keep = upper ? v[i + h] : v[i];
+                    v[i] = Policy::jadd(keep, Policy::jshfl_xor(send, m));
+                }
+            }
+            cnt = h;
+        } else {
+            v[0] = Policy::jadd(v[0], Policy::jshfl_xor(v[0], m));
+        }
+    }
+}
+
+// One symmetric work item: target block `tblock` against sources
+// [j_begin, j_end), no correction pair among them (the schedule guarantees it).
+// Every pair is evaluated once for both orientations (Policy::pair_sym).  The
+// target sums go to out_i[c * BS + (i - tblock * BS)], the source sums to
+// out_j[c * len + (j - j_begin)], len = j_end - j_begin.  Sources are read by
+// broadcast as in the one-sided item; a thread accumulates the source-side
+// terms of a chunk of V sources over its R targets, the warp transposes and
+// sums them (transpose_sum), and the kWarps warp sums of a tile are added in
+// warp order in shared memory (jred: kWarps * TILE entries).  The chunk loop
+// is unrolled S sources at a time (S = V: fully); with S < V the chunk's
+// accumulators shift by S registers per step, which keeps the code of long
+// pair arithmetics within the instruction cache.
+template <typename Policy, int R, int V, int U, int S = V>
+__device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __restrict__ src, int M, int tblock,
+                                              int j_begin, int j_end, double* __restrict__ out_i,
+                                              double* __restrict__ out_j, const PairConsts& kc,
+                                              int* __restrict__ err, typename Policy::Src* ring,
+                                              typename Policy::JAcc* jred, const float2* tab, uint64_t* bar,
+                                              uint32_t& gt) {
+    using Src = typename Policy::Src;
+    using J = typename Policy::JAcc;
+    constexpr int TILE = Policy::kTile;
+    constexpr int VEC = Policy::kVec;
+    constexpr int BS = kThreads * R;
+    constexpr int kWarps = kThreads / 32;
+    constexpr int kShift = (V == 32) ? 0 : (V == 16) ? 1 : (V == 8) ? 2 : (V == 4) ? 3 : (V == 2) ? 4 : 5;
+    static_assert(TILE % V == 0 && TILE <= kThreads, "tile layout");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int len = j_end - j_begin;
+    const int ntiles = (len + TILE - 1) / TILE;
+
+    typename Policy::Tgt tg[R];
+    double s1[R], s2[R];
+    int ti[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ti[r] = tblock * BS + r * kThreads + tid;
+        tg[r] = Policy::load(src, min(ti[r], M - 1));
+        if (ti[r] >= M) Policy::clear_w(tg[r]);   // a padding target adds nothing to the sources
+        s1[r] = 0.0;
+        s2[r] = 0.0;
+    }
+    auto issue = [&](int k) {
+        const uint32_t g = gt + (uint32_t)k;
+        const int j0 = j_begin + k * TILE;
+        const int n = min(TILE, j_end - j0);
+        const uint32_t bytes = (uint32_t)(n * VEC * sizeof(Src));
+        Src* dst = ring + (g & 1) * TILE * VEC;
+        fence_proxy_async();
+        mbar_expect_tx(&bar[g & 1], bytes);
+        bulk_load(dst, src + (size_t)VEC * j0, bytes, &bar[g & 1]);
+    };
+    if (tid == 0 && ntiles > 0) issue(0);
+
+    for (int k = 0; k < ntiles; ++k) {
+        const uint32_t g = gt + (uint32_t)k;
+        if (tid == 0 && k + 1 < ntiles) issue(k + 1);
+        const bool ok = mbar_wait(&bar[g & 1], (g >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(err, kErrWait);
+                if (k + 1 < ntiles) (void)mbar_wait(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
+            }
+            return false;
+        }
+        const Src* tile = ring + (g & 1) * TILE * VEC;
+        const int j0 = j_begin + k * TILE;
+        const int n = min(TILE, j_end - j0);
+        typename Policy::Acc acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) Policy::zero(acc[r]);
+#pragma unroll U
+        for (int c0 = 0; c0 < n; c0 += V) {
+            J ja[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) Policy::zero(ja[q]);
+            if constexpr (S == V) {
+                if (c0 + V <= n) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            Policy::pair_sym(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], ja[q]);
+                    }
+                } else {   // ragged end of the item: warp-uniform skip
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        if (c0 + q < n) {
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                Policy::pair_sym(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], ja[q]);
+                        }
+                    }
+                }
+            } else {
+                // S sources per step; afterwards ja[k] holds source V - S (k / S + 1) + k % S of the chunk
+#pragma unroll 1
+                for (int q0 = 0; q0 < V; q0 += S) {
+                    J cur[S];
+#pragma unroll
+                    for (int t = 0; t < S; ++t) {
+                        Policy::zero(cur[t]);
+                        const int q = c0 + q0 + t;
+                        if (q < n) {   // warp-uniform
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                Policy::pair_sym(tg[r], tile + q * VEC, kc, tab, acc[r], cur[t]);
+                        }
+                    }
+#pragma unroll
+                    for (int k = V - 1; k >= S; --k) ja[k] = ja[k - S];
+#pragma unroll
+                    for (int t = 0; t < S; ++t) ja[t] = cur[t];
+                }
+            }
+            transpose_sum<Policy, V>(ja, lane);
+            const int e = lane >> kShift;
+            const int qs = V - S * (e / S + 1) + e % S;
+            if ((lane & ((1 << kShift) - 1)) == 0 && c0 + qs < n) jred[warp * TILE + c0 + qs] = ja[0];
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) Policy::fold(acc[r], s1[r], s2[r]);
+        __syncthreads();   // all warp sums of this tile are in jred
+        if (tid < n) {
+            J t = jred[tid];
+#pragma unroll
+            for (int w = 1; w < kWarps; ++w) t = Policy::jadd(t, jred[w * TILE + tid]);
+            double d1 = 0.0, d2 = 0.0;
+            Policy::fold(t, d1, d2);
+            out_j[j0 - j_begin + tid] = d1;
+            out_j[(int64_t)len + j0 - j_begin + tid] = d2;
+        }
+        __syncthreads();   // jred and the buffer of this tile are free again
+    }
+    gt += (uint32_t)ntiles;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (ti[r] < M) {
+            out_i[ti[r] - tblock * BS] = s1[r];
+            out_i[BS + ti[r] - tblock * BS] = s2[r];
+        }
+    }
+    return true;
+}
+
+// Runs one item of a schedule (dispatch on its kind).
+template <typename Policy, int R, int V, int U>
+__device__ __forceinline__ bool run_item(const PairItem& it, const typename Policy::Src* __restrict__ src, int M,
+                                         const int32_t* __restrict__ eptr, const int32_t* __restrict__ excl,
+                                         double* __restrict__ buf, const PairConsts& kc, int* __restrict__ err,
+                                         typename Policy::Src* ring, typename Policy::JAcc* jred,
+                                         const float2* tab, uint64_t* bar, uint32_t& gt) {
+    constexpr int BS = kThreads * R;
+    constexpr int S = Policy::kSymStep < V ? Policy::kSymStep : V;
+    if (it.sym)
+        return pair_item_sym<Policy, R, V, U, S>(src, M, it.I, it.j_begin, it.j_end, buf + it.ibase,
+                                                 buf + it.jbase, kc, err, ring, jred, tab, bar, gt);
+    return pair_item<Policy, R, U>(src, M, eptr, excl, it.I, it.j_begin, it.j_end, buf + it.ibase, BS,
+                                   (int64_t)it.I * BS, kc, err, ring, tab, bar, gt);
+}
+
+// Fixed-order sum of every partial region that covers node i (block i / BS).
+__device__ __forceinline__ void gather_partials(const PairRec* __restrict__ recs, const int32_t* __restrict__ rptr,
+                                                int BS, const double* __restrict__ buf, int64_t i, double& s1,
+                                                double& s2) {
+    const int b = (int)(i / BS);
+    for (int q = rptr[b]; q < rptr[b + 1]; ++q) {
+        const PairRec r = recs[q];
+        const int64_t off = i - r.origin;
+        if (off < 0 || off >= r.len) continue;
+        s1 += buf[r.base + off];
+        s2 += buf[r.base + r.len + off];
+    }
+}
+
+// Shared-memory bytes of a pair block: the two-stage source ring, the warp
+// sums of a symmetric tile and, for the float-float policy, the exponential
+// tables (in that order; each part a multiple of 16 bytes).
+template <typename Policy>
+constexpr size_t pair_ring_bytes() {
+    return 2 * Policy::kTile * Policy::kVec * sizeof(typename Policy::Src);
+}
+template <typename Policy>
+constexpr size_t pair_jred_bytes() {
+    return (size_t)(kThreads / 32) * Policy::kTile * sizeof(typename Policy::JAcc);
+}
 template <typename Policy>
 constexpr size_t pair_smem_bytes() {
-    return 2 * Policy::kTile * Policy::kVec * sizeof(typename Policy::Src) +
+    return pair_ring_bytes<Policy>() + pair_jred_bytes<Policy>() +
            (Policy::kTables ? (kExpHi + kExpLo) * sizeof(float2) : 0);
 }
+// The dynamic shared memory of a pair block, carved in the order above.
+template <typename Policy>
+struct PairSmem {
+    typename Policy::Src* ring;
+    typename Policy::JAcc* jred;
+    float2* tab;
+    __device__ explicit PairSmem(unsigned char* raw)
+        : ring(reinterpret_cast<typename Policy::Src*>(raw)),
+          jred(reinterpret_cast<typename Policy::JAcc*>(raw + pair_ring_bytes<Policy>())),
+          tab(reinterpret_cast<float2*>(raw + pair_ring_bytes<Policy>() + pair_jred_bytes<Policy>())) {}
+};
+
+// Fixed launch shapes of the schedules: targets per thread and sources per
+// transposed chunk.  R fixes the target blocks and hence the summation order,
+// so it is the same for every kernel variant of an arithmetic.
+constexpr int kR32 = 4, kRdf = 1, kR64 = 1;
+constexpr int kChunkDf = 8, kChunk64 = 8;
+// FP32 schedule-kernel variants: (sources per transposed chunk, unroll of the chunk loop)
+constexpr int kNumVariants32 = 4;
+extern const int kVariants32[kNumVariants32][2];
 
 // Per-block setup shared by every pair kernel: exponential tables and the two mbarriers.
 template <typename Policy>
@@ -458,10 +823,15 @@ inline float2 split_ff(double v) {
 // float-float table of e^{-k} (k < 64) and e^{-k/1024} (k < 1024) on a device
 int exp_table(int device, const float2** out);
 // Splits of the source range for equal-work items filling whole waves of `slots` resident blocks
+// (one-sided grid launch of the fixed-scratch entry point)
 PairPlan make_plan(int64_t M, int R, int tile, int slots);
-// Resident blocks of the pair kernels on the whole device
-int resident_slots_fp32(int R, int sms, int* slots);
-int resident_slots_df64(int sms, int* slots);
+// Resident blocks of the schedule kernels of the three arithmetics: [0] FP32, [1] float-float, [2] FP64
+int schedule_slots(int sms, int slots[3]);
+// FP32 variant used by the schedule kernels of this process (set by the engine's autotuner)
+void set_fp32_variant(int v);
+int fp32_variant();
+// Runs a handle's schedule of one arithmetic (policy index 0 FP32, 1 float-float, 2 FP64) on its stream
+int launch_schedule(ctr_ibim* s, int pol, const void* src, const pk::PairConsts& kc);
 // Pair constants of a handle (kernel-ratio terms, kappa, tables when needed)
 int pair_consts(ctr_ibim* s, bool tables, pk::PairConsts* out);
 

@@ -14,9 +14,11 @@
 // copies (cp.async.bulk + mbarrier transaction counts); every thread of the
 // block reads each source by broadcast.  The correction pairs N(i) (sorted
 // per target) are skipped exactly: a warp takes a masked path only for tiles
-// that contain one of its lanes' excluded nodes.  Source ranges are split
-// across blockIdx.y; each split writes FP64 partial sums, which the
-// finishing kernel adds in a fixed order (deterministic).
+// that contain one of its lanes' excluded nodes.  The work is a schedule of
+// one-sided and symmetric items (schedule.cu): block pairs without correction
+// pairs are evaluated once for both orientations, each item writes FP64
+// partial regions, and the finishing kernel adds them in a fixed order
+// (deterministic).
 //
 // Three pair arithmetics share this pipeline (policies below):
 //   Fp32  FP32 terms, rsqrt and exp2 on the SFU (44 FP32-pipe ops per pair);
@@ -38,17 +40,15 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(const typename Policy::S
                                                         const int32_t* __restrict__ excl, int src_per_split,
                                                         double* __restrict__ partial, PairConsts kc,
                                                         int* __restrict__ err) {
-    using Src = typename Policy::Src;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Src* ring = reinterpret_cast<Src*>(smem_raw);
-    float2* tab = reinterpret_cast<float2*>(smem_raw + 2 * Policy::kTile * Policy::kVec * sizeof(Src));
+    PairSmem<Policy> sm(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
-    pair_block_init<Policy>(kc, tab, bar);
+    pair_block_init<Policy>(kc, sm.tab, bar);
     const int j_begin = blockIdx.y * src_per_split;
     const int j_end = min(M, j_begin + src_per_split);
     uint32_t gt = 0;
-    (void)pair_item<Policy, R>(src, M, eptr, excl, blockIdx.x, j_begin, j_end, blockIdx.y, partial, kc, err, ring,
-                               tab, bar, gt);
+    (void)pair_item<Policy, R>(src, M, eptr, excl, blockIdx.x, j_begin, j_end,
+                               partial + (size_t)blockIdx.y * 2 * M, M, 0, kc, err, sm.ring, sm.tab, bar, gt);
 }
 
 // a = h^3 W rho1/(4 pi), b = h^3 W rho2/(4 pi) into the weight slots of the packed sources
@@ -75,18 +75,16 @@ __global__ void pack_kernel(const double* __restrict__ x, const double* __restri
     }
 }
 
-// y = diag + fixed-order sum of the split partials + correction (FP64)
-__global__ void finish_kernel(int64_t M, int S, const double* __restrict__ partial, const double* __restrict__ x,
+// y = diag + fixed-order sum of the schedule's partial regions + correction (FP64)
+__global__ void finish_kernel(int64_t M, const PairRec* __restrict__ recs, const int32_t* __restrict__ rptr, int BS,
+                              const double* __restrict__ partial, const double* __restrict__ x,
                               double* __restrict__ y, const double* __restrict__ W, const int32_t* __restrict__ ptr,
                               const int32_t* __restrict__ node, const double* __restrict__ w, int64_t E,
                               double lam1, double lam2, double h2, double h3) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     double s1 = 0.0, s2 = 0.0;
-    for (int s = 0; s < S; ++s) {
-        s1 += partial[((size_t)s * 2 + 0) * M + i];
-        s2 += partial[((size_t)s * 2 + 1) * M + i];
-    }
+    gather_partials(recs, rptr, BS, partial, i, s1, s2);
     double c1 = 0.0, c2 = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
         const int m = node[e];
@@ -96,17 +94,6 @@ __global__ void finish_kernel(int64_t M, int S, const double* __restrict__ parti
     }
     y[i] = lam1 * x[i] + s1 + c1;
     y[M + i] = lam2 * x[M + i] + s2 + c2;
-}
-
-template <typename Policy, int R>
-int launch_pairs(ctr_ibim* s, const typename Policy::Src* src, const PairPlan& p, const PairConsts& kc) {
-    const size_t smem = pair_smem_bytes<Policy>();
-    dim3 grid(p.target_blocks, p.splits);
-    pair_kernel<Policy, R><<<grid, kThreads, smem, s->stream>>>(src, (int)s->M, s->corr_ptr.as<int32_t>(),
-                                                               s->excl.as<int32_t>(), p.src_per_split,
-                                                               s->partial.as<double>(), kc, s->err.as<int>());
-    CTR_LAUNCHED();
-    return CTR_OK;
 }
 
 // float-float static source data {P.hi}{P.lo}{n.hi}{n.lo} (weights filled per application)
@@ -164,16 +151,6 @@ int resident_slots(int sms, int* slots) {
     return CTR_OK;
 }
 
-int resident_slots_fp32(int R, int sms, int* slots) {
-    switch (R) {
-        case 1: return resident_slots<Fp32Policy, 1>(sms, slots);
-        case 4: return resident_slots<Fp32Policy, 4>(sms, slots);
-        default: return resident_slots<Fp32Policy, 2>(sms, slots);
-    }
-}
-
-int resident_slots_df64(int sms, int* slots) { return resident_slots<Df64Policy, 1>(sms, slots); }
-
 // float-float table of e^{-k} (k < 64) and e^{-k/1024} (k < 1024), one per device
 int exp_table(int dev, const float2** out) {
     static DevBuf tabs[64];
@@ -212,17 +189,9 @@ int pair_consts(ctr_ibim* s, bool tables, PairConsts* out) {
 int plan_pairs(ctr_ibim* s) {
     int sms = 0;
     CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-    int R32 = s->opt.tile_targets;
-    if (R32 != 1 && R32 != 2 && R32 != 4) R32 = 2;
-    int slots32 = 0, slots64 = 0, slotsdf = 0;
-    CTR_TRY(resident_slots_fp32(R32, sms, &slots32));
-    CTR_TRY((resident_slots<Fp64Policy, 1>(sms, &slots64)));
-    CTR_TRY((resident_slots<Df64Policy, 1>(sms, &slotsdf)));
-    s->plan32 = make_plan(s->M, R32, Fp32Policy::kTile, slots32);
-    s->plan64 = make_plan(s->M, 1, Fp64Policy::kTile, slots64);
-    s->plandf = make_plan(s->M, 1, Df64Policy::kTile, slotsdf);
-    const int S = std::max(s->plan32.splits, std::max(s->plan64.splits, s->plandf.splits));
-    CTR_TRY(s->partial.alloc(sizeof(double) * 2 * (size_t)S * s->M));
+    int slots[3] = {0, 0, 0};
+    CTR_TRY(schedule_slots(sms, slots));
+    CTR_TRY(build_schedules(s, slots));
     CTR_TRY(s->srcdf.alloc(sizeof(float4) * 4 * (size_t)s->M));
     df_static_kernel<<<grid_for(s->M, 256), 256, 0, s->stream>>>(s->na, s->M, s->srcdf.as<float4>());
     CTR_LAUNCHED();
@@ -240,24 +209,14 @@ int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision) {
     CTR_LAUNCHED();
     PairConsts kc;
     CTR_TRY(pair_consts(s, precision == CTR_DF64, &kc));
-    const PairPlan* p = nullptr;
-    if (precision == CTR_FP32_REFINE) {
-        p = &s->plan32;
-        switch (p->R) {
-            case 1: CTR_TRY((launch_pairs<Fp32Policy, 1>(s, s32, *p, kc))); break;
-            case 4: CTR_TRY((launch_pairs<Fp32Policy, 4>(s, s32, *p, kc))); break;
-            default: CTR_TRY((launch_pairs<Fp32Policy, 2>(s, s32, *p, kc))); break;
-        }
-    } else if (precision == CTR_DF64) {
-        p = &s->plandf;
-        CTR_TRY((launch_pairs<Df64Policy, 1>(s, sdf, *p, kc)));
-    } else {
-        p = &s->plan64;
-        CTR_TRY((launch_pairs<Fp64Policy, 1>(s, s64, *p, kc)));
-    }
+    const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
+    const void* src = s32 ? (const void*)s32 : (sdf ? (const void*)sdf : (const void*)s64);
+    CTR_TRY(launch_schedule(s, pol, src, kc));
+    const PairSchedule& p = s->sched[pol];
     const double h2 = s->h * s->h;
     const double h3 = s->h * s->h * s->h;
-    finish_kernel<<<grid_for(M, 256), 256, 0, st>>>(M, p->splits, s->partial.as<double>(), d_x, d_y, s->na.W,
+    finish_kernel<<<grid_for(M, 256), 256, 0, st>>>(M, p.d_recs.as<PairRec>(), p.d_rptr.as<int32_t>(), p.BS,
+                                                   s->partial.as<double>(), d_x, d_y, s->na.W,
                                                    s->corr_ptr.as<int32_t>(), s->corr_node.as<int32_t>(),
                                                    s->corr_w.as<double>(), s->E,
                                                    0.5 * (1.0 + s->eps_out / s->eps_in),

@@ -1,0 +1,299 @@
+// Pair schedules: which (target block, source range) items evaluate the dense
+// sum of Eq. (2.30), and in what order their partial sums are added.
+//
+// The punctured kernel sum is symmetric in structure: the pair (i, j) needs
+// r = |P_i - P_j|, e^{-kappa r}, the three dot products of d = P_i - P_j with
+// n_i and n_j, and n_i . n_j, whichever of the two nodes is the target.  A
+// symmetric item evaluates each pair of its (target block, source range) once
+// for both orientations (pairkern.cuh, pair_item_sym); a one-sided item
+// evaluates target rows only and masks the correction pairs N(i), which the
+// dense sum omits.  N(i) is not symmetric (j in N(i) does not imply i in N(j)),
+// so every block pair (I, J) in which some correction pair occurs in either
+// direction is "near" and gets one-sided items from both sides; every other
+// block pair with J > I gets symmetric items.  Since the correction nodes of i
+// lie within a few h of P_i, near pairs form a band around the diagonal.
+//
+// Items are split to at most a quarter-wave of work each and sorted by cost
+// for the atomic-counter scheduler.  Every item writes its own partial region;
+// the nodes of a block add the regions that cover them in a fixed order
+// (PairRec lists), so the result does not depend on which block ran what.
+#include <algorithm>
+#include <atomic>
+#include <numeric>
+
+#include "pairkern.cuh"
+
+namespace ctr {
+
+using namespace pk;
+
+namespace {
+
+constexpr int kItemsPerSlot = 4;     // items per resident block in a single-system launch
+constexpr int kMaxBaseBlocks = 8192; // near-flag matrix side (bytes: its square)
+
+// Relative cost of one symmetric pair evaluation (two orientations) against a
+// one-sided one, per arithmetic: extra terms of the second orientation plus the
+// in-warp transposed sums.
+constexpr double kSymCost[3] = {1.25, 1.20, 1.15};
+
+__global__ void near_flags_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ excl, int64_t M,
+                                  int g0, int nb0, uint8_t* __restrict__ flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int bi = (int)(i / g0);
+    flags[(size_t)bi * nb0 + bi] = 1;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int bj = excl[e] / g0;
+        flags[(size_t)bi * nb0 + bj] = 1;
+        flags[(size_t)bj * nb0 + bi] = 1;
+    }
+}
+
+template <typename Policy, int R, int V, int U>
+__global__ void __launch_bounds__(kThreads) sched_kernel(const typename Policy::Src* __restrict__ src, int M,
+                                                         const int32_t* __restrict__ eptr,
+                                                         const int32_t* __restrict__ excl,
+                                                         const PairItem* __restrict__ items, int n_items,
+                                                         int* __restrict__ counter, double* __restrict__ buf,
+                                                         PairConsts kc, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    PairSmem<Policy> sm(smem_raw);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int cur;
+    pair_block_init<Policy>(kc, sm.tab, bar);
+    uint32_t gt = 0;
+    for (;;) {
+        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = cur;
+        __syncthreads();
+        if (it >= n_items) break;
+        if (!run_item<Policy, R, V, U>(items[it], src, M, eptr, excl, buf, kc, err, sm.ring, sm.jred, sm.tab, bar,
+                                       gt))
+            return;
+    }
+}
+
+template <typename Policy, int R, int V, int U>
+int sched_per_sm() {
+    static int per_sm = 0;   // resident blocks of this instantiation (same on every GB300)
+    if (per_sm == 0) {
+        int b = 0;
+        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sched_kernel<Policy, R, V, U>, kThreads,
+                                                                   pair_smem_bytes<Policy>()));
+        per_sm = std::max(1, b);
+    }
+    return per_sm;
+}
+
+template <typename Policy, int R, int V, int U>
+int sched_launch(ctr_ibim* s, int pol, const void* src, const PairConsts& kc, int sms) {
+    const PairSchedule& p = s->sched[pol];
+    if (p.items.empty()) return CTR_OK;
+    const int per_sm = sched_per_sm<Policy, R, V, U>();
+    if (per_sm < 0) return per_sm;
+    const int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, (int64_t)p.items.size());
+    int* counter = s->counter.as<int>() + pol;
+    CTR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s->stream));
+    sched_kernel<Policy, R, V, U><<<grid, kThreads, pair_smem_bytes<Policy>(), s->stream>>>(
+        reinterpret_cast<const typename Policy::Src*>(src), (int)s->M, s->corr_ptr.as<int32_t>(),
+        s->excl.as<int32_t>(), p.d_items.as<PairItem>(), (int)p.items.size(), counter, s->partial.as<double>(), kc,
+        s->err.as<int>());
+    CTR_LAUNCHED();
+    return CTR_OK;
+}
+
+// Items of one arithmetic for a system of M nodes with the given near-flag matrix.
+void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost, const std::vector<uint8_t>& flags,
+                   int g0, int nb0, int slots) {
+    p.R = R;
+    p.BS = kThreads * R;
+    p.tile = tile;
+    const int BS = p.BS;
+    const int nb = (int)((M + BS - 1) / BS);
+    p.nb = nb;
+    auto base_range = [&](int I, int& lo, int& hi) {
+        lo = (int)((int64_t)I * BS / g0);
+        hi = (int)std::min<int64_t>(nb0 - 1, (((int64_t)I + 1) * BS - 1) / g0);
+    };
+    auto near = [&](int I, int J) {
+        int a0, a1, b0, b1;
+        base_range(I, a0, a1);
+        base_range(J, b0, b1);
+        for (int a = a0; a <= a1; ++a)
+            for (int b = b0; b <= b1; ++b)
+                if (flags[(size_t)a * nb0 + b]) return true;
+        return false;
+    };
+    struct Run {
+        int I, j0, j1, sym;
+    };
+    std::vector<Run> runs;
+    double total = 0.0;
+    for (int I = 0; I < nb; ++I) {
+        int J = 0;
+        while (J < nb) {
+            if (near(I, J)) {
+                int J1 = J;
+                while (J1 < nb && near(I, J1)) ++J1;
+                runs.push_back(Run{I, (int)((int64_t)J * BS), (int)std::min<int64_t>(M, (int64_t)J1 * BS), 0});
+                J = J1;
+            } else if (J > I) {
+                int J1 = J;
+                while (J1 < nb && !near(I, J1)) ++J1;
+                runs.push_back(Run{I, (int)((int64_t)J * BS), (int)std::min<int64_t>(M, (int64_t)J1 * BS), 1});
+                J = J1;
+            } else {
+                ++J;
+            }
+        }
+    }
+    for (const Run& r : runs) total += (double)BS * (r.j1 - r.j0) * (r.sym ? sym_cost : 1.0);
+    // split runs into items of at most a quarter-wave of work (whole tiles, at least two when possible)
+    const double cmax = std::max(1.0, total / ((double)kItemsPerSlot * std::max(1, slots)));
+    p.items.clear();
+    p.cost.clear();
+    p.pairs_sym = p.pairs_one = 0;
+    int64_t off = 0;
+    for (const Run& r : runs) {
+        const int64_t len = r.j1 - r.j0;
+        const double unit = (double)BS * (r.sym ? sym_cost : 1.0);
+        int64_t pieces = std::max<int64_t>(1, (int64_t)std::ceil(unit * (double)len / cmax));
+        int64_t plen = (len + pieces - 1) / pieces;
+        plen = ((plen + tile - 1) / tile) * tile;
+        plen = std::max<int64_t>(plen, std::min<int64_t>(len, 2 * (int64_t)tile));
+        for (int64_t a = r.j0; a < r.j1; a += plen) {
+            PairItem it{};
+            it.I = r.I;
+            it.j_begin = (int32_t)a;
+            it.j_end = (int32_t)std::min<int64_t>(r.j1, a + plen);
+            it.sym = r.sym;
+            it.ibase = off;
+            off += 2 * (int64_t)BS;
+            it.jbase = 0;
+            if (r.sym) {
+                it.jbase = off;
+                off += 2 * (int64_t)(it.j_end - it.j_begin);
+            }
+            const int64_t tgt = std::min<int64_t>(BS, M - (int64_t)r.I * BS);
+            if (r.sym) p.pairs_sym += tgt * (it.j_end - it.j_begin);
+            else p.pairs_one += tgt * (it.j_end - it.j_begin);
+            p.items.push_back(it);
+            p.cost.push_back(unit * (double)(it.j_end - it.j_begin));
+        }
+    }
+    p.part_doubles = off;
+}
+
+// Device copies: items sorted by decreasing cost, region lists per block in item order.
+int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
+    const int nb = p.nb;
+    std::vector<std::vector<PairRec>> per(nb);
+    for (const PairItem& it : p.items) {
+        per[it.I].push_back(PairRec{it.ibase, p.BS, (int32_t)((int64_t)it.I * p.BS)});
+        if (it.sym) {
+            const int b0 = it.j_begin / p.BS, b1 = (it.j_end - 1) / p.BS;
+            for (int b = b0; b <= b1; ++b)
+                per[b].push_back(PairRec{it.jbase, it.j_end - it.j_begin, it.j_begin});
+        }
+    }
+    std::vector<int32_t> rptr(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) rptr[b + 1] = rptr[b] + (int32_t)per[b].size();
+    std::vector<PairRec> recs;
+    recs.reserve(rptr[nb]);
+    for (int b = 0; b < nb; ++b) recs.insert(recs.end(), per[b].begin(), per[b].end());
+    std::vector<int> order(p.items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p.cost[a] > p.cost[b]; });
+    std::vector<PairItem> sorted(p.items.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = p.items[order[k]];
+    CTR_TRY(p.d_items.alloc(sizeof(PairItem) * std::max<size_t>(1, sorted.size())));
+    CTR_TRY(p.d_rptr.alloc(sizeof(int32_t) * rptr.size()));
+    CTR_TRY(p.d_recs.alloc(sizeof(PairRec) * std::max<size_t>(1, recs.size())));
+    if (!sorted.empty())
+        CTR_CUDA_TRY(cudaMemcpyAsync(p.d_items.p, sorted.data(), sizeof(PairItem) * sorted.size(),
+                                     cudaMemcpyHostToDevice, st));
+    CTR_CUDA_TRY(cudaMemcpyAsync(p.d_rptr.p, rptr.data(), sizeof(int32_t) * rptr.size(), cudaMemcpyHostToDevice, st));
+    if (!recs.empty())
+        CTR_CUDA_TRY(
+            cudaMemcpyAsync(p.d_recs.p, recs.data(), sizeof(PairRec) * recs.size(), cudaMemcpyHostToDevice, st));
+    CTR_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+    (void)M;
+    return CTR_OK;
+}
+
+std::atomic<int> g_var32{0};
+
+}  // namespace
+
+// FP32 schedule-kernel variants (sources per transposed chunk, unroll of the chunk loop); they
+// differ in speed only, not in results (same summation trees).
+const int pk::kVariants32[pk::kNumVariants32][2] = {{8, 1}, {4, 1}, {8, 2}, {4, 2}};
+
+void set_fp32_variant(int v) { g_var32.store((v >= 0 && v < kNumVariants32) ? v : 0); }
+int fp32_variant() { return g_var32.load(); }
+
+int schedule_slots(int sms, int slots[3]) {
+    int a = 0;
+    switch (fp32_variant()) {
+        case 1: a = sched_per_sm<Fp32Policy, kR32, 4, 1>(); break;
+        case 2: a = sched_per_sm<Fp32Policy, kR32, 8, 2>(); break;
+        case 3: a = sched_per_sm<Fp32Policy, kR32, 4, 2>(); break;
+        default: a = sched_per_sm<Fp32Policy, kR32, 8, 1>(); break;
+    }
+    if (a < 0) return a;
+    const int b = sched_per_sm<Df64Policy, kRdf, kChunkDf, 1>();
+    if (b < 0) return b;
+    const int c = sched_per_sm<Fp64Policy, kR64, kChunk64, 1>();
+    if (c < 0) return c;
+    slots[0] = a * sms;
+    slots[1] = b * sms;
+    slots[2] = c * sms;
+    return CTR_OK;
+}
+
+int launch_schedule(ctr_ibim* s, int pol, const void* src, const PairConsts& kc) {
+    int sms = 0;
+    CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+    if (pol == 0) {
+        switch (fp32_variant()) {
+            case 1: return sched_launch<Fp32Policy, kR32, 4, 1>(s, 0, src, kc, sms);
+            case 2: return sched_launch<Fp32Policy, kR32, 8, 2>(s, 0, src, kc, sms);
+            case 3: return sched_launch<Fp32Policy, kR32, 4, 2>(s, 0, src, kc, sms);
+            default: return sched_launch<Fp32Policy, kR32, 8, 1>(s, 0, src, kc, sms);
+        }
+    }
+    if (pol == 1) return sched_launch<Df64Policy, kRdf, kChunkDf, 1>(s, 1, src, kc, sms);
+    return sched_launch<Fp64Policy, kR64, kChunk64, 1>(s, 2, src, kc, sms);
+}
+
+int build_schedules(ctr_ibim* s, const int slots[3]) {
+    const int64_t M = s->M;
+    // near flags on base blocks of g0 nodes (the smallest target block, coarsened for huge systems)
+    int g0 = kThreads;
+    while ((M + g0 - 1) / g0 > kMaxBaseBlocks) g0 *= 2;
+    const int nb0 = (int)((M + g0 - 1) / g0);
+    DevBuf d_flags;
+    CTR_TRY(d_flags.alloc((size_t)nb0 * nb0));
+    CTR_CUDA_TRY(cudaMemsetAsync(d_flags.p, 0, (size_t)nb0 * nb0, s->stream));
+    near_flags_kernel<<<grid_for(M, 256), 256, 0, s->stream>>>(s->corr_ptr.as<int32_t>(), s->excl.as<int32_t>(), M,
+                                                              g0, nb0, d_flags.as<uint8_t>());
+    CTR_LAUNCHED();
+    std::vector<uint8_t> flags((size_t)nb0 * nb0);
+    CTR_CUDA_TRY(cudaMemcpyAsync(flags.data(), d_flags.p, flags.size(), cudaMemcpyDeviceToHost, s->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    const int Rs[3] = {kR32, kRdf, kR64};
+    const int tiles[3] = {Fp32Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
+    int64_t need = 1;
+    for (int p = 0; p < 3; ++p) {
+        plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], flags, g0, nb0, slots[p]);
+        CTR_TRY(upload_schedule(s->sched[p], M, s->stream));
+        need = std::max(need, s->sched[p].part_doubles);
+    }
+    CTR_TRY(s->partial.alloc(sizeof(double) * (size_t)need));
+    CTR_TRY(s->counter.alloc(sizeof(int) * 4));
+    return CTR_OK;
+}
+
+}  // namespace ctr

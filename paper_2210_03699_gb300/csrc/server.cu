@@ -94,11 +94,13 @@ int64_t estimate_bytes(const Request& r) {
     for (double d : r.sdist) M += (std::fabs(d) < eps) ? 1 : 0;
     const int m = r.opt.restart > 0 ? r.opt.restart : 64;
     // per node: geometry 16 doubles, packed sources 32 + 64 + 64 bytes, corrections (~50 entries
-    // worst case, K-reg) 36 bytes each, solver vectors 12 doubles, Krylov (m + 1) x 2 doubles,
-    // split partials up to 16 x 2 doubles
-    const int64_t per_node = 16 * 8 + 160 + 50 * 36 + 12 * 8 + (int64_t)(m + 1) * 16 + 16 * 16;
+    // worst case, K-reg) 36 bytes each, solver vectors 12 doubles, Krylov (m + 1) x 2 doubles;
+    // pair partial regions: the source sums of the symmetric items, M^2 / 256 doubles for the
+    // 256-node blocks of the float-float and FP64 schedules, plus the target sums (a few MB)
+    const int64_t per_node = 16 * 8 + 160 + 50 * 36 + 12 * 8 + (int64_t)(m + 1) * 16;
+    const int64_t regions = M * M / 32 + ((int64_t)16 << 20);
     const int64_t grid_bytes = (int64_t)r.sdist.size() * (8 + 4);   // staging copy + node map during setup
-    return M * per_node + grid_bytes;
+    return M * per_node + regions + grid_bytes;
 }
 
 void finish_request(ctr_server* sv, Request* r, int status) {

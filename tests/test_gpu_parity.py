@@ -115,6 +115,35 @@ def test_operator_parity(which, request, ctr):
     assert np.array_equal(G.matvec(p, ctr.FP32_REFINE), y32)
 
 
+def test_operator_parity_all_rows_many_blocks(ctr, oracle_tables):
+    """Ellipsoid at h = 0.1 (~45k nodes): ~44 FP32 and ~175 float-float target blocks, so the
+    schedules hold near (one-sided, masked) items, split symmetric items and a ragged last block;
+    every row against the oracle."""
+    prob = syn.ellipsoid_problem(h=0.1)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables)
+    G = ctr.CtrIbim.from_problem(prob)
+    assert G.M == S.M > 40_000 and G.M % 1024 != 0
+    for prec in (ctr.FP32_REFINE, ctr.DF64, ctr.FP64):   # every ordered pair covered exactly once
+        sc = G.pair_schedule(prec)
+        assert sc["one_sided_pairs"] + 2 * sc["symmetric_pairs"] == G.M * G.M
+        assert sc["symmetric_pairs"] > 0.3 * G.M * G.M
+    p = syn.random_density(S.M, seed=17, smooth_points=S.geo.P)
+    ref = S.matvec(p)
+    y64 = G.matvec(p, ctr.FP64)
+    ydf = G.matvec(p, ctr.DF64)
+    y32 = G.matvec(p, ctr.FP32_REFINE)
+    assert _rel(y64, ref) < 1e-12
+    assert _rel(ydf, ref) < 1e-12
+    assert _rel(y32, ref) < 2e-5
+    # row by row too (rows below 1e-3 of the largest are measured against that floor): FP64 and
+    # float-float (about 2^-44 per operation) keep every row to the oracle's digits less the
+    # cancellation of that row's terms; FP32 keeps about 4 digits
+    for name, y, tol in (("fp64", y64, 1e-11), ("df64", ydf, 1e-10), ("fp32", y32, 1e-3)):
+        err = np.abs(y - ref) / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+        assert np.max(err) < tol, (name, float(np.max(err)))
+    G.close()
+
+
 def test_operator_device_buffers(sphere, ctr):
     import torch
     prob, S, G = sphere
@@ -261,11 +290,10 @@ def test_error_statuses(ctr):
 
 
 # ---------------------------------------------------------------- full size, sampled rows
-@pytest.mark.parametrize("tile_targets", [2])
-def test_full_size_sampled_rows(ctr, oracle_tables, tile_targets):
+def test_full_size_sampled_rows(ctr, oracle_tables):
     """Ellipsoid at h = 0.05 (~178k nodes), the benchmark's launch configuration; rows sampled."""
     prob = syn.ellipsoid_problem(h=0.05)
-    G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, tile_targets=tile_targets))
+    G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube))
     rng = np.random.Generator(np.random.PCG64(7))
     rows = np.unique(np.concatenate([[0, G.M - 1], rng.integers(0, G.M, size=46)]))
     S = OracleSystem.from_problem(prob, tables=oracle_tables, rows=rows)
