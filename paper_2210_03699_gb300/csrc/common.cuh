@@ -193,6 +193,7 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist);
 int setup_rhs(ctr_ibim* s);
 // weights.cu
 int weight_tables_device(double* d_tables, cudaStream_t st);
+int weight_tables_cached(int device, cudaStream_t st, const double** out);
 int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node_of);
 // pairsum.cu
 int plan_pairs(ctr_ibim* s);

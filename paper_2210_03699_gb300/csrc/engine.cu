@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int2* __re
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
-        if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, kc, err, sm.ring,
+        const PairConsts k = kc;   // block-uniform: a register copy keeps the pair loops free of shared loads
+        if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, k, err, sm.ring,
                                        sm.jred, sm.tab, bar, gt))
             return;
         __syncthreads();

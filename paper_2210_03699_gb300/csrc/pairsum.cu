@@ -26,6 +26,8 @@
 //   Df64  double-FP32 "float-float" terms (error-free sums and products with
 //         FMA, rsqrt by one Newton step in df64, exp by two exact tables and
 //         a degree-4 polynomial), ~2^-44 relative, on the FP32 pipe.
+#include <mutex>
+
 #include "pairkern.cuh"
 
 namespace ctr {
@@ -153,9 +155,11 @@ int resident_slots(int sms, int* slots) {
 
 // float-float table of e^{-k} (k < 64) and e^{-k/1024} (k < 1024), one per device
 int exp_table(int dev, const float2** out) {
+    static std::mutex mu;
     static DevBuf tabs[64];
     static bool ready[64] = {false};
     if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
+    std::lock_guard<std::mutex> lk(mu);
     if (!ready[dev]) {
         std::vector<float2> h(kExpHi + kExpLo);
         for (int k = 0; k < kExpHi; ++k) h[k] = split_ff(std::exp(-(double)k));

@@ -237,7 +237,7 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
     const int64_t total = s->n[0] * s->n[1] * s->n[2];
     const int64_t nchunks = (total + kChunk - 1) / kChunk;
     cudaStream_t st = s->stream;
-    DevBuf counts, offsets, node_of, tables, scratch;
+    DevBuf counts, offsets, node_of, scratch;
     CTR_TRY(counts.alloc(sizeof(int32_t) * nchunks));
     CTR_TRY(offsets.alloc(sizeof(int32_t) * (nchunks + 1)));
     tube_count_kernel<<<(unsigned)nchunks, kScanThreads, 0, st>>>(d_sdist, total, s->eps, counts.as<int32_t>());
@@ -273,10 +273,10 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
     CTR_LAUNCHED();
     CTR_TRY(check_device_error(s, "geometry"));
 
-    // correction-weight tables (Ewald), then the correction matrix
-    CTR_TRY(tables.alloc(sizeof(double) * kTabSize));
-    CTR_TRY(weight_tables_device(tables.as<double>(), st));
-    CTR_TRY(setup_corrections(s, tables.as<double>(), node_of.as<int32_t>()));
+    // correction-weight tables (Ewald, computed once per device), then the correction matrix
+    const double* tab = nullptr;
+    CTR_TRY(weight_tables_cached(s->device, st, &tab));
+    CTR_TRY(setup_corrections(s, tab, node_of.as<int32_t>()));
     CTR_CUDA_TRY(cudaStreamSynchronize(st));   // temporaries are freed on return
     return CTR_OK;
 }

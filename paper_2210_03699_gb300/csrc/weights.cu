@@ -29,6 +29,8 @@
 // (alpha, beta), the angular functions of the theorem in Sec. 2.4.1 (Eq. 2.28,
 // with kappa^2 in s0^(21)), their even Fourier coefficients by a direct DFT of
 // 64 samples, and the tensor Lagrange (degree 5) interpolation of the tables.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ctr {
@@ -360,6 +362,23 @@ int weight_tables_device(double* d_tables, cudaStream_t st) {
     const int n = kModes * kTabN * kTabN;
     ewald_tables_kernel<<<grid_for(n, 128), 128, 0, st>>>(d_tables);
     CTR_LAUNCHED();
+    return CTR_OK;
+}
+
+// The tables depend on nothing but their grid: computed once per device (complete before use).
+int weight_tables_cached(int dev, cudaStream_t st, const double** out) {
+    static std::mutex mu;
+    static DevBuf tabs[64];
+    static bool ready[64] = {false};
+    if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
+        CTR_TRY(tabs[dev].alloc(sizeof(double) * kTabSize));
+        CTR_TRY(weight_tables_device(tabs[dev].as<double>(), st));
+        CTR_CUDA_TRY(cudaStreamSynchronize(st));
+        ready[dev] = true;
+    }
+    *out = tabs[dev].as<double>();
     return CTR_OK;
 }
 
