@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 # in-warp transposed sums), for the FP32 and the float-float pair arithmetics.  SFU work (rsqrt, ex2)
 # and shared-memory loads are not counted.
 OPS_FP32 = {"one": 44, "sym": 54}
-OPS_DF64 = {"one": 507, "sym": 643}
+OPS_DF64 = {"one": 507, "sym": 501}
 
 
 def parse():

@@ -108,6 +108,22 @@ __device__ __forceinline__ F2 mul(F2 a, F2 b) {
     const F2 p = two_prod(a.hi, b.hi);
     return fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
 }
+// Lazy forms for the symmetric pair terms.  A lazy value is hi + lo with |lo|
+// a few ulp(hi) instead of at most ulp(hi)/2: it carries the same value to the
+// same accuracy, and a product of two lazy values loses only the dropped
+// lo * lo term (relative 2^-44 or less).  Results that meet a cancellation
+// (differences, 1 - E, 3 - E q) go through the normalised add, whose two_sum
+// is exact for any inputs.
+__device__ __forceinline__ F2 mull(F2 a, F2 b) {
+    const F2 p = two_prod(a.hi, b.hi);
+    return F2{p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo))};
+}
+// acc += x without renormalising acc: exact two_sum of the high parts, plain sum of the low parts
+__device__ __forceinline__ void acc_add(F2& acc, F2 x) {
+    const F2 s = two_sum(acc.hi, x.hi);
+    acc.hi = s.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
+}
 // a0 b0 + a1 b1 + a2 b2
 __device__ __forceinline__ F2 dot3(F2 a0, F2 a1, F2 a2, F2 b0, F2 b1, F2 b2) {
     const F2 p0 = two_prod(a0.hi, b0.hi), p1 = two_prod(a1.hi, b1.hi), p2 = two_prod(a2.hi, b2.hi);
@@ -144,6 +160,24 @@ __device__ __forceinline__ F2 exp_neg_ff(F2 x, const float2* tab) {
     const F2 omf = fast_two_sum(1.0f, -fh);
     const F2 ef = fast_two_sum(omf.hi, __fadd_rn(__fsub_rn(omf.lo, f.lo), q));
     return mul(mul(f2(tab[k >> 10]), f2(tab[kExpHi + (k & 1023)])), ef);
+}
+// The same with lazy products (for the symmetric pair terms).
+__device__ __forceinline__ F2 exp_neg_ffl(F2 x, const float2* tab) {
+    float xh = x.hi, xl = x.lo;
+    if (xh > 63.9f) {
+        xh = 63.9f;
+        xl = 0.f;
+    }
+    const float t = __fmaf_rn(xh, 1024.f, 12582912.f);
+    const int k = min(max(__float_as_int(t) - 0x4B400000, 0), kExpHi * kExpLo - 1);
+    const float kf = __fsub_rn(t, 12582912.f);
+    const F2 f = two_sum(__fmaf_rn(kf, -1.0f / 1024.f, xh), xl);
+    const float fh = f.hi;
+    const float poly = __fmaf_rn(__fmaf_rn(fh, 1.0f / 24.0f, -1.0f / 6.0f), fh, 0.5f);
+    const float q = __fmul_rn(__fmul_rn(fh, fh), poly);
+    const F2 omf = fast_two_sum(1.0f, -fh);
+    const F2 ef = fast_two_sum(omf.hi, __fadd_rn(__fsub_rn(omf.lo, f.lo), q));
+    return mull(mull(f2(tab[k >> 10]), f2(tab[kExpHi + (k & 1023)])), ef);
 }
 
 // ------------------------------------------------------------------ pair policies
@@ -184,6 +218,8 @@ struct Fp32Policy {
     // weights and the source's sums (ja) get K(x_j, y_i) applied to target i's weights.  With
     // d = P_i - P_j the swapped pair has d' = -d, so d'.n_j = -(d.n_j) and d'.n_i = -(d.n_i) swap
     // roles while r, E, n_i.n_j and the K21 bracket are shared: 8 extra FP32 ops for the second term.
+    // kFirst: ja holds nothing yet (first target of the thread): its terms are assigned, not added.
+    template <bool kFirst>
     __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
                                     JAcc& ja) {
         const float4 pa = S[0], nb = S[1];
@@ -213,9 +249,14 @@ struct Fp32Policy {
         acc.a2 = fmaf(bs, dnx * t2, acc.a2);
         acc.a2 = fmaf(as, X, acc.a2);
         const float ast = T.wa * s, bst = T.wb * s;
-        ja.a1 = fmaf(-ast, dnx * t1, ja.a1);
+        if constexpr (kFirst) {
+            ja.a1 = -ast * (dnx * t1);
+            ja.a2 = -bst * (dny * t2);
+        } else {
+            ja.a1 = fmaf(-ast, dnx * t1, ja.a1);
+            ja.a2 = fmaf(-bst, dny * t2, ja.a2);
+        }
         ja.a1 = fmaf(-T.wb, om, ja.a1);
-        ja.a2 = fmaf(-bst, dny * t2, ja.a2);
         ja.a2 = fmaf(ast, X, ja.a2);
     }
     template <bool kMask>
@@ -279,6 +320,7 @@ struct Fp64Policy {
     __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
         return JAcc{__shfl_xor_sync(0xffffffffu, x.a1, m), __shfl_xor_sync(0xffffffffu, x.a2, m)};
     }
+    template <bool kFirst>
     __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
                                     JAcc& ja) {
         const double4 pa = S[0], nb = S[1];
@@ -308,9 +350,14 @@ struct Fp64Policy {
         acc.a2 = fma(bs, dnx * t2, acc.a2);
         acc.a2 = fma(as, X, acc.a2);
         const double ast = T.wa * s, bst = T.wb * s;
-        ja.a1 = fma(-ast, dnx * t1, ja.a1);
+        if constexpr (kFirst) {
+            ja.a1 = -ast * (dnx * t1);
+            ja.a2 = -bst * (dny * t2);
+        } else {
+            ja.a1 = fma(-ast, dnx * t1, ja.a1);
+            ja.a2 = fma(-bst, dny * t2, ja.a2);
+        }
         ja.a1 = fma(-T.wb, om, ja.a1);
-        ja.a2 = fma(-bst, dny * t2, ja.a2);
         ja.a2 = fma(ast, X, ja.a2);
     }
     template <bool kMask>
@@ -372,7 +419,13 @@ struct Df64Policy {
         s1 += (double)c.a1.hi + (double)c.a1.lo;
         s2 += (double)c.a2.hi + (double)c.a2.lo;
     }
-    __device__ static JAcc jadd(const JAcc& x, const JAcc& y) { return JAcc{add(x.a1, y.a1), add(x.a2, y.a2)}; }
+    // unnormalised sums (exact two_sum of the high parts); the caller folds the result to FP64
+    __device__ static JAcc jadd(const JAcc& x, const JAcc& y) {
+        JAcc r = x;
+        acc_add(r.a1, y.a1);
+        acc_add(r.a2, y.a2);
+        return r;
+    }
     __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
         return JAcc{F2{__shfl_xor_sync(0xffffffffu, x.a1.hi, m), __shfl_xor_sync(0xffffffffu, x.a1.lo, m)},
                     F2{__shfl_xor_sync(0xffffffffu, x.a2.hi, m), __shfl_xor_sync(0xffffffffu, x.a2.lo, m)}};
@@ -415,6 +468,9 @@ struct Df64Policy {
         const F2 Bt = mul(mul(t3, mul(dnx, dny)), rinv2);
         acc.a2 = add(acc.a2, mul(as, sub(mul(u, nn), Bt)));
     }
+    // Both orientations with lazy products (mull) and unnormalised accumulation (acc_add); the
+    // differences that can cancel (d, the dot products, 1 - E, 1 - E1, 3 - E q, X) stay normalised.
+    template <bool kFirst>
     __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2* tab, Acc& acc,
                                     JAcc& ja) {
         const float4 s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3];
@@ -423,33 +479,38 @@ struct Df64Policy {
         const F2 dx = sub(T.px, Px), dy = sub(T.py, Py), dz = sub(T.pz, Pz);
         const F2 r2 = dot3(dx, dy, dz, dx, dy, dz);
         const F2 rinv = rsqrt_ff(r2);
-        const F2 r = mul(r2, rinv);
-        const F2 kr = mul(f2(k.kappad), r);
-        const F2 E = exp_neg_ff(kr, tab);
-        const F2 E1 = mul(E, add_f(kr, 1.f));
+        const F2 r = mull(r2, rinv);
+        const F2 kr = mull(f2(k.kappad), r);
+        const F2 E = exp_neg_ffl(kr, tab);
+        const F2 E1 = mull(E, add_f(kr, 1.f));
         const F2 dny = dot3(dx, dy, dz, Nx, Ny, Nz);
         const F2 dnx = dot3(dx, dy, dz, T.qx, T.qy, T.qz);
         const F2 nn = dot3(T.qx, T.qy, T.qz, Nx, Ny, Nz);
-        const F2 rinv2 = mul(rinv, rinv);
-        const F2 s = mul(rinv2, rinv);
-        const F2 t1 = add_f(neg(mul(E1, f2(k.c1d))), 1.f);
-        const F2 om = mul(rinv, add_f(neg(E), 1.f));
-        const F2 t2 = add_f(neg(mul(E1, f2(k.c2d))), 1.f);
+        const F2 rinv2 = mull(rinv, rinv);
+        const F2 s = mull(rinv2, rinv);
+        const F2 t1 = add_f(neg(mull(E1, f2(k.c1d))), 1.f);
+        const F2 om = mull(rinv, add_f(neg(E), 1.f));
+        const F2 t2 = add_f(neg(mull(E1, f2(k.c2d))), 1.f);
         const F2 u = add_f(neg(E1), 1.f);
-        const F2 q = add_f(mul(kr, add_f(kr, 3.f)), 3.f);
-        const F2 t3 = add_f(neg(mul(E, q)), 3.f);
-        const F2 Bt = mul(mul(t3, mul(dnx, dny)), rinv2);
-        const F2 X = sub(mul(u, nn), Bt);
-        const F2 as = mul(A, s), bs = mul(Bw, s);
-        acc.a1 = add(acc.a1, mul(as, mul(dny, t1)));
-        acc.a1 = sub(acc.a1, mul(Bw, om));
-        acc.a2 = add(acc.a2, mul(bs, mul(dnx, t2)));
-        acc.a2 = add(acc.a2, mul(as, X));
-        const F2 ast = mul(T.wa, s), bst = mul(T.wb, s);
-        ja.a1 = sub(ja.a1, mul(ast, mul(dnx, t1)));
-        ja.a1 = sub(ja.a1, mul(T.wb, om));
-        ja.a2 = sub(ja.a2, mul(bst, mul(dny, t2)));
-        ja.a2 = add(ja.a2, mul(ast, X));
+        const F2 q = add_f(mull(kr, add_f(kr, 3.f)), 3.f);
+        const F2 t3 = add_f(neg(mull(E, q)), 3.f);
+        const F2 Bt = mull(mull(t3, mull(dnx, dny)), rinv2);
+        const F2 X = sub(mull(u, nn), Bt);
+        const F2 as = mull(A, s), bs = mull(Bw, s);
+        acc_add(acc.a1, mull(as, mull(dny, t1)));
+        acc_add(acc.a1, neg(mull(Bw, om)));
+        acc_add(acc.a2, mull(bs, mull(dnx, t2)));
+        acc_add(acc.a2, mull(as, X));
+        const F2 ast = mull(T.wa, s), bst = mull(T.wb, s);
+        if constexpr (kFirst) {
+            ja.a1 = neg(mull(ast, mull(dnx, t1)));
+            ja.a2 = neg(mull(bst, mull(dny, t2)));
+        } else {
+            acc_add(ja.a1, neg(mull(ast, mull(dnx, t1))));
+            acc_add(ja.a2, neg(mull(bst, mull(dny, t2))));
+        }
+        acc_add(ja.a1, neg(mull(T.wb, om)));
+        acc_add(ja.a2, mull(ast, X));
     }
 };
 
@@ -667,17 +728,20 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
                 if (c0 + V <= n) {
 #pragma unroll
                     for (int q = 0; q < V; ++q) {
+                        Policy::template pair_sym<true>(tg[0], tile + (c0 + q) * VEC, kc, tab, acc[0], ja[q]);
 #pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            Policy::pair_sym(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], ja[q]);
+                        for (int r = 1; r < R; ++r)
+                            Policy::template pair_sym<false>(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], ja[q]);
                     }
                 } else {   // ragged end of the item: warp-uniform skip
 #pragma unroll
                     for (int q = 0; q < V; ++q) {
                         if (c0 + q < n) {
+                            Policy::template pair_sym<true>(tg[0], tile + (c0 + q) * VEC, kc, tab, acc[0], ja[q]);
 #pragma unroll
-                            for (int r = 0; r < R; ++r)
-                                Policy::pair_sym(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], ja[q]);
+                            for (int r = 1; r < R; ++r)
+                                Policy::template pair_sym<false>(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r],
+                                                                 ja[q]);
                         }
                     }
                 }
@@ -691,9 +755,10 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
                         Policy::zero(cur[t]);
                         const int q = c0 + q0 + t;
                         if (q < n) {   // warp-uniform
+                            Policy::template pair_sym<true>(tg[0], tile + q * VEC, kc, tab, acc[0], cur[t]);
 #pragma unroll
-                            for (int r = 0; r < R; ++r)
-                                Policy::pair_sym(tg[r], tile + q * VEC, kc, tab, acc[r], cur[t]);
+                            for (int r = 1; r < R; ++r)
+                                Policy::template pair_sym<false>(tg[r], tile + q * VEC, kc, tab, acc[r], cur[t]);
                         }
                     }
 #pragma unroll
