@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the baseline sample")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels"],
                     help="solve: the default single-system line; batch: many molecules in one engine; "
-                         "serve: continuous-batching server under Poisson arrivals")
+                         "serve: continuous-batching server under Poisson arrivals; kernels: two FP32 and two "
+                         "float-float operator applications of the ellipsoid at --h (the profiling case)")
     ap.add_argument("--molecules", type=int, default=64, help="batch mode: molecules in the batch")
     ap.add_argument("--max-atoms", type=int, default=2000, help="batch/serve: largest molecule")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per load level")
@@ -358,18 +359,40 @@ def run_serve(args, ctr):
     print(json.dumps(line), flush=True)
 
 
+def run_kernels(args, ctr):
+    """Two FP32 and two float-float operator applications (first warms up), timed with events."""
+    import torch
+    prob, cfg = workload(args.h)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "kernels", "config": cfg}
+    with ctr.CtrIbim.from_problem(prob) as G:
+        x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, 2 * G.M), device="cuda")
+        y = torch.empty_like(x)
+        out["M"] = G.M
+        for pr, name in ((ctr.FP32_REFINE, "fp32"), (ctr.DF64, "df64")):
+            G.matvec(x, pr, out=y)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.matvec(x, pr, out=y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = dict(G.pair_schedule(pr), t_matvec_ms=e0.elapsed_time(e1))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.mode in ("batch", "serve"):
+    if args.mode in ("batch", "serve", "kernels"):
         import torch
         torch.cuda.set_device(local)
         import paper_2210_03699_gb300 as ctr
         if rank == 0:
-            (run_batch if args.mode == "batch" else run_serve)(args, ctr)
+            {"batch": run_batch, "serve": run_serve, "kernels": run_kernels}[args.mode](args, ctr)
         return
     import torch
     torch.cuda.set_device(local)

@@ -133,7 +133,7 @@ struct PairSchedule {
     int nb = 0;           // target blocks
     int64_t part_doubles = 0;
     int64_t pairs_sym = 0, pairs_one = 0;   // evaluated pair orientations of each kind
-    std::vector<PairItem> items;
+    std::vector<PairItem> items;   // in the order of d_items (decreasing cost)
     std::vector<double> cost;
     DevBuf d_items, d_rptr, d_recs;
 };

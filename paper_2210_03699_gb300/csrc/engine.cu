@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -103,12 +104,14 @@ __global__ void k_update_x(SlotDev* S) {
 }
 
 // ---------------------------------------------------------------- persistent pair kernels
-// Work entries (slot, item of that slot's schedule), sorted by decreasing cost.
-template <typename Policy, int R, int V, int U>
+// Work entries (slot, item of that slot's schedule), sorted by decreasing cost.  kShared: every slot
+// of this arithmetic has the same pair constants, passed as the launch parameter `pkc` (read from the
+// constant bank, no registers); otherwise each item takes its slot's constants.
+template <typename Policy, int R, int V, int U, bool kShared>
 __global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int2* __restrict__ items,
                                                     const int* __restrict__ n_items, int* __restrict__ counter,
                                                     int half, int prec, int pol, const float2* __restrict__ exp_tab,
-                                                    int* __restrict__ err) {
+                                                    int* __restrict__ err, const PairConsts pkc) {
     using Src = typename Policy::Src;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PairSmem<Policy> sm(smem_raw);
@@ -131,19 +134,25 @@ __global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int2* __re
         const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec)
                                     : (update_active(s) && s.res_prec == prec);
         if (!want) continue;
-        if (threadIdx.x == 0) {
-            const float2* t = kc.exp_tab;
-            kc = s.kc;
-            kc.exp_tab = t;
-        }
-        __syncthreads();
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
-        const PairConsts k = kc;   // block-uniform: a register copy keeps the pair loops free of shared loads
-        if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, k, err, sm.ring,
-                                       sm.jred, sm.tab, bar, gt))
-            return;
+        if constexpr (kShared) {
+            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, pkc, err, sm.ring,
+                                           sm.jred, sm.tab, bar, gt))
+                return;
+        } else {
+            if (threadIdx.x == 0) {
+                const float2* t = kc.exp_tab;
+                kc = s.kc;
+                kc.exp_tab = t;
+            }
+            __syncthreads();
+            const PairConsts k = kc;   // block-uniform register copy: no shared loads in the pair loops
+            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, k, err, sm.ring,
+                                           sm.jred, sm.tab, bar, gt))
+                return;
+        }
         __syncthreads();
     }
 }
@@ -351,20 +360,27 @@ __global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
     if (q < cap) out[q] = S[q].stat;
 }
 
-template <typename Policy, int R, int V, int U>
-int launch_persistent(Engine* e, int pol, int half, int prec) {
+template <typename Policy, int R, int V, int U, bool kShared>
+int launch_persistent_k(Engine* e, int pol, int half, int prec) {
     const size_t smem = pair_smem_bytes<Policy>();
     static int per_sm = 0;   // resident blocks of this instantiation (same on every GB300)
     if (per_sm == 0) {
         int b = 0;
-        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs<Policy, R, V, U>, kThreads, smem));
+        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs<Policy, R, V, U, kShared>, kThreads,
+                                                                   smem));
         per_sm = std::max(1, b);
     }
-    k_pairs<Policy, R, V, U><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
+    k_pairs<Policy, R, V, U, kShared><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
         e->slots.as<SlotDev>(), e->items[pol].as<int2>(), e->n_items.as<int>() + pol,
-        e->counters.as<int>() + 2 * pol + half, half, prec, pol, e->exp_tab, e->err.as<int>());
+        e->counters.as<int>() + 2 * pol + half, half, prec, pol, e->exp_tab, e->err.as<int>(), e->kc_val[pol]);
     CTR_LAUNCHED();
     return CTR_OK;
+}
+
+template <typename Policy, int R, int V, int U>
+int launch_persistent(Engine* e, int pol, int half, int prec) {
+    return e->kc_shared[pol] ? launch_persistent_k<Policy, R, V, U, true>(e, pol, half, prec)
+                             : launch_persistent_k<Policy, R, V, U, false>(e, pol, half, prec);
 }
 
 int launch_fp32(Engine* e, int half) {
@@ -463,6 +479,28 @@ static int rebuild_items(Engine* e) {
             for (size_t k = 0; k < sc.items.size(); ++k) list.push_back(It{make_int2(q, (int)k), sc.cost[k]});
         }
         std::stable_sort(list.begin(), list.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+        // one set of pair constants for every slot of this arithmetic: pass it as a launch parameter
+        bool shared = true, any = false;
+        PairConsts val{};
+        for (int q = 0; q < e->cap && shared; ++q) {
+            if (!e->owner[q]) continue;
+            const SlotDev& s = e->host[q];
+            if (policy_index(s.inner_prec) != p && policy_index(s.res_prec) != p) continue;
+            PairConsts c = s.kc;
+            c.exp_tab = e->exp_tab;
+            if (!any) {
+                val = c;
+                any = true;
+            } else if (std::memcmp(&val, &c, sizeof(PairConsts)) != 0) {
+                shared = false;
+            }
+        }
+        if (!any) val.exp_tab = e->exp_tab;
+        if (shared != e->kc_shared[p] || std::memcmp(&val, &e->kc_val[p], sizeof(PairConsts)) != 0) {
+            e->kc_shared[p] = shared;
+            e->kc_val[p] = val;
+            e->graph_dirty = true;   // the captured launches carry the constants
+        }
         std::vector<int2> v(list.size());
         for (size_t i = 0; i < list.size(); ++i) v[i] = list[i].v;
         if ((int64_t)v.size() > e->item_cap[p]) {

@@ -69,6 +69,8 @@ struct Engine {
     bool autotune = true;     // choose var32 by timing at the first step
     bool tuned = false;
     const float2* exp_tab = nullptr;
+    bool kc_shared[3] = {false, false, false};   // all slots of an arithmetic share their pair constants
+    pk::PairConsts kc_val[3] = {};               // ... and these are they (launch parameter)
     std::vector<SlotDev> host;
     std::vector<ctr_ibim*> owner;
     DevBuf slots, stats, items[3], n_items, counters, err;

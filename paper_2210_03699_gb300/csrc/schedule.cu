@@ -186,7 +186,8 @@ void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost,
     p.part_doubles = off;
 }
 
-// Device copies: items sorted by decreasing cost, region lists per block in item order.
+// Device copies: region lists per block in item creation order, items sorted by decreasing cost
+// (afterwards the host copy is in that sorted order too).
 int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
     const int nb = p.nb;
     std::vector<std::vector<PairRec>> per(nb);
@@ -207,7 +208,11 @@ int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p.cost[a] > p.cost[b]; });
     std::vector<PairItem> sorted(p.items.size());
-    for (size_t k = 0; k < order.size(); ++k) sorted[k] = p.items[order[k]];
+    std::vector<double> sorted_cost(p.items.size());
+    for (size_t k = 0; k < order.size(); ++k) {
+        sorted[k] = p.items[order[k]];
+        sorted_cost[k] = p.cost[order[k]];
+    }
     CTR_TRY(p.d_items.alloc(sizeof(PairItem) * std::max<size_t>(1, sorted.size())));
     CTR_TRY(p.d_rptr.alloc(sizeof(int32_t) * rptr.size()));
     CTR_TRY(p.d_recs.alloc(sizeof(PairRec) * std::max<size_t>(1, recs.size())));
@@ -219,6 +224,9 @@ int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
         CTR_CUDA_TRY(
             cudaMemcpyAsync(p.d_recs.p, recs.data(), sizeof(PairRec) * recs.size(), cudaMemcpyHostToDevice, st));
     CTR_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+    // the host copy follows the device order: the engine's work entries index the device list
+    p.items.swap(sorted);
+    p.cost.swap(sorted_cost);
     (void)M;
     return CTR_OK;
 }
