@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 # and shared-memory loads are not counted.
 OPS_FP32 = {"one": 44, "sym": 54}
 OPS_DF64 = {"one": 507, "sym": 501}
+# DRAM bytes (read + write) per launch of the schedule kernels at the default workload (h = 0.05), from one
+# ncu capture (profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt); None at any other size, or once
+# the kernels change.
+TRAFFIC_H005 = {"fp32": 2.185e8, "df64": 1.0471e9}
 
 
 def parse():
@@ -464,21 +468,21 @@ def main():
     rate_ex2 = ctypes_probe(ctr, 2)
     rate_dfma = ctypes_probe(ctr, 4)
 
-    def roof(pr, ops, name):
+    def roof(pr, ops, name, key):
         sc = sched[pr]
         n_ops = ops["one"] * sc["one_sided_pairs"] + ops["sym"] * sc["symmetric_pairs"]
         peak = rate_ffma * Mk * Mk / n_ops
         ach = Mk * Mk / t_mv[pr]
         return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "pair-interactions/s",
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak, "traffic": TRAFFIC_H005[key] if abs(args.h - 0.05) < 1e-12 else None,
                 "peak_basis": f"measured FFMA rate {rate_ffma:.4g}/s x M^2 / FP32-pipe ops of the schedule "
                               f"({ops['one']} per one-sided and {ops['sym']} per symmetric pair evaluation)",
                 "t_matvec_ms": t_mv[pr] * 1e3, "one_sided_pairs": sc["one_sided_pairs"],
                 "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"]}
 
     i_last = infos[-1]
-    r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32Policy> (FP32 pair sum, inner GMRES)")
-    rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)")
+    r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32Policy> (FP32 pair sum, inner GMRES)", "fp32")
+    rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)", "df64")
     share32 = i_last.matvecs_fp32 * t_mv[ctr.FP32_REFINE]
     sharedf = i_last.matvecs_fp64 * t_mv[ctr.DF64]
     dominant, other = (rdf, r32) if sharedf >= share32 else (r32, rdf)
