@@ -30,16 +30,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# FP32-pipe instructions per pair evaluation, counted from the kernel source (see the design notes):
+# FP32-pipe lane operations per pair evaluation, counted from the kernel source (see the design notes):
 # one-sided evaluations (one orientation) and symmetric ones (both orientations, with the share of the
-# in-warp transposed sums), for the FP32 and the float-float pair arithmetics.  SFU work (rsqrt, ex2)
-# and shared-memory loads are not counted.
-OPS_FP32 = {"one": 44, "sym": 54}
+# in-warp transposed sums), for the packed FP32 and the float-float pair arithmetics (a packed f32x2
+# instruction counts as two lane operations, the FMA pipe's throughput being the same either way).
+# SFU work (rsqrt, ex2) and shared-memory loads are not counted.
+OPS_FP32 = {"one": 41, "sym": 50}
 OPS_DF64 = {"one": 507, "sym": 501}
 # DRAM bytes (read + write) per launch of the schedule kernels at the default workload (h = 0.05), from one
 # ncu capture (profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt); None at any other size, or once
 # the kernels change.
-TRAFFIC_H005 = {"fp32": 2.185e8, "df64": 1.0471e9}
+TRAFFIC_H005 = {"fp32": None, "df64": 1.0471e9}
 
 
 def parse():
@@ -481,7 +482,7 @@ def main():
                 "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"]}
 
     i_last = infos[-1]
-    r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32Policy> (FP32 pair sum, inner GMRES)", "fp32")
+    r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32x2Policy> (packed FP32 pair sum, inner GMRES)", "fp32")
     rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)", "df64")
     share32 = i_last.matvecs_fp32 * t_mv[ctr.FP32_REFINE]
     sharedf = i_last.matvecs_fp64 * t_mv[ctr.DF64]

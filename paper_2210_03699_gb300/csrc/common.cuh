@@ -167,7 +167,7 @@ struct ctr_ibim {
     ctr::DevBuf lin;         // int64 [M] grid index
     ctr::DevBuf nodes;       // double [16][M]
     ctr::NodeArrays na{};
-    ctr::DevBuf src32;       // float4 [2M]: {P, a} {n, b}
+    ctr::DevBuf src32;       // float4 [4M]: {x,x,y,y} {z,z,a,a} {nx,nx,ny,ny} {nz,nz,-b,-b} (f32x2 operands)
     ctr::DevBuf src64;       // double4 [2M]
     ctr::DevBuf srcdf;       // float4 [4M]: float-float {P.hi, a.hi} {P.lo, a.lo} {n.hi, b.hi} {n.lo, b.lo}
     ctr::DevBuf corr_ptr;    // int32 [M+1]

@@ -56,8 +56,8 @@ __device__ __forceinline__ bool update_active(const SlotDev& s) { return s.stat.
 // ---------------------------------------------------------------- packing
 __device__ __forceinline__ void pack_weights(const SlotDev& s, int prec, int64_t t, double a, double b) {
     if (prec == CTR_FP32_REFINE) {
-        s.src32[2 * t].w = (float)a;
-        s.src32[2 * t + 1].w = (float)b;
+        s.src32[4 * t + 1].z = s.src32[4 * t + 1].w = (float)a;   // duplicated pairs: a and -b
+        s.src32[4 * t + 3].z = s.src32[4 * t + 3].w = -(float)b;
     } else if (prec == CTR_FP64) {
         s.src64[2 * t].w = a;
         s.src64[2 * t + 1].w = b;
@@ -108,7 +108,7 @@ __global__ void k_update_x(SlotDev* S) {
 // of this arithmetic has the same pair constants, passed as the launch parameter `pkc` (read from the
 // constant bank, no registers); otherwise each item takes its slot's constants.
 template <typename Policy, int R, int V, int U, bool kShared>
-__global__ void __launch_bounds__(kThreads) k_pairs(SlotDev* S, const int2* __restrict__ items,
+__global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* __restrict__ items,
                                                     const int* __restrict__ n_items, int* __restrict__ counter,
                                                     int half, int prec, int pol, const float2* __restrict__ exp_tab,
                                                     int* __restrict__ err, const PairConsts pkc) {
@@ -363,9 +363,16 @@ __global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
 template <typename Policy, int R, int V, int U, bool kShared>
 int launch_persistent_k(Engine* e, int pol, int half, int prec) {
     const size_t smem = pair_smem_bytes<Policy>();
-    static int per_sm = 0;   // resident blocks of this instantiation (same on every GB300)
+    static int per_dev[64] = {0};   // resident blocks of this instantiation, per device (attribute set there)
+    int dev = 0;
+    CTR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
+    int& per_sm = per_dev[dev];
     if (per_sm == 0) {
         int b = 0;
+        // dynamic shared memory above the default 48 KB per block needs the kernel's opt-in
+        CTR_CUDA_TRY(cudaFuncSetAttribute(k_pairs<Policy, R, V, U, kShared>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs<Policy, R, V, U, kShared>, kThreads,
                                                                    smem));
         per_sm = std::max(1, b);
@@ -385,10 +392,10 @@ int launch_persistent(Engine* e, int pol, int half, int prec) {
 
 int launch_fp32(Engine* e, int half) {
     switch (e->var32) {
-        case 1: return launch_persistent<Fp32Policy, kR32, 4, 1>(e, 0, half, CTR_FP32_REFINE);
-        case 2: return launch_persistent<Fp32Policy, kR32, 8, 2>(e, 0, half, CTR_FP32_REFINE);
-        case 3: return launch_persistent<Fp32Policy, kR32, 4, 2>(e, 0, half, CTR_FP32_REFINE);
-        default: return launch_persistent<Fp32Policy, kR32, 8, 1>(e, 0, half, CTR_FP32_REFINE);
+        case 1: return launch_persistent<Fp32x2Policy, kR32, 4, 1>(e, 0, half, CTR_FP32_REFINE);
+        case 2: return launch_persistent<Fp32x2Policy, kR32, 8, 2>(e, 0, half, CTR_FP32_REFINE);
+        case 3: return launch_persistent<Fp32x2Policy, kR32, 4, 2>(e, 0, half, CTR_FP32_REFINE);
+        default: return launch_persistent<Fp32x2Policy, kR32, 8, 1>(e, 0, half, CTR_FP32_REFINE);
     }
 }
 

@@ -19,6 +19,8 @@ struct PairConsts {
     double c1, c2, kappa;
     float2 c1d, c2d, kappad;         // float-float copies
     const float2* exp_tab;           // [kExpHi + kExpLo] float-float, global
+    // the FP32 values duplicated into both halves of a 64-bit word (f32x2 operands)
+    unsigned long long one2, mone2, three2, mthree2, c1x2, nc1x2, c2x2, nc2x2, kap2, kl2x2;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -71,6 +73,49 @@ __device__ __forceinline__ float ex2_sfu(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// ------------------------------------------------------------------ f32x2 arithmetic
+// Two FP32 values in one 64-bit register pair, one IEEE round-to-nearest operation per half
+// (add/sub/mul/fma.rn.f32x2): half the issue slots of two scalar instructions.
+using u64 = unsigned long long;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ void up2(u64 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {   // a * b + c
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 rsqrt2(u64 v) {
+    float a, b;
+    up2(v, a, b);
+    return pk2(rsqrt_sfu(a), rsqrt_sfu(b));
+}
+__device__ __forceinline__ u64 ex2_2(u64 v) {
+    float a, b;
+    up2(v, a, b);
+    return pk2(ex2_sfu(a), ex2_sfu(b));
 }
 
 // ------------------------------------------------------------------ float-float arithmetic
@@ -199,7 +244,10 @@ struct Fp32Policy {
     struct Acc {
         float a1, a2;
     };
-    using JAcc = Acc;   // source-side (transposed) sums of a symmetric tile
+    using JAcc = Acc;
+    using JAccR = Acc;                  // source-side sums while a source meets the thread's targets
+    static constexpr int kPack = 1;     // targets per thread slot
+    __device__ static JAcc jfinal(const JAccR& a) { return a; }   // source-side (transposed) sums of a symmetric tile
     __device__ static Tgt load(const Src* src, int t) {
         const float4 a = src[2 * t], b = src[2 * t + 1];
         return Tgt{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
@@ -260,7 +308,8 @@ struct Fp32Policy {
         ja.a2 = fmaf(ast, X, ja.a2);
     }
     template <bool kMask>
-    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, bool ex) {
+    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, const bool* exv) {
+        const bool ex = exv[0];
         float4 pa = S[0], nb = S[1];
         if (kMask && ex) {   // excluded correction pair: a zero-weight source at distance 1
             pa = make_float4(T.px + 1.f, T.py, T.pz, 0.f);
@@ -293,6 +342,167 @@ struct Fp32Policy {
     }
 };
 
+// Packed FP32: the Fp32 terms for two targets at once (lanes of f32x2 operations).  A thread slot
+// holds targets a, b (lanes x, y); a source node is stored with every value duplicated,
+// {(x,x),(y,y)} {(z,z),(a,a)} {(nx,nx),(ny,ny)} {(nz,nz),(-b,-b)} (64 B), so a broadcast
+// shared-memory load gives ready operands.  Signs are arranged so that every step is a plain
+// add/sub/mul or a*b + c (the f32x2 forms take no negated operands):
+//   t1 = 1 - c1 E1, t1n = -t1, t2 = 1 - c2 E1, t2n = -t2, om = (1 - E)/r, u = 1 - E1,
+//   t3n = E q - 3, Bn = t3n (d.n_x)(d.n_y)/r^2, X = u n_x.n_y + Bn,
+//   target rows: a1 += a s (d.n_y) t1 + (-b) om,   a2 += (-b s)(d.n_x) t2n + a s X;
+//   source rows: a1 += ((-a_t) s)(d.n_x) t1 + (-b_t) om,
+//                -a2 += ((-b_t) s)(d.n_y) t2n + ((-a_t) s) X   (negated; jfinal restores the sign).
+struct Fp32x2Policy {
+    using Src = ulonglong2;
+    static constexpr int kVec = 4;      // Src per node (64 B)
+    static constexpr int kTile = 256;   // nodes per tile (16 KB)
+    static constexpr bool kTables = false;
+    static constexpr int kSymStep = 32;
+    static constexpr int kPack = 2;
+    struct Tgt {
+        u64 px, py, pz, qx, qy, qz, nwa, nwb;
+    };
+    struct Acc {
+        u64 a1, a2;
+    };
+    struct JAcc {
+        float a1, a2;
+    };
+    using JAccR = Acc;
+    __device__ static JAcc jfinal(const JAccR& j) {
+        float x0, x1, y0, y1;
+        up2(j.a1, x0, x1);
+        up2(j.a2, y0, y1);
+        return JAcc{x0 + x1, -(y0 + y1)};
+    }
+    __device__ static Tgt load_pack(const Src* src, int M, const int* ti) {
+        float v[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = min(ti[h], M - 1);
+            const ulonglong2 a = src[4 * t], b = src[4 * t + 1], c = src[4 * t + 2], d = src[4 * t + 3];
+            float dummy;
+            up2(a.x, v[h][0], dummy);
+            up2(a.y, v[h][1], dummy);
+            up2(b.x, v[h][2], dummy);
+            up2(b.y, v[h][6], dummy);   // a
+            up2(c.x, v[h][3], dummy);
+            up2(c.y, v[h][4], dummy);
+            up2(d.x, v[h][5], dummy);
+            up2(d.y, v[h][7], dummy);   // -b
+            v[h][6] = -v[h][6];                        // -a
+            if (ti[h] >= M) v[h][6] = v[h][7] = 0.f;   // a padding target adds nothing to the sources
+        }
+        return Tgt{pk2(v[0][0], v[1][0]), pk2(v[0][1], v[1][1]), pk2(v[0][2], v[1][2]), pk2(v[0][3], v[1][3]),
+                   pk2(v[0][4], v[1][4]), pk2(v[0][5], v[1][5]), pk2(v[0][6], v[1][6]), pk2(v[0][7], v[1][7])};
+    }
+    __device__ static void zero(Acc& c) { c.a1 = c.a2 = 0ull; }
+    __device__ static void zero(JAcc& c) { c.a1 = c.a2 = 0.f; }
+    __device__ static void fold_pack(const Acc& c, double* s1, double* s2) {
+        float x0, x1, y0, y1;
+        up2(c.a1, x0, x1);
+        up2(c.a2, y0, y1);
+        s1[0] += (double)x0;
+        s1[1] += (double)x1;
+        s2[0] += (double)y0;
+        s2[1] += (double)y1;
+    }
+    __device__ static void fold(const JAcc& c, double& s1, double& s2) {
+        s1 += (double)c.a1;
+        s2 += (double)c.a2;
+    }
+    __device__ static JAcc jadd(const JAcc& x, const JAcc& y) { return JAcc{x.a1 + y.a1, x.a2 + y.a2}; }
+    __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
+        return JAcc{__shfl_xor_sync(0xffffffffu, x.a1, m), __shfl_xor_sync(0xffffffffu, x.a2, m)};
+    }
+    // The terms shared by both orientations for the two targets of T and source S.
+    struct Common {
+        u64 dnx, dny, om, t1, t2n, X, s;
+    };
+    __device__ static Common common(const Tgt& T, u64 Sx, u64 Sy, u64 Sz, u64 Nx, u64 Ny, u64 Nz,
+                                    const PairConsts& k) {
+        const u64 dx = sub2(T.px, Sx), dy = sub2(T.py, Sy), dz = sub2(T.pz, Sz);
+        const u64 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const u64 rinv = rsqrt2(r2);
+        const u64 r = mul2(r2, rinv);
+        const u64 E = ex2_2(mul2(k.kl2x2, r));
+        const u64 kr = mul2(k.kap2, r);
+        const u64 E1 = fma2(E, kr, E);
+        Common c;
+        c.dny = fma2(dz, Nz, fma2(dy, Ny, mul2(dx, Nx)));
+        c.dnx = fma2(dz, T.qz, fma2(dy, T.qy, mul2(dx, T.qx)));
+        const u64 nn = fma2(T.qz, Nz, fma2(T.qy, Ny, mul2(T.qx, Nx)));
+        const u64 rinv2 = mul2(rinv, rinv);
+        c.s = mul2(rinv2, rinv);
+        c.t1 = fma2(k.nc1x2, E1, k.one2);
+        c.t2n = fma2(k.c2x2, E1, k.mone2);
+        c.om = mul2(rinv, sub2(k.one2, E));
+        const u64 u = sub2(k.one2, E1);
+        const u64 q = fma2(kr, add2(kr, k.three2), k.three2);
+        const u64 t3n = fma2(E, q, k.mthree2);
+        const u64 Bn = mul2(mul2(mul2(t3n, c.dnx), c.dny), rinv2);
+        c.X = fma2(u, nn, Bn);
+        return c;
+    }
+    __device__ static void target_terms(const Common& c, u64 Sa, u64 Snb, Acc& acc) {
+        const u64 as = mul2(Sa, c.s), nbs = mul2(Snb, c.s);
+        acc.a1 = fma2(mul2(as, c.dny), c.t1, acc.a1);
+        acc.a1 = fma2(Snb, c.om, acc.a1);
+        acc.a2 = fma2(mul2(nbs, c.dnx), c.t2n, acc.a2);
+        acc.a2 = fma2(as, c.X, acc.a2);
+    }
+    template <bool kMask>
+    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
+                                const bool* ex) {
+        const ulonglong2 v0 = S[0], v1 = S[1], v2 = S[2], v3 = S[3];
+        u64 Sx = v0.x, Sy = v0.y, Sz = v1.x, Sa = v1.y, Snb = v3.y;
+        if (kMask && (ex[0] || ex[1])) {   // excluded correction pair: a zero-weight source at distance 1
+            float x[2], y[2], z[2], a[2], b[2], tx[2], ty[2], tz[2];
+            up2(Sx, x[0], x[1]);
+            up2(Sy, y[0], y[1]);
+            up2(Sz, z[0], z[1]);
+            up2(Sa, a[0], a[1]);
+            up2(Snb, b[0], b[1]);
+            up2(T.px, tx[0], tx[1]);
+            up2(T.py, ty[0], ty[1]);
+            up2(T.pz, tz[0], tz[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (ex[h]) {
+                    x[h] = tx[h] + 1.f;
+                    y[h] = ty[h];
+                    z[h] = tz[h];
+                    a[h] = b[h] = 0.f;
+                }
+            }
+            Sx = pk2(x[0], x[1]);
+            Sy = pk2(y[0], y[1]);
+            Sz = pk2(z[0], z[1]);
+            Sa = pk2(a[0], a[1]);
+            Snb = pk2(b[0], b[1]);
+        }
+        const Common c = common(T, Sx, Sy, Sz, v2.x, v2.y, v3.x, k);
+        target_terms(c, Sa, Snb, acc);
+    }
+    template <bool kFirst>
+    __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
+                                    JAccR& ja) {
+        const ulonglong2 v0 = S[0], v1 = S[1], v2 = S[2], v3 = S[3];
+        const Common c = common(T, v0.x, v0.y, v1.x, v2.x, v2.y, v3.x, k);
+        target_terms(c, v1.y, v3.y, acc);
+        const u64 nwas = mul2(T.nwa, c.s), nwbs = mul2(T.nwb, c.s);
+        if constexpr (kFirst) {
+            ja.a1 = mul2(mul2(nwas, c.dnx), c.t1);
+            ja.a2 = mul2(mul2(nwbs, c.dny), c.t2n);   // ja.a2 holds -a2 until jfinal
+        } else {
+            ja.a1 = fma2(mul2(nwas, c.dnx), c.t1, ja.a1);
+            ja.a2 = fma2(mul2(nwbs, c.dny), c.t2n, ja.a2);
+        }
+        ja.a1 = fma2(T.nwb, c.om, ja.a1);
+        ja.a2 = fma2(nwas, c.X, ja.a2);
+    }
+};
+
 struct Fp64Policy {
     using Src = double4;
     static constexpr int kVec = 2;
@@ -306,6 +516,9 @@ struct Fp64Policy {
         double a1, a2;
     };
     using JAcc = Acc;
+    using JAccR = Acc;                  // source-side sums while a source meets the thread's targets
+    static constexpr int kPack = 1;     // targets per thread slot
+    __device__ static JAcc jfinal(const JAccR& a) { return a; }
     __device__ static Tgt load(const Src* src, int t) {
         const double4 a = src[2 * t], b = src[2 * t + 1];
         return Tgt{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
@@ -361,7 +574,8 @@ struct Fp64Policy {
         ja.a2 = fma(ast, X, ja.a2);
     }
     template <bool kMask>
-    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, bool ex) {
+    __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, const bool* exv) {
+        const bool ex = exv[0];
         double4 pa = S[0], nb = S[1];
         if (kMask && ex) {
             pa = make_double4(T.px + 1.0, T.py, T.pz, 0.0);
@@ -408,6 +622,9 @@ struct Df64Policy {
         F2 a1, a2;
     };
     using JAcc = Acc;
+    using JAccR = Acc;                  // source-side sums while a source meets the thread's targets
+    static constexpr int kPack = 1;     // targets per thread slot
+    __device__ static JAcc jfinal(const JAccR& a) { return a; }
     __device__ static Tgt load(const Src* src, int t) {
         const float4 a = src[4 * t], b = src[4 * t + 1], c = src[4 * t + 2], d = src[4 * t + 3];
         return Tgt{F2{a.x, b.x}, F2{a.y, b.y}, F2{a.z, b.z}, F2{c.x, d.x}, F2{c.y, d.y}, F2{c.z, d.z},
@@ -432,7 +649,8 @@ struct Df64Policy {
     }
     template <bool kMask>
     __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2* tab, Acc& acc,
-                                bool ex) {
+                                const bool* exv) {
+        const bool ex = exv[0];
         const float4 s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3];
         F2 Px{s0.x, s1.x}, Py{s0.y, s1.y}, Pz{s0.z, s1.z}, A{s0.w, s1.w};
         const F2 Nx{s2.x, s3.x}, Ny{s2.y, s3.y}, Nz{s2.z, s3.z};
@@ -514,6 +732,24 @@ struct Df64Policy {
     }
 };
 
+// Generic target handling for policies with kPack targets per thread slot: slot r of a thread holds
+// targets tblock * BS + (r * kPack + h) * kThreads + tid, h < kPack.
+template <typename Policy>
+__device__ __forceinline__ typename Policy::Tgt load_targets(const typename Policy::Src* src, int M, const int* ti) {
+    if constexpr (Policy::kPack == 1) {
+        typename Policy::Tgt t = Policy::load(src, min(ti[0], M - 1));
+        if (ti[0] >= M) Policy::clear_w(t);   // a padding target adds nothing to the sources
+        return t;
+    } else {
+        return Policy::load_pack(src, M, ti);
+    }
+}
+template <typename Policy>
+__device__ __forceinline__ void fold_targets(const typename Policy::Acc& a, double* s1, double* s2) {
+    if constexpr (Policy::kPack == 1) Policy::fold(a, s1[0], s2[0]);
+    else Policy::fold_pack(a, s1, s2);
+}
+
 // One one-sided work item of the dense pair sum: target block `tblock`
 // (kThreads * R targets) against sources [j_begin, j_end), with the correction
 // pairs masked; the sums of target i go to out[c * cstride + (i - t0)], c = 0, 1.
@@ -531,25 +767,28 @@ __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict
     using Src = typename Policy::Src;
     constexpr int TILE = Policy::kTile;
     constexpr int VEC = Policy::kVec;
+    constexpr int P = Policy::kPack;
+    constexpr int RP = R * P;
     const int tid = threadIdx.x;
     const int ntiles = (j_end > j_begin) ? (j_end - j_begin + TILE - 1) / TILE : 0;
 
     typename Policy::Tgt tg[R];
-    double s1[R], s2[R];
-    int ti[R], epos[R], eend[R], enext[R];
+    double s1[RP], s2[RP];
+    int ti[RP], epos[RP], eend[RP], enext[RP];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        ti[r] = tblock * (kThreads * R) + r * kThreads + tid;
-        const int t = min(ti[r], M - 1);
-        tg[r] = Policy::load(src, t);
-        s1[r] = 0.0;
-        s2[r] = 0.0;
+    for (int a = 0; a < RP; ++a) {
+        ti[a] = tblock * (kThreads * RP) + a * kThreads + tid;
+        const int t = min(ti[a], M - 1);
+        s1[a] = 0.0;
+        s2[a] = 0.0;
         int e = eptr[t], ee = eptr[t + 1];
         while (e < ee && excl[e] < j_begin) ++e;
-        epos[r] = e;
-        eend[r] = ee;
-        enext[r] = (e < ee) ? excl[e] : INT_MAX;
+        epos[a] = e;
+        eend[a] = ee;
+        enext[a] = (e < ee) ? excl[e] : INT_MAX;
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) tg[r] = load_targets<Policy>(src, M, &ti[r * P]);
     auto issue = [&](int k) {
         const uint32_t g = gt + (uint32_t)k;
         const int j0 = j_begin + k * TILE;
@@ -579,41 +818,47 @@ __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict
         const int n = min(TILE, j_end - j0);
         bool need = false;
 #pragma unroll
-        for (int r = 0; r < R; ++r) need |= (enext[r] < j0 + n);
+        for (int a = 0; a < RP; ++a) need |= (enext[a] < j0 + n);
         typename Policy::Acc acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) Policy::zero(acc[r]);
         if (!__any_sync(0xffffffffu, need)) {
+            const bool none[P] = {};
 #pragma unroll U
             for (int q = 0; q < n; ++q) {
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    Policy::template pair<false>(tg[r], tile + q * VEC, kc, tab, acc[r], false);
+                    Policy::template pair<false>(tg[r], tile + q * VEC, kc, tab, acc[r], none);
             }
         } else {
             for (int q = 0; q < n; ++q) {
                 const int j = j0 + q;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const bool ex = (j == enext[r]);
-                    if (ex) {
-                        ++epos[r];
-                        enext[r] = (epos[r] < eend[r]) ? excl[epos[r]] : INT_MAX;
+                    bool ex[P];
+#pragma unroll
+                    for (int h = 0; h < P; ++h) {
+                        const int a = r * P + h;
+                        ex[h] = (j == enext[a]);
+                        if (ex[h]) {
+                            ++epos[a];
+                            enext[a] = (epos[a] < eend[a]) ? excl[epos[a]] : INT_MAX;
+                        }
                     }
                     Policy::template pair<true>(tg[r], tile + q * VEC, kc, tab, acc[r], ex);
                 }
             }
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) Policy::fold(acc[r], s1[r], s2[r]);
+        for (int r = 0; r < R; ++r) fold_targets<Policy>(acc[r], &s1[r * P], &s2[r * P]);
         __syncthreads();   // the buffer of this tile is free for the tile after next
     }
     gt += (uint32_t)ntiles;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (ti[r] < M) {
-            out[ti[r] - t0] = s1[r];
-            out[cstride + ti[r] - t0] = s2[r];
+    for (int a = 0; a < RP; ++a) {
+        if (ti[a] < M) {
+            out[ti[a] - t0] = s1[a];
+            out[cstride + ti[a] - t0] = s2[a];
         }
     }
     return true;
@@ -671,7 +916,9 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
     using J = typename Policy::JAcc;
     constexpr int TILE = Policy::kTile;
     constexpr int VEC = Policy::kVec;
-    constexpr int BS = kThreads * R;
+    constexpr int P = Policy::kPack;
+    constexpr int RP = R * P;
+    constexpr int BS = kThreads * RP;
     constexpr int kWarps = kThreads / 32;
     constexpr int kShift = (V == 32) ? 0 : (V == 16) ? 1 : (V == 8) ? 2 : (V == 4) ? 3 : (V == 2) ? 4 : 5;
     static_assert(TILE % V == 0 && TILE <= kThreads, "tile layout");
@@ -680,16 +927,16 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
     const int ntiles = (len + TILE - 1) / TILE;
 
     typename Policy::Tgt tg[R];
-    double s1[R], s2[R];
-    int ti[R];
+    double s1[RP], s2[RP];
+    int ti[RP];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        ti[r] = tblock * BS + r * kThreads + tid;
-        tg[r] = Policy::load(src, min(ti[r], M - 1));
-        if (ti[r] >= M) Policy::clear_w(tg[r]);   // a padding target adds nothing to the sources
-        s1[r] = 0.0;
-        s2[r] = 0.0;
+    for (int a = 0; a < RP; ++a) {
+        ti[a] = tblock * BS + a * kThreads + tid;
+        s1[a] = 0.0;
+        s2[a] = 0.0;
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) tg[r] = load_targets<Policy>(src, M, &ti[r * P]);
     auto issue = [&](int k) {
         const uint32_t g = gt + (uint32_t)k;
         const int j0 = j_begin + k * TILE;
@@ -728,20 +975,23 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
                 if (c0 + V <= n) {
 #pragma unroll
                     for (int q = 0; q < V; ++q) {
-                        Policy::template pair_sym<true>(tg[0], tile + (c0 + q) * VEC, kc, tab, acc[0], ja[q]);
+                        typename Policy::JAccR jr;
+                        Policy::template pair_sym<true>(tg[0], tile + (c0 + q) * VEC, kc, tab, acc[0], jr);
 #pragma unroll
                         for (int r = 1; r < R; ++r)
-                            Policy::template pair_sym<false>(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], ja[q]);
+                            Policy::template pair_sym<false>(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], jr);
+                        ja[q] = Policy::jfinal(jr);
                     }
                 } else {   // ragged end of the item: warp-uniform skip
 #pragma unroll
                     for (int q = 0; q < V; ++q) {
                         if (c0 + q < n) {
-                            Policy::template pair_sym<true>(tg[0], tile + (c0 + q) * VEC, kc, tab, acc[0], ja[q]);
+                            typename Policy::JAccR jr;
+                            Policy::template pair_sym<true>(tg[0], tile + (c0 + q) * VEC, kc, tab, acc[0], jr);
 #pragma unroll
                             for (int r = 1; r < R; ++r)
-                                Policy::template pair_sym<false>(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r],
-                                                                 ja[q]);
+                                Policy::template pair_sym<false>(tg[r], tile + (c0 + q) * VEC, kc, tab, acc[r], jr);
+                            ja[q] = Policy::jfinal(jr);
                         }
                     }
                 }
@@ -755,10 +1005,12 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
                         Policy::zero(cur[t]);
                         const int q = c0 + q0 + t;
                         if (q < n) {   // warp-uniform
-                            Policy::template pair_sym<true>(tg[0], tile + q * VEC, kc, tab, acc[0], cur[t]);
+                            typename Policy::JAccR jr;
+                            Policy::template pair_sym<true>(tg[0], tile + q * VEC, kc, tab, acc[0], jr);
 #pragma unroll
                             for (int r = 1; r < R; ++r)
-                                Policy::template pair_sym<false>(tg[r], tile + q * VEC, kc, tab, acc[r], cur[t]);
+                                Policy::template pair_sym<false>(tg[r], tile + q * VEC, kc, tab, acc[r], jr);
+                            cur[t] = Policy::jfinal(jr);
                         }
                     }
 #pragma unroll
@@ -773,7 +1025,7 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
             if ((lane & ((1 << kShift) - 1)) == 0 && c0 + qs < n) jred[warp * TILE + c0 + qs] = ja[0];
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) Policy::fold(acc[r], s1[r], s2[r]);
+        for (int r = 0; r < R; ++r) fold_targets<Policy>(acc[r], &s1[r * P], &s2[r * P]);
         __syncthreads();   // all warp sums of this tile are in jred
         if (tid < n) {
             J t = jred[tid];
@@ -788,10 +1040,10 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
     }
     gt += (uint32_t)ntiles;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (ti[r] < M) {
-            out_i[ti[r] - tblock * BS] = s1[r];
-            out_i[BS + ti[r] - tblock * BS] = s2[r];
+    for (int a = 0; a < RP; ++a) {
+        if (ti[a] < M) {
+            out_i[ti[a] - tblock * BS] = s1[a];
+            out_i[BS + ti[a] - tblock * BS] = s2[a];
         }
     }
     return true;
@@ -804,7 +1056,7 @@ __device__ __forceinline__ bool run_item(const PairItem& it, const typename Poli
                                          double* __restrict__ buf, const PairConsts& kc, int* __restrict__ err,
                                          typename Policy::Src* ring, typename Policy::JAcc* jred,
                                          const float2* tab, uint64_t* bar, uint32_t& gt) {
-    constexpr int BS = kThreads * R;
+    constexpr int BS = kThreads * R * Policy::kPack;
     constexpr int S = Policy::kSymStep < V ? Policy::kSymStep : V;
     if (it.sym)
         return pair_item_sym<Policy, R, V, U, S>(src, M, it.I, it.j_begin, it.j_end, buf + it.ibase,
@@ -855,10 +1107,10 @@ struct PairSmem {
           tab(reinterpret_cast<float2*>(raw + pair_ring_bytes<Policy>() + pair_jred_bytes<Policy>())) {}
 };
 
-// Fixed launch shapes of the schedules: targets per thread and sources per
+// Fixed launch shapes of the schedules: thread slots (x the policy's kPack targets) and sources per
 // transposed chunk.  R fixes the target blocks and hence the summation order,
 // so it is the same for every kernel variant of an arithmetic.
-constexpr int kR32 = 4, kRdf = 1, kR64 = 1;
+constexpr int kR32 = 2, kRdf = 1, kR64 = 1;   // thread slots (FP32: 2 packed pairs = 4 targets)
 constexpr int kChunkDf = 8, kChunk64 = 8;
 // FP32 schedule-kernel variants: (sources per transposed chunk, unroll of the chunk loop)
 constexpr int kNumVariants32 = 4;
@@ -897,6 +1149,8 @@ void set_fp32_variant(int v);
 int fp32_variant();
 // Runs a handle's schedule of one arithmetic (policy index 0 FP32, 1 float-float, 2 FP64) on its stream
 int launch_schedule(ctr_ibim* s, int pol, const void* src, const pk::PairConsts& kc);
+// Fill the f32x2 copies of a PairConsts from its FP32 fields
+void set_packed_consts(pk::PairConsts& kc);
 // Pair constants of a handle (kernel-ratio terms, kappa, tables when needed)
 int pair_consts(ctr_ibim* s, bool tables, pk::PairConsts* out);
 

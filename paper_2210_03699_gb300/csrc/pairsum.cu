@@ -26,6 +26,7 @@
 //   Df64  double-FP32 "float-float" terms (error-free sums and products with
 //         FMA, rsqrt by one Newton step in df64, exp by two exact tables and
 //         a degree-4 polynomial), ~2^-44 relative, on the FP32 pipe.
+#include <cstring>
 #include <mutex>
 
 #include "pairkern.cuh"
@@ -60,9 +61,9 @@ __global__ void pack_kernel(const double* __restrict__ x, const double* __restri
     if (j >= M) return;
     const double a = scale * W[j] * x[j];
     const double b = scale * W[j] * x[M + j];
-    if (s32) {
-        s32[2 * j].w = (float)a;
-        s32[2 * j + 1].w = (float)b;
+    if (s32) {   // duplicated pairs: a and -b
+        s32[4 * j + 1].z = s32[4 * j + 1].w = (float)a;
+        s32[4 * j + 3].z = s32[4 * j + 3].w = -(float)b;
     }
     if (s64) {
         s64[2 * j].w = a;
@@ -172,6 +173,25 @@ int exp_table(int dev, const float2** out) {
     return CTR_OK;
 }
 
+// The f32x2 operands: each FP32 constant in both halves of a 64-bit word.
+void set_packed_consts(PairConsts& kc) {
+    auto dup = [](float f) {
+        uint32_t b;
+        std::memcpy(&b, &f, sizeof b);
+        return ((unsigned long long)b << 32) | (unsigned long long)b;
+    };
+    kc.one2 = dup(1.f);
+    kc.mone2 = dup(-1.f);
+    kc.three2 = dup(3.f);
+    kc.mthree2 = dup(-3.f);
+    kc.c1x2 = dup(kc.c1f);
+    kc.nc1x2 = dup(-kc.c1f);
+    kc.c2x2 = dup(kc.c2f);
+    kc.nc2x2 = dup(-kc.c2f);
+    kc.kap2 = dup(kc.kappaf);
+    kc.kl2x2 = dup(kc.kl2f);
+}
+
 int pair_consts(ctr_ibim* s, bool tables, PairConsts* out) {
     PairConsts kc{};
     kc.c1 = s->eps_out / s->eps_in;
@@ -184,6 +204,7 @@ int pair_consts(ctr_ibim* s, bool tables, PairConsts* out) {
     kc.c1d = split_ff(kc.c1);
     kc.c2d = split_ff(kc.c2);
     kc.kappad = split_ff(kc.kappa);
+    set_packed_consts(kc);
     kc.exp_tab = nullptr;
     if (tables) CTR_TRY(exp_table(s->device, &kc.exp_tab));
     *out = kc;
@@ -261,6 +282,7 @@ int launch_fp32_pairs_external(const float4* src, int64_t M, const int32_t* eptr
     kc.c2f = (float)kc.c2;
     kc.kappaf = (float)kappa;
     kc.kl2f = (float)(-kappa * 1.4426950408889634);
+    set_packed_consts(kc);
     const size_t smem = 2 * Fp32Policy::kTile * Fp32Policy::kVec * sizeof(float4);
     dim3 grid(p.target_blocks, p.splits);
     pair_kernel<Fp32Policy, 2><<<grid, kThreads, smem, st>>>(src, (int)M, eptr, excl, p.src_per_split, partial, kc,

@@ -51,7 +51,7 @@ __global__ void near_flags_kernel(const int32_t* __restrict__ ptr, const int32_t
 }
 
 template <typename Policy, int R, int V, int U>
-__global__ void __launch_bounds__(kThreads) sched_kernel(const typename Policy::Src* __restrict__ src, int M,
+__global__ void __launch_bounds__(kThreads, 2) sched_kernel(const typename Policy::Src* __restrict__ src, int M,
                                                          const int32_t* __restrict__ eptr,
                                                          const int32_t* __restrict__ excl,
                                                          const PairItem* __restrict__ items, int n_items,
@@ -77,9 +77,16 @@ __global__ void __launch_bounds__(kThreads) sched_kernel(const typename Policy::
 
 template <typename Policy, int R, int V, int U>
 int sched_per_sm() {
-    static int per_sm = 0;   // resident blocks of this instantiation (same on every GB300)
+    static int per_dev[64] = {0};   // resident blocks of this instantiation, per device (attribute set there)
+    int dev = 0;
+    CTR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
+    int& per_sm = per_dev[dev];
     if (per_sm == 0) {
         int b = 0;
+        // dynamic shared memory above the default 48 KB per block needs the kernel's opt-in
+        CTR_CUDA_TRY(cudaFuncSetAttribute(sched_kernel<Policy, R, V, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pair_smem_bytes<Policy>()));
         CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sched_kernel<Policy, R, V, U>, kThreads,
                                                                    pair_smem_bytes<Policy>()));
         per_sm = std::max(1, b);
@@ -245,10 +252,10 @@ int fp32_variant() { return g_var32.load(); }
 int schedule_slots(int sms, int slots[3]) {
     int a = 0;
     switch (fp32_variant()) {
-        case 1: a = sched_per_sm<Fp32Policy, kR32, 4, 1>(); break;
-        case 2: a = sched_per_sm<Fp32Policy, kR32, 8, 2>(); break;
-        case 3: a = sched_per_sm<Fp32Policy, kR32, 4, 2>(); break;
-        default: a = sched_per_sm<Fp32Policy, kR32, 8, 1>(); break;
+        case 1: a = sched_per_sm<Fp32x2Policy, kR32, 4, 1>(); break;
+        case 2: a = sched_per_sm<Fp32x2Policy, kR32, 8, 2>(); break;
+        case 3: a = sched_per_sm<Fp32x2Policy, kR32, 4, 2>(); break;
+        default: a = sched_per_sm<Fp32x2Policy, kR32, 8, 1>(); break;
     }
     if (a < 0) return a;
     const int b = sched_per_sm<Df64Policy, kRdf, kChunkDf, 1>();
@@ -266,10 +273,10 @@ int launch_schedule(ctr_ibim* s, int pol, const void* src, const PairConsts& kc)
     CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
     if (pol == 0) {
         switch (fp32_variant()) {
-            case 1: return sched_launch<Fp32Policy, kR32, 4, 1>(s, 0, src, kc, sms);
-            case 2: return sched_launch<Fp32Policy, kR32, 8, 2>(s, 0, src, kc, sms);
-            case 3: return sched_launch<Fp32Policy, kR32, 4, 2>(s, 0, src, kc, sms);
-            default: return sched_launch<Fp32Policy, kR32, 8, 1>(s, 0, src, kc, sms);
+            case 1: return sched_launch<Fp32x2Policy, kR32, 4, 1>(s, 0, src, kc, sms);
+            case 2: return sched_launch<Fp32x2Policy, kR32, 8, 2>(s, 0, src, kc, sms);
+            case 3: return sched_launch<Fp32x2Policy, kR32, 4, 2>(s, 0, src, kc, sms);
+            default: return sched_launch<Fp32x2Policy, kR32, 8, 1>(s, 0, src, kc, sms);
         }
     }
     if (pol == 1) return sched_launch<Df64Policy, kRdf, kChunkDf, 1>(s, 1, src, kc, sms);
@@ -291,8 +298,8 @@ int build_schedules(ctr_ibim* s, const int slots[3]) {
     std::vector<uint8_t> flags((size_t)nb0 * nb0);
     CTR_CUDA_TRY(cudaMemcpyAsync(flags.data(), d_flags.p, flags.size(), cudaMemcpyDeviceToHost, s->stream));
     CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    const int Rs[3] = {kR32, kRdf, kR64};
-    const int tiles[3] = {Fp32Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
+    const int Rs[3] = {kR32 * Fp32x2Policy::kPack, kRdf, kR64};   // targets per thread
+    const int tiles[3] = {Fp32x2Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
     int64_t need = 1;
     for (int p = 0; p < 3; ++p) {
         plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], flags, g0, nb0, slots[p]);

@@ -184,8 +184,10 @@ __global__ void geometry_kernel(const double* __restrict__ sd, const int64_t* __
     na.t1x[m] = t1[0]; na.t1y[m] = t1[1]; na.t1z[m] = t1[2];
     na.t2x[m] = t2[0]; na.t2y[m] = t2[1]; na.t2z[m] = t2[2];
     na.m1[m] = -k1; na.m2[m] = -k2;
-    src32[2 * m] = make_float4((float)P0, (float)P1, (float)P2, 0.f);
-    src32[2 * m + 1] = make_float4((float)n0, (float)n1, (float)n2, 0.f);
+    src32[4 * m] = make_float4((float)P0, (float)P0, (float)P1, (float)P1);
+    src32[4 * m + 1] = make_float4((float)P2, (float)P2, 0.f, 0.f);
+    src32[4 * m + 2] = make_float4((float)n0, (float)n0, (float)n1, (float)n1);
+    src32[4 * m + 3] = make_float4((float)n2, (float)n2, 0.f, 0.f);
     src64[2 * m] = make_double4(P0, P1, P2, 0.0);
     src64[2 * m + 1] = make_double4(n0, n1, n2, 0.0);
 }
@@ -262,7 +264,7 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
                                       &s->na.W, &s->na.d, &s->na.t1x, &s->na.t1y, &s->na.t1z,
                                       &s->na.t2x, &s->na.t2y, &s->na.t2z, &s->na.m1, &s->na.m2};
     for (int q = 0; q < NodeArrays::kCount; ++q) *f[q] = b + (size_t)q * M;
-    CTR_TRY(s->src32.alloc(sizeof(float4) * 2 * M));
+    CTR_TRY(s->src32.alloc(sizeof(float4) * 4 * M));
     CTR_TRY(s->src64.alloc(sizeof(double4) * 2 * M));
     CTR_TRY(s->bad.alloc(M));
     geometry_kernel<<<grid_for(M, 128), 128, 0, st>>>(d_sdist, s->lin.as<int64_t>(), M, s->n[0], s->n[1], s->n[2],
