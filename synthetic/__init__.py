@@ -292,6 +292,46 @@ def molecule_problem(n_atoms: int = 500, seed: int = 0, h: float = 0.5, probe: f
                    info={"n_atoms": n_atoms, "seed": seed, "probe": probe, "radii": radii})
 
 
+# ---------------------------------------------------------------- convergence-study surfaces (Sec. 3.3.2)
+TORUS_ANGLES = (1.99487, 2.54097947651017, 4.219760487439292)   # rotations about x, y, z (Sec. 3.3.2)
+
+
+def torus_rotation(angles=TORUS_ANGLES) -> np.ndarray:
+    """R = Rz(c) Ry(b) Rx(a): the body-frame torus (axis z) rotated about x, then y, then z."""
+    a, b, c = angles
+    Rx = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]])
+    Ry = np.array([[math.cos(b), 0, math.sin(b)], [0, 1, 0], [-math.sin(b), 0, math.cos(b)]])
+    Rz = np.array([[math.cos(c), -math.sin(c), 0], [math.sin(c), math.cos(c), 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def torus_sdist(grid: Grid, R1: float = 1.0, R2: float = 0.5, angles=TORUS_ANGLES) -> np.ndarray:
+    """Exact signed distance to the rotated torus: sqrt((rho - R1)^2 + z^2) - R2 in the body frame."""
+    X, Y, Z = grid.points()
+    Rt = torus_rotation(angles).T
+    xb = Rt[0, 0] * X + Rt[0, 1] * Y + Rt[0, 2] * Z
+    yb = Rt[1, 0] * X + Rt[1, 1] * Y + Rt[1, 2] * Z
+    zb = Rt[2, 0] * X + Rt[2, 1] * Y + Rt[2, 2] * Z
+    return np.sqrt((np.sqrt(xb * xb + yb * yb) - R1) ** 2 + zb * zb) - R2
+
+
+def torus_area(R1: float = 1.0, R2: float = 0.5) -> float:
+    return 4.0 * math.pi ** 2 * R1 * R2
+
+
+def torus_problem(h: float, R1: float = 1.0, R2: float = 0.5, q: float = 1.0, kappa: float = KAPPA,
+                  tube_mult: float = 2.0) -> Problem:
+    """The rotated torus of Sec. 3.3.2 (R1 = 1, R2 = 1/2), one charge q inside the tube at the body point
+    (R1, 0, 0) (a charge at the origin, as printed, lies outside the torus), tube 2h."""
+    eps = tube_mult * h
+    half = R1 + R2 + eps + 3 * h
+    grid = box_grid((-half,) * 3, (half,) * 3, h)
+    z = torus_rotation() @ np.array([R1, 0.0, 0.0])
+    return Problem(name=f"torus_h{h:g}", grid=grid, sdist=torus_sdist(grid, R1, R2),
+                   charge_xyz=z.reshape(1, 3), charge_q=np.array([q]), kappa=kappa, tube=eps,
+                   info={"R1": R1, "R2": R2, "area": torus_area(R1, R2)})
+
+
 # ---------------------------------------------------------------- batches and request streams
 def batch_specs(n: int, seed: int = 0, min_atoms: int = 20, max_atoms: int = 2000, spacings=(0.5, 0.35)):
     """Molecule specs of the batched workload: atom counts log-uniform in [min, max], h from `spacings`.

@@ -391,3 +391,47 @@ def test_server_isolates_failed_requests(ctr):
         r1, rb, r2 = sv.wait(t1, 120), sv.wait(t_bad, 120), sv.wait(t2, 120)
         assert r1.status == 0 and r2.status == 0 and rb.status == -2
         assert r1.G_pol == r2.G_pol
+
+
+# ---------------------------------------------------------------- convergence studies (Sec. 3.3.2)
+def test_torus_area_and_potential_convergence(ctr, oracle_tables):
+    """Rotated torus (R1 = 1, R2 = 1/2, eps = 2h): the GPU area equals the oracle's, its error against
+    4 pi^2 R1 R2 falls at least fourfold per halving of h, and psi_rxn(0) (Eq. 2.31) converges: the
+    successive differences shrink (the paper's 'diff' column falls 3.8x and 5.2x)."""
+    from oracle.geometry import tube_area, tube_geometry
+    areas, rx = [], []
+    for h in (0.1, 0.05, 0.025):
+        p = syn.torus_problem(h)
+        with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP32_REFINE)) as G:
+            areas.append(G.area())
+            psi, dpsi, info = G.solve()
+            assert info.converged
+            rx.append(G.reaction_potential(psi, dpsi, np.zeros((1, 3)))[0])
+            if h == 0.1:
+                g = p.grid
+                geo = tube_geometry(g.n, g.origin, g.h, p.sdist, p.tube)
+                assert abs(areas[0] / tube_area(geo) - 1) < 1e-12
+    err = [abs(a / syn.torus_area() - 1) for a in areas]
+    assert err[0] / err[1] > 4.0 and err[1] / err[2] > 4.0 and err[2] < 1e-5
+    d1, d2 = abs(rx[1] - rx[0]), abs(rx[2] - rx[1])
+    assert d1 / d2 > 2.5
+
+
+def test_sphere_r10_ctr2_beats_kreg(ctr):
+    """Sphere r = 10, one unit charge at the centre, eps = 2h (Sec. 3.3.2, Fig. 2): psi_rxn(0) against the
+    closed form.  CTR2 converges (order about 1 at eps = 2h) and its error is at least ten times smaller
+    than K-reg's at every h, as the paper reports; K-reg converges at first order."""
+    R, q = 10.0, 1.0
+    exact = q / (4 * math.pi * R) * (1 / (syn.EPS_OUT * (1 + syn.KAPPA * R)) - 1 / syn.EPS_IN)
+    e_ctr, e_kreg = [], []
+    for h in (1.0, 0.5, 0.25):
+        p = syn.sphere_problem(h=h, R=R, half_box=R + 5 * h, q=q)
+        for meth, errs in ((ctr.METHOD_HYB, e_ctr), (ctr.METHOD_KREG, e_kreg)):
+            with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP32_REFINE,
+                                                                 method=meth)) as G:
+                psi, dpsi, info = G.solve()
+                assert info.converged
+                errs.append(abs(G.reaction_potential(psi, dpsi, np.zeros((1, 3)))[0] / exact - 1))
+    assert all(a * 10 < b for a, b in zip(e_ctr, e_kreg))
+    assert e_ctr[0] > e_ctr[1] > e_ctr[2] and e_ctr[2] < 2e-5
+    assert all(1.6 < e_kreg[k] / e_kreg[k + 1] < 2.5 for k in range(2))

@@ -336,3 +336,17 @@ def test_hybrid_classification_on_smooth_and_kinked_surfaces(oracle_tables):
     geo = geometry.tube_geometry(mol.grid.n, mol.grid.origin, mol.grid.h, mol.sdist, mol.tube)
     assert geo.bad.any() and not geo.bad.all()
     assert np.all(geo.J[geo.bad] == 1.0) and np.all(np.isfinite(geo.W)) and np.all(geo.W >= 0)
+
+
+def test_oracle_torus_area_converges():
+    """Rotated torus of Sec. 3.3.2 (R1 = 1, R2 = 1/2): the tube rule with J_h (Eq. 2.6, f = 1) against the
+    closed form 4 pi^2 R1 R2 at eps = 2h; at least second order (the paper tabulates 1e-6..1e-5 errors)."""
+    from oracle.geometry import tube_area, tube_geometry
+    errs = []
+    for h in (0.1, 0.05):
+        p = syn.torus_problem(h)
+        g = p.grid
+        geo = tube_geometry(g.n, g.origin, g.h, p.sdist, p.tube)
+        errs.append(abs(tube_area(geo) / syn.torus_area() - 1))
+    assert errs[0] < 5e-4 and errs[1] < 1e-4
+    assert errs[0] / errs[1] > 4.0
