@@ -408,13 +408,13 @@ static std::atomic<int> g_last_var{-1};
 
 void last_tuning(int* R, int* chunk, int* unroll) {
     const int v = g_last_var.load();
-    *R = v < 0 ? 0 : kR32;
+    *R = v < 0 ? 0 : kR32 * Fp32x2Policy::kPack;
     *chunk = v < 0 ? 0 : kVariants32[v][0];
     *unroll = v < 0 ? 0 : kVariants32[v][1];
 }
 
 int engine_fp32_variant(const Engine* e, int* R, int* chunk, int* unroll) {
-    *R = kR32;
+    *R = kR32 * Fp32x2Policy::kPack;
     *chunk = kVariants32[e->var32][0];
     *unroll = kVariants32[e->var32][1];
     return CTR_OK;

@@ -9,6 +9,8 @@ Tolerances (arithmetic behind them in the design notes):
   * FP32-pair operator: 2e-5 relative (FP32 pair terms, FP64 accumulation per tile);
   * FP32 + FP64-refinement solve: 1e-6 relative in psi, dpsi and G_pol.
 """
+import math
+
 import numpy as np
 import pytest
 
