@@ -313,6 +313,39 @@ def test_full_size_sampled_rows(ctr, oracle_tables):
     G.close()
 
 
+def test_full_size_molecule_sampled_rows_and_energy(ctr, oracle_tables):
+    """The 500-atom SES molecule at h = 0.5 (the single-molecule workload, ~90k nodes; HYB with K-reg rows
+    at the bad nodes): every ordered pair covered once by each schedule, sampled rows against the oracle
+    in the three arithmetics, and the FP32-refined polarization energy within 1e-6 of the plain FP64
+    solve on the GPU."""
+    prob = syn.molecule_problem(n_atoms=500, seed=0, h=0.5)
+    G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE))
+    assert G.M > 80_000 and G.bad_nodes().sum() > 0
+    for prec in (ctr.FP32_REFINE, ctr.DF64, ctr.FP64):
+        sc = G.pair_schedule(prec)
+        assert sc["one_sided_pairs"] + 2 * sc["symmetric_pairs"] == G.M * G.M
+    rng = np.random.Generator(np.random.PCG64(11))
+    bad = np.nonzero(G.bad_nodes())[0]
+    rows = np.unique(np.concatenate([[0, G.M - 1], rng.integers(0, G.M, size=38), rng.choice(bad, size=8)]))
+    S = OracleSystem.from_problem(prob, tables=oracle_tables, rows=rows)
+    assert S.M == G.M
+    p = syn.random_density(S.M, seed=19, smooth_points=S.geo.P)
+    ref = S.matvec(p, rows=rows)
+    sel = np.concatenate([rows, G.M + rows])
+    assert _rel(G.matvec(p, ctr.FP64)[sel], ref) < 1e-12
+    assert _rel(G.matvec(p, ctr.DF64)[sel], ref) < 1e-12
+    assert _rel(G.matvec(p, ctr.FP32_REFINE)[sel], ref) < 2e-5
+    psi, dpsi, info = G.solve()
+    assert info.converged and info.residual < 1e-10
+    E32 = G.energy(psi, dpsi)[0]
+    G.close()
+    with ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP64)) as G64:
+        psi64, dpsi64, info64 = G64.solve()
+        assert info64.converged
+        E64 = G64.energy(psi64, dpsi64)[0]
+    assert abs(E32 / E64 - 1) < 1e-6
+
+
 # ---------------------------------------------------------------- batched engine (many systems, one engine)
 def test_batch_matches_alone_bitwise(ctr, oracle_tables):
     """Each system's result is the same alone and in a mixed batch (sizes, methods, precisions)."""
