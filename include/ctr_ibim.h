@@ -302,9 +302,10 @@ int ctr_weight_tables(double* out);
 /*
  * Allocation-free variant of the FP32 dense pair sum (the paper has no
  * counterpart: it is an interface for callers, not a step of the method).
- * For callers that cannot call cudaMalloc -- code running while a CUDA graph
- * is being captured, or under an allocator that owns all device memory, or a
- * real-time loop that must not allocate -- this entry point takes every
+ * For callers that cannot call cudaMalloc -- code running under an allocator
+ * that owns all of the device's memory (a framework's caching pool, an
+ * embedding application that reserved the GPU for itself), or a real-time
+ * loop that must not stall on an allocation -- this entry point takes every
  * input and output from the caller and keeps its scratch (the per-split
  * partial sums) in a fixed device array of 2 * CTR_STATIC_SCRATCH_NODES
  * doubles (16 MiB), which each GPU that loads the library holds until the

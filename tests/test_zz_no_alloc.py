@@ -1,8 +1,8 @@
 """The allocation-free FP32 pair sum (ctr_pair_sum_fp32_static) against ctr_ibim_matvec.
 
-Callers that cannot allocate device memory (code inside a CUDA graph
-capture, an allocator that owns all device memory, a loop that must not
-allocate) use ctr_pair_sum_fp32_static, whose scratch is a fixed device
+Callers that cannot allocate device memory (code running under an allocator
+that owns all of the device's memory, or a loop that must not stall on an
+allocation) use ctr_pair_sum_fp32_static, whose scratch is a fixed device
 array.  Its output must equal the dense pair part of ctr_ibim_matvec's FP32
 operator (the matvec minus its diagonal and its correction) within the FP32
 operator tolerance of the parity tests, on two calls in a row with different
