@@ -6,6 +6,11 @@
  * direct transcription of a definition in the paper; there is no blocking,
  * no reordering and no approximation beyond IEEE FP64 rounding.  It must be
  * compiled with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Parity status: pinned through the operator (the double-layer identity,
+ * the sphere kernel integrals in closed form, the exact sphere solution
+ * satisfying the discrete equations to the method's order, planted mistakes
+ * that the consistency test must catch).
  */
 #include <math.h>
 #include <stdint.h>

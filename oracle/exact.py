@@ -10,6 +10,9 @@ On a sphere every kernel of Eq. (1.4) between two surface points depends on
 r = |x - y| only: (x - y).n_x = r^2/(2R), (x - y).n_y = -r^2/(2R),
 n_x.n_y = 1 - r^2/(2 R^2), and dsigma = 2 pi r dr/... integrated on r in [0, 2R]
 (dsigma = (R / R) 2 pi r dr for a sphere: r dr = R^2 sin(theta) dtheta).
+
+Parity status: these closed forms are the pins; each is checked against an independent route in the
+tests (the boundary integral equations on the sphere, the sphere kernel integrals, Kirkwood's energy).
 """
 from __future__ import annotations
 

@@ -32,6 +32,10 @@ design notes):
     Lagrange interpolation of degree 5 (6 x 6 stencil) around (alpha, beta).
 
 Test infrastructure only: see the package docstring.
+
+Parity status: pinned (the square-lattice constant omega[1/r] = -4 zeta(1/2) beta(1/2), the limit
+against an independent Ewald-split evaluation, the table symmetries, omega[1] = 1, and the plane rule's
+second-order convergence for a smooth test function).
 """
 from __future__ import annotations
 
