@@ -262,51 +262,6 @@ struct Fp32Policy {
     __device__ static JAcc jshfl_xor(const JAcc& x, int m) {
         return JAcc{__shfl_xor_sync(0xffffffffu, x.a1, m), __shfl_xor_sync(0xffffffffu, x.a2, m)};
     }
-    // Both orientations of one pair: the target's sums (acc) get K(x_i, y_j) applied to source j's
-    // weights and the source's sums (ja) get K(x_j, y_i) applied to target i's weights.  With
-    // d = P_i - P_j the swapped pair has d' = -d, so d'.n_j = -(d.n_j) and d'.n_i = -(d.n_i) swap
-    // roles while r, E, n_i.n_j and the K21 bracket are shared: 8 extra FP32 ops for the second term.
-    // kFirst: ja holds nothing yet (first target of the thread): its terms are assigned, not added.
-    template <bool kFirst>
-    __device__ static void pair_sym(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc,
-                                    JAcc& ja) {
-        const float4 pa = S[0], nb = S[1];
-        const float dx = T.px - pa.x, dy = T.py - pa.y, dz = T.pz - pa.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float rinv = rsqrt_sfu(r2);
-        const float r = r2 * rinv;
-        const float E = ex2_sfu(k.kl2f * r);
-        const float kr = k.kappaf * r;
-        const float E1 = fmaf(E, kr, E);
-        const float dny = fmaf(dz, nb.z, fmaf(dy, nb.y, dx * nb.x));
-        const float dnx = fmaf(dz, T.qz, fmaf(dy, T.qy, dx * T.qx));
-        const float nn = fmaf(T.qz, nb.z, fmaf(T.qy, nb.y, T.qx * nb.x));
-        const float rinv2 = rinv * rinv;
-        const float s = rinv2 * rinv;
-        const float as = pa.w * s, bs = nb.w * s;
-        const float t1 = fmaf(-k.c1f, E1, 1.f);
-        const float om = fmaf(-rinv, E, rinv);
-        const float t2 = fmaf(-k.c2f, E1, 1.f);
-        const float u = 1.f - E1;
-        const float q = fmaf(kr, kr + 3.f, 3.f);
-        const float t3 = fmaf(-E, q, 3.f);
-        const float B = t3 * dnx * dny * rinv2;
-        const float X = fmaf(u, nn, -B);
-        acc.a1 = fmaf(as, dny * t1, acc.a1);
-        acc.a1 = fmaf(-nb.w, om, acc.a1);
-        acc.a2 = fmaf(bs, dnx * t2, acc.a2);
-        acc.a2 = fmaf(as, X, acc.a2);
-        const float ast = T.wa * s, bst = T.wb * s;
-        if constexpr (kFirst) {
-            ja.a1 = -ast * (dnx * t1);
-            ja.a2 = -bst * (dny * t2);
-        } else {
-            ja.a1 = fmaf(-ast, dnx * t1, ja.a1);
-            ja.a2 = fmaf(-bst, dny * t2, ja.a2);
-        }
-        ja.a1 = fmaf(-T.wb, om, ja.a1);
-        ja.a2 = fmaf(ast, X, ja.a2);
-    }
     template <bool kMask>
     __device__ static void pair(const Tgt& T, const Src* S, const PairConsts& k, const float2*, Acc& acc, const bool* exv) {
         const bool ex = exv[0];
