@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels"],
                     help="solve: the default single-system line; batch: many molecules in one engine; "
-                         "serve: continuous-batching server under Poisson arrivals; kernels: two FP32 and two "
-                         "float-float operator applications of the ellipsoid at --h (the profiling case)")
+                         "serve: continuous-batching server under Poisson arrivals; kernels: two FP32, two "
+                         "float-float and two FP64 operator applications of the ellipsoid at --h (the profiling "
+                         "case)")
     ap.add_argument("--molecules", type=int, default=64, help="batch mode: molecules in the batch")
     ap.add_argument("--max-atoms", type=int, default=2000, help="batch/serve: largest molecule")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per load level")
@@ -365,7 +366,7 @@ def run_serve(args, ctr):
 
 
 def run_kernels(args, ctr):
-    """Two FP32 and two float-float operator applications (first warms up), timed with events."""
+    """Two FP32, two float-float and two FP64 operator applications (the first of each warms up), timed."""
     import torch
     prob, cfg = workload(args.h)
     stream = torch.cuda.current_stream()
@@ -374,7 +375,7 @@ def run_kernels(args, ctr):
         x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, 2 * G.M), device="cuda")
         y = torch.empty_like(x)
         out["M"] = G.M
-        for pr, name in ((ctr.FP32_REFINE, "fp32"), (ctr.DF64, "df64")):
+        for pr, name in ((ctr.FP32_REFINE, "fp32"), (ctr.DF64, "df64"), (ctr.FP64, "fp64")):
             G.matvec(x, pr, out=y)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
