@@ -15,9 +15,10 @@
 //   update half  (slots in state UPDATE) x += Lambda^-1 V y, pack, pairs,
 //                finish r = g - A x, norm, decide (done / next cycle), start cycle.
 // The dense pair sums of all slots run in persistent kernels (one per pair
-// arithmetic and half) whose blocks take work items (slot, target block,
-// source split) from a list sorted by cost through an atomic counter; items of
-// slots in another state return at once.  A slot's items, partial-sum layout,
+// arithmetic and half) whose blocks take work entries (slot, item of that
+// slot's pair schedule: target block, source range, one-sided or symmetric)
+// from a list sorted by cost through an atomic counter; entries of slots in
+// another state return at once.  A slot's items, partial-sum layout,
 // reduction chunks and scalar updates are exactly those of the slot alone, so
 // a system's result does not depend on what else the engine holds.
 #include <algorithm>
@@ -821,7 +822,7 @@ int engine_step(Engine* e, std::vector<SlotStat>* stats) {
     return CTR_OK;
 }
 
-// The handle's solver workspace, sized for the engine (Krylov basis, vectors, split partials).
+// The handle's solver workspace, sized for the engine (Krylov basis, vectors).
 int engine_prepare_handle(ctr_ibim* s) {
     CTR_TRY(ensure_krylov_public(s));
     return CTR_OK;

@@ -12,9 +12,9 @@
 // Admission is first-come first-served: a request that does not fit waits
 // for memory to free up (requests behind it wait too, so none starves).  The
 // footprint estimate counts the tube nodes on the host (|d| < eps) and charges
-// the per-node cost of geometry, packed sources, split partials, solver
-// vectors and the Krylov basis; after setup the handle's real allocation is
-// charged instead.
+// the per-node cost of geometry, packed sources, solver vectors and the
+// Krylov basis plus the pair schedules' partial regions (M^2 / 32 bytes);
+// after setup the handle's real allocation is charged instead.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
