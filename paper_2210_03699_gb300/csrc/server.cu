@@ -57,6 +57,8 @@ size_t handle_bytes(const ctr_ibim* s) {
                             &s->kr.part, &s->kr.scal};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
+    for (const PairSchedule& p : s->sched) b += p.d_items.bytes + p.d_rptr.bytes + p.d_recs.bytes;
+    b += s->counter.bytes;
     return b;
 }
 
