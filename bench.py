@@ -37,10 +37,14 @@ if ROOT not in sys.path:
 # SFU work (rsqrt, ex2) and shared-memory loads are not counted.
 OPS_FP32 = {"one": 41, "sym": 50}
 OPS_DF64 = {"one": 507, "sym": 501}
+# FP64 pipe lane operations per pair evaluation of the FP64 schedule (CUDA's exp and rsqrt included): the
+# ncu count sm__inst_executed_pipe_fp64 x 32 / evaluations over one launch at h = 0.1 (69); its peak is the
+# measured DFMA probe rate, there being no FP64 unit count to go by.
+OPS_FP64 = {"one": 69, "sym": 69}
 # DRAM bytes (read + write) per launch of the schedule kernels at the default workload (h = 0.05), from one
 # ncu capture (profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt); None at any other size, or once
 # the kernels change.
-TRAFFIC_H005 = {"fp32": 2.286e8, "df64": 1.0483e9}
+TRAFFIC_H005 = {"fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
 
 
 def parse():
@@ -454,7 +458,8 @@ def main():
     with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
         x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, 2 * G.M), device="cuda")
         y = torch.empty_like(x)
-        for pr, reps in ((ctr.FP32_REFINE, 5), (ctr.DF64, 2)):
+        timed = ((ctr.FP32_REFINE, 5), (ctr.DF64, 2)) if prec == ctr.FP32_REFINE else ((ctr.FP64, 1),)
+        for pr, reps in timed:
             G.matvec(x, pr, out=y)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -476,10 +481,10 @@ def main():
     f_max = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
     rate_units = sms * 128 * f_max
 
-    def roof(pr, ops, name, key):
+    def roof(pr, ops, name, key, rate=None):
         sc = sched[pr]
         n_ops = ops["one"] * sc["one_sided_pairs"] + ops["sym"] * sc["symmetric_pairs"]
-        peak = rate_units * Mk * Mk / n_ops
+        peak = (rate or rate_units) * Mk * Mk / n_ops
         ach = Mk * Mk / t_mv[pr]
         return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "pair-interactions/s",
                 "frac": ach / peak, "traffic": TRAFFIC_H005[key] if abs(args.h - 0.05) < 1e-12 else None,
@@ -490,14 +495,24 @@ def main():
                 "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"]}
 
     i_last = infos[-1]
-    r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32x2Policy> (packed FP32 pair sum, inner GMRES)", "fp32")
-    rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)", "df64")
-    share32 = i_last.matvecs_fp32 * t_mv[ctr.FP32_REFINE]
-    sharedf = i_last.matvecs_fp64 * t_mv[ctr.DF64]
-    dominant, other = (rdf, r32) if sharedf >= share32 else (r32, rdf)
-    dominant = dict(dominant, ex2_rate=rate_ex2, dfma_rate=rate_dfma,
-                    step_share=max(share32, sharedf) / (t_max / args.steps))
-    other = dict(other, step_share=min(share32, sharedf) / (t_max / args.steps))
+    if prec == ctr.FP32_REFINE:
+        r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32x2Policy> (packed FP32 pair sum, inner GMRES)",
+                   "fp32")
+        rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)",
+                   "df64")
+        share32 = i_last.matvecs_fp32 * t_mv[ctr.FP32_REFINE]
+        sharedf = i_last.matvecs_fp64 * t_mv[ctr.DF64]
+        dominant, other = (rdf, r32) if sharedf >= share32 else (r32, rdf)
+        dominant = dict(dominant, ex2_rate=rate_ex2, dfma_rate=rate_dfma,
+                        step_share=max(share32, sharedf) / (t_max / args.steps))
+        other = dict(other, step_share=min(share32, sharedf) / (t_max / args.steps))
+    else:   # plain FP64 solves: every application is the FP64 schedule, bound by the DFMA pipe
+        dominant = roof(ctr.FP64, OPS_FP64, "sched_kernel<Fp64Policy> (FP64 pair sum)", "fp64", rate=rate_dfma)
+        dominant["bound"] = "alu"
+        dominant["peak_basis"] = (f"measured DFMA probe {rate_dfma:.4g}/s x M^2 / FP64-pipe lane ops of the "
+                                  f"schedule ({OPS_FP64['one']} per pair evaluation, ncu count)")
+        dominant = dict(dominant, step_share=i_last.matvecs_fp64 * t_mv[ctr.FP64] / (t_max / args.steps))
+        other = None
 
     # e2e through the public API with host buffers
     e2e = None
