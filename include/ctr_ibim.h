@@ -226,13 +226,15 @@ int ctr_ibim_batch_solve(ctr_ibim* const* systems, int64_t n, double* const* psi
 
 /* ---------------------------------------------------------------- serving
  * A server solves requests (one surface + charges each) as they arrive, with
- * continuous batching: a host thread admits waiting requests into free slots
- * of one multi-slot engine while the device-memory budget allows (first come,
- * first served), advances every admitted system one engine step at a time,
- * and retires finished ones (their result and polarization energy kept until
- * released).  Requests that arrive while others run share the same launches.
- * Every system's arithmetic is the same as when it is solved alone.  The
- * server uses the device current at ctr_server_create.
+ * continuous batching: a setup thread takes waiting requests (first come,
+ * first served) while a slot is free and the device-memory budget allows, and
+ * sets them up on the GPU alongside the running work; a worker thread puts
+ * set-up systems into free slots of one multi-slot engine, advances every
+ * admitted system one engine step at a time, and retires finished ones
+ * (their result and polarization energy kept until released).  Requests that
+ * arrive while others run share the same launches.  Every system's
+ * arithmetic is the same as when it is solved alone.  The server uses the
+ * device current at ctr_server_create.
  */
 typedef struct ctr_server ctr_server;
 
@@ -251,7 +253,7 @@ typedef struct {
 
 typedef struct {
     int64_t budget_bytes, used_bytes, peak_used_bytes;
-    int peak_slots, running, waiting;
+    int peak_slots, running, waiting;   /* waiting: not yet in an engine slot (queued, in setup, set up) */
     int64_t steps;
 } ctr_server_stats_t;
 
@@ -271,7 +273,7 @@ int ctr_server_fetch(ctr_server* sv, uint64_t ticket, double* psi, double* dpsi_
 /* Forgets a finished request and its stored result. */
 int ctr_server_release(ctr_server* sv, uint64_t ticket);
 int ctr_server_stats(ctr_server* sv, ctr_server_stats_t* out);
-/* Stops the worker (waiting requests are dropped) and frees everything. */
+/* Stops the server's threads (waiting requests are dropped) and frees everything. */
 void ctr_server_destroy(ctr_server* sv);
 
 /*

@@ -1,9 +1,13 @@
 // Request server with continuous batching over the multi-slot engine.
 //
-// A host thread owns one engine (fixed slot capacity) and loops:
-//   1. admit: while a slot is free and the oldest waiting request fits the
-//      device-memory budget, set it up on the GPU (tube, geometry,
-//      corrections, right-hand side) and put it in a slot;
+// Two host threads share one engine (fixed slot capacity):
+//   setup thread: while a slot is free (running + ready + in setup < slots)
+//      and the oldest waiting request fits the device-memory budget, set it
+//      up on the GPU (tube, geometry, corrections, right-hand side, pair
+//      schedules) on the handle's own stream and queue it as ready -- this
+//      overlaps with the engine's steps instead of stalling them;
+//   worker thread (owns the engine):
+//   1. admit: put every ready handle into a free slot;
 //   2. step: one engine step advances every admitted system (an Arnoldi
 //      iteration, or a true-residual evaluation at a cycle end), so requests
 //      that arrive while others run share the same launches;
@@ -46,6 +50,8 @@ struct Request {
     std::vector<double> psi, dpsi;
     ctr_ibim* sys = nullptr;
     int slot = -1;
+    int64_t need = 0;      // footprint estimate, computed at submission
+    cudaStream_t stream = nullptr;   // the handle's own non-blocking stream (created and destroyed here)
     int64_t charged = 0;
     bool done = false;
 };
@@ -77,13 +83,15 @@ struct ctr_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<ctr::Request*> waiting;
+    std::deque<ctr::Request*> ready;     // set up, not yet in an engine slot
+    int preparing = 0;                   // requests the setup thread is working on
     std::map<uint64_t, ctr::Request*> all;
     std::vector<ctr::Request*> running;
     uint64_t next_ticket = 1;
     bool stop = false;
     int fatal = 0;
     std::string fatal_msg;
-    std::thread worker;
+    std::thread worker, setup;
     int64_t steps = 0;
 };
 
@@ -103,6 +111,11 @@ int64_t estimate_bytes(const Request& r) {
     const int64_t regions = M * M / 32 + ((int64_t)16 << 20);
     const int64_t grid_bytes = (int64_t)r.sdist.size() * (8 + 4);   // staging copy + node map during setup
     return M * per_node + regions + grid_bytes;
+}
+
+void release_stream(Request* r) {
+    if (r->stream) cudaStreamDestroy(r->stream);
+    r->stream = nullptr;
 }
 
 void finish_request(ctr_server* sv, Request* r, int status) {
@@ -138,6 +151,7 @@ int retire_done(ctr_server* sv, const std::vector<SlotStat>& st, std::vector<Req
         }
         ctr_ibim_destroy(r->sys);
         r->sys = nullptr;
+        release_stream(r);
         r->slot = -1;
         finished.push_back(r);
         r->res.status = status;
@@ -145,60 +159,106 @@ int retire_done(ctr_server* sv, const std::vector<SlotStat>& st, std::vector<Req
     return CTR_OK;
 }
 
+// Setup thread: FCFS admission under the slot and memory limits, setup off the engine's thread.
+void setup_loop(ctr_server* sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        Request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            auto can = [&] {
+                if (sv->stop || sv->fatal) return true;
+                if (sv->waiting.empty()) return false;
+                const int in_flight = (int)(sv->running.size() + sv->ready.size()) + sv->preparing;
+                if (in_flight >= sv->cap) return false;
+                // the oldest request goes in when it fits, or alone when it exceeds the budget
+                return sv->used + sv->waiting.front()->need <= sv->budget || in_flight == 0;
+            };
+            sv->cv_work.wait(lk, can);
+            if (sv->stop || sv->fatal) break;
+            r = sv->waiting.front();
+            sv->waiting.pop_front();
+            r->charged = r->need;
+            sv->used += r->need;
+            sv->preparing++;
+        }
+        r->res.t_admit = now_s();
+        ctr_ibim* sys = nullptr;
+        int s1 = (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess)
+                     ? CTR_OK
+                     : fail(CTR_ERR_CUDA, "stream create");
+        if (s1 >= 0)
+            s1 = ctr_ibim_setup(&r->grid, r->sdist.data(), 0, r->eps_in, r->eps_out, r->kappa, (int64_t)r->q.size(),
+                                r->xyz.data(), r->q.data(), &r->opt, r->stream, &sys);
+        if (s1 < 0) {
+            if (sys) ctr_ibim_destroy(sys);
+            sys = nullptr;
+            release_stream(r);
+        }
+        const int64_t real = sys ? (int64_t)handle_bytes(sys) : 0;
+        std::unique_lock<std::mutex> lk(sv->mu);
+        sv->preparing--;
+        r->sdist.clear();
+        r->sdist.shrink_to_fit();
+        if (s1 >= 0 && (sv->fatal || sv->stop)) {   // the engine is gone: nothing will run this system
+            sv->used -= r->charged;
+            r->charged = 0;
+            finish_request(sv, r, sv->fatal ? sv->fatal : CTR_ERR_INVALID);
+            lk.unlock();
+            ctr_ibim_destroy(sys);
+            release_stream(r);
+            break;
+        }
+        if (s1 < 0) {
+            sv->used -= r->charged;
+            r->charged = 0;
+            finish_request(sv, r, s1);
+        } else {
+            // charge the real allocation instead of the estimate
+            sv->used += real - r->charged;
+            r->charged = real;
+            r->sys = sys;
+            sv->ready.push_back(r);
+            sv->peak_used = std::max(sv->peak_used, sv->used);
+        }
+        sv->cv_work.notify_all();
+    }
+}
+
+// Worker thread: owns the engine; admits ready systems, steps, retires.
 void worker_loop(ctr_server* sv) {
     cudaSetDevice(sv->device);
     std::vector<SlotStat> st;
     for (;;) {
-        // ---- admission (under the lock: pick; setup outside the lock)
-        Request* admit = nullptr;
+        std::deque<Request*> take;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             if (sv->stop) break;
-            if (sv->running.empty() && sv->waiting.empty()) {
-                sv->cv_work.wait(lk, [&] { return sv->stop || !sv->waiting.empty(); });
-                if (sv->stop) break;
-            }
-            if (!sv->waiting.empty() && (int)sv->running.size() < sv->cap) {
-                Request* head = sv->waiting.front();
-                const int64_t need = estimate_bytes(*head);
-                if (sv->used + need <= sv->budget || sv->running.empty()) {
-                    sv->waiting.pop_front();
-                    head->charged = need;
-                    sv->used += need;
-                    admit = head;
-                }
-            }
+            if (sv->running.empty() && sv->ready.empty())
+                sv->cv_work.wait(lk, [&] { return sv->stop || !sv->ready.empty(); });
+            if (sv->stop) break;
+            take.swap(sv->ready);
         }
-        if (admit) {
-            admit->res.t_admit = now_s();
-            ctr_ibim* sys = nullptr;
-            int s1 = ctr_ibim_setup(&admit->grid, admit->sdist.data(), 0, admit->eps_in, admit->eps_out, admit->kappa,
-                                    (int64_t)admit->q.size(), admit->xyz.data(), admit->q.data(), &admit->opt,
-                                    nullptr, &sys);
+        for (Request* r : take) {
             int slot = -1;
-            if (s1 >= 0) s1 = engine_admit(sv->engine, sys, &slot);
-            std::lock_guard<std::mutex> lk(sv->mu);
-            admit->sdist.clear();
-            admit->sdist.shrink_to_fit();
+            const int s1 = engine_admit(sv->engine, r->sys, &slot);
             if (s1 < 0) {
-                if (sys) ctr_ibim_destroy(sys);
-                sv->used -= admit->charged;
-                admit->res.status = s1;
-                finish_request(sv, admit, s1);
+                ctr_ibim_destroy(r->sys);
+                release_stream(r);
+            }
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (s1 < 0) {
+                r->sys = nullptr;
+                sv->used -= r->charged;
+                r->charged = 0;
+                finish_request(sv, r, s1);
+                sv->cv_work.notify_all();
             } else {
-                // charge the real allocation instead of the estimate
-                const int64_t real = (int64_t)handle_bytes(sys);
-                sv->used += real - admit->charged;
-                admit->charged = real;
-                admit->sys = sys;
-                admit->slot = slot;
-                sv->running.push_back(admit);
-                sv->peak_used = std::max(sv->peak_used, sv->used);
+                r->slot = slot;
+                sv->running.push_back(r);
                 sv->peak_slots = std::max(sv->peak_slots, (int)sv->running.size());
             }
-            continue;   // admit as many as fit before the next step
         }
-        // ---- one engine step for every admitted system
         bool any;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
@@ -208,13 +268,30 @@ void worker_loop(ctr_server* sv) {
         const int rs = engine_step(sv->engine, &st);
         std::vector<Request*> finished;
         if (rs < 0) {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            sv->fatal = rs;
-            sv->fatal_msg = ctr_last_error();
-            for (Request* r : sv->running) finish_request(sv, r, rs);
-            sv->running.clear();
-            for (Request* r : sv->waiting) finish_request(sv, r, rs);
-            sv->waiting.clear();
+            std::vector<Request*> drop;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                sv->fatal = rs;
+                sv->fatal_msg = ctr_last_error();
+                for (Request* r : sv->running) {
+                    finish_request(sv, r, rs);
+                    drop.push_back(r);
+                }
+                sv->running.clear();
+                for (Request* r : sv->ready) {
+                    finish_request(sv, r, rs);
+                    drop.push_back(r);
+                }
+                sv->ready.clear();
+                for (Request* r : sv->waiting) finish_request(sv, r, rs);
+                sv->waiting.clear();
+                sv->cv_work.notify_all();   // the setup thread stops
+            }
+            for (Request* r : drop) {
+                if (r->sys) ctr_ibim_destroy(r->sys);
+                r->sys = nullptr;
+                release_stream(r);
+            }
             break;
         }
         retire_done(sv, st, finished);
@@ -225,6 +302,7 @@ void worker_loop(ctr_server* sv) {
             sv->used -= r->charged;
             finish_request(sv, r, r->res.status);
         }
+        if (!finished.empty()) sv->cv_work.notify_all();   // slots and memory were freed
     }
 }
 
@@ -271,6 +349,7 @@ int ctr_server_create(const ctr_server_options* opt, ctr_server** out) {
     }
     sv->engine->vec_blocks = 1;
     sv->worker = std::thread(worker_loop, sv);
+    sv->setup = std::thread(setup_loop, sv);
     *out = sv;
     return CTR_OK;
 }
@@ -292,6 +371,7 @@ int ctr_server_submit(ctr_server* sv, const ctr_grid* grid, const double* sdist,
     r->q.assign(charge_q ? charge_q : nullptr, charge_q ? charge_q + n_charges : nullptr);
     ctr_default_options(&r->opt);
     if (opt) r->opt = *opt;
+    r->need = estimate_bytes(*r);   // outside the lock: it scans the grid
     r->res.t_submit = now_s();
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->fatal) {
@@ -366,7 +446,7 @@ int ctr_server_stats(ctr_server* sv, ctr_server_stats_t* out) {
     out->peak_used_bytes = sv->peak_used;
     out->peak_slots = sv->peak_slots;
     out->running = (int)sv->running.size();
-    out->waiting = (int)sv->waiting.size();
+    out->waiting = (int)(sv->waiting.size() + sv->ready.size()) + sv->preparing;
     out->steps = sv->steps;
     return CTR_OK;
 }
@@ -378,9 +458,14 @@ void ctr_server_destroy(ctr_server* sv) {
         sv->stop = true;
     }
     sv->cv_work.notify_all();
+    if (sv->setup.joinable()) sv->setup.join();
     if (sv->worker.joinable()) sv->worker.join();
-    for (Request* r : sv->running)
-        if (r->sys) ctr_ibim_destroy(r->sys);
+    for (std::vector<Request*> q : {sv->running, std::vector<Request*>(sv->ready.begin(), sv->ready.end())})
+        for (Request* r : q) {
+            if (r->sys) ctr_ibim_destroy(r->sys);
+            r->sys = nullptr;
+            release_stream(r);
+        }
     for (auto& kv : sv->all) delete kv.second;
     delete sv->engine;
     delete sv;
