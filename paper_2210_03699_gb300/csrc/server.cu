@@ -184,7 +184,10 @@ void setup_loop(ctr_server* sv) {
         }
         r->res.t_admit = now_s();
         ctr_ibim* sys = nullptr;
-        int s1 = (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess)
+        // highest priority: setup kernels go ahead of the engine's queued ones between its launches
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        int s1 = (cudaStreamCreateWithPriority(&r->stream, cudaStreamNonBlocking, hi) == cudaSuccess)
                      ? CTR_OK
                      : fail(CTR_ERR_CUDA, "stream create");
         if (s1 >= 0)
