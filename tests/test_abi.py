@@ -53,3 +53,9 @@ def test_invalid_arguments_rejected_without_gpu(library):
     st = ctr.lib.ctr_ibim_setup(None, None, 0, 1.0, 80.0, 0.1, 0, None, None, None, None, ctypes.byref(h))
     assert st == -1 and h.value is None
     assert b"NULL" in ctr.lib.ctr_last_error()
+    # inspection entry points reject missing handles and arguments before touching the GPU
+    i64 = ctypes.c_int64()
+    assert ctr.lib.ctr_ibim_pair_schedule(None, ctr.FP32_REFINE, ctypes.byref(i64), None, None, None) == -1
+    v = ctypes.c_int()
+    assert ctr.lib.ctr_tuning_info(None, ctypes.byref(v), ctypes.byref(v)) == -1
+    assert ctr.lib.ctr_ibim_matvec(None, None, None, ctr.FP32_REFINE, 0) == -1
