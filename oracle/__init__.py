@@ -17,6 +17,8 @@ Modules:
   gmres       textbook GMRES (modified Gram-Schmidt, Givens rotations)
   energy      reaction potential Eq. (2.31) and polarization energy Eq. (3.3)
   exact       closed forms used as pins (sphere solution, Kirkwood energy)
+  treecode    far-field acceleration of the dense sum (Sec. 2.5): Chebyshev
+              interpolation on well-separated clusters of an integer octree
 
 Every parity-relevant function names the passage it follows.  Parity
 status of each function is listed in the module docstrings.

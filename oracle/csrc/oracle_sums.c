@@ -202,6 +202,92 @@ void oracle_punctured_lattice_many(int64_t n_pts, const double* alpha, const dou
         oracle_punctured_lattice(alpha[p], beta[p], h, r0, kmax, kstep, re + p * nk, im + p * nk);
 }
 
+/*
+ * Far-field acceleration of the punctured sum (the fast summation of K v inside
+ * GMRES, Sec. 2.5), evaluation loops of oracle/treecode.py.  Tree positions
+ * p = 0..M-1 hold node perm[p]; target block I is the positions
+ * [I*BS, min(M, (I+1)*BS)).
+ *
+ * Near field: for target i in block I, the punctured sum of Eqs. (2.14)-(2.15)
+ * over the sources at the positions of the block's near ranges
+ * [near_rng[2r], near_rng[2r+1]), r in [near_ptr[I], near_ptr[I+1]).
+ * Results go to out1/out2 at the original index i (overwritten).
+ */
+void oracle_tree_near(int64_t M, const double* P, const double* N, const double* W,
+                      const double* rho1, const double* rho2, double h, double kappa, double ratio_EI,
+                      const int64_t* excl_ptr, const int64_t* excl_idx, const int64_t* perm, int64_t BS,
+                      const int64_t* near_ptr, const int64_t* near_rng, double* out1, double* out2) {
+    double h3 = h * h * h;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < M; ++p) {
+        int64_t i = perm[p], I = p / BS;
+        acc_t a1 = {0, 0}, a2 = {0, 0};
+        for (int64_t r = near_ptr[I]; r < near_ptr[I + 1]; ++r) {
+            for (int64_t q = near_rng[2 * r]; q < near_rng[2 * r + 1]; ++q) {
+                int64_t j = perm[q];
+                int skip = 0;
+                for (int64_t e = excl_ptr[i]; e < excl_ptr[i + 1]; ++e)
+                    if (excl_idx[e] == j) skip = 1;
+                if (skip) continue;
+                double K[4];
+                pb_kernels(P + 3 * i, N + 3 * i, P + 3 * j, N + 3 * j, kappa, ratio_EI, K);
+                double w = h3 * W[j];
+                acc_add(&a1, w * (K[0] * rho1[j] - K[1] * rho2[j]));
+                acc_add(&a2, w * (K[2] * rho1[j] - K[3] * rho2[j]));
+            }
+        }
+        out1[i] = acc_get(&a1);
+        out2[i] = acc_get(&a2);
+    }
+}
+
+/*
+ * Far field: for target i in block I and every cluster c = far_cl[r],
+ * r in [far_ptr[I], far_ptr[I+1]), the sum over the cluster's proxy points
+ * s_k = (sx[c][0][k1], sx[c][1][k2], sx[c][2][k3]), k = (k3 n1 + k2) n1 + k1, of
+ *   out1 += G0(P_i, s_k) Q[c][0][k] + Gk(P_i, s_k) Q[c][1][k]
+ *   out2 += dG0/dn_x(P_i, s_k) Q[c][0][k] + dGk/dn_x(P_i, s_k) Q[c][2][k]
+ * with G0 = 1/(4 pi r), Gk = e^{-kappa r}/(4 pi r), d/dn_x = n_i . grad_x.
+ * sx is [n_far][3][n1], Q is [n_far][3][n1^3].  Results are added to out1/out2
+ * at the original index i.
+ */
+void oracle_tree_far(int64_t M, const double* P, const double* N, double kappa, const int64_t* perm,
+                     int64_t BS, const int64_t* far_ptr, const int64_t* far_cl, int64_t n1, const double* sx,
+                     const double* Q, double* out1, double* out2) {
+    double fourpi = 4.0 * M_PI;
+    int64_t np = n1 * n1 * n1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < M; ++p) {
+        int64_t i = perm[p], I = p / BS;
+        const double* x = P + 3 * i;
+        const double* nx = N + 3 * i;
+        acc_t a1 = {0, 0}, a2 = {0, 0};
+        for (int64_t r = far_ptr[I]; r < far_ptr[I + 1]; ++r) {
+            int64_t c = far_cl[r];
+            const double* s = sx + c * 3 * n1;
+            const double* q = Q + c * 3 * np;
+            for (int64_t k3 = 0; k3 < n1; ++k3)
+                for (int64_t k2 = 0; k2 < n1; ++k2)
+                    for (int64_t k1 = 0; k1 < n1; ++k1) {
+                        int64_t k = (k3 * n1 + k2) * n1 + k1;
+                        double d[3] = {x[0] - s[k1], x[1] - s[n1 + k2], x[2] - s[2 * n1 + k3]};
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        double rr = sqrt(r2);
+                        double E = exp(-kappa * rr);
+                        double dnx = d[0] * nx[0] + d[1] * nx[1] + d[2] * nx[2];
+                        double G0 = 1.0 / (fourpi * rr);
+                        double Gk = E / (fourpi * rr);
+                        double dG0_dnx = -dnx / (fourpi * r2 * rr);
+                        double dGk_dnx = -E * (1.0 + kappa * rr) * dnx / (fourpi * r2 * rr);
+                        acc_add(&a1, G0 * q[k] + Gk * q[np + k]);
+                        acc_add(&a2, dG0_dnx * q[k] + dGk_dnx * q[2 * np + k]);
+                    }
+        }
+        out1[i] += acc_get(&a1);
+        out2[i] += acc_get(&a2);
+    }
+}
+
 #ifdef _OPENMP
 #include <omp.h>
 void oracle_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }

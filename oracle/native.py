@@ -57,6 +57,12 @@ def lib():
                                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                         _D, _D]
             L.oracle_punctured_lattice_many.restype = None
+            L.oracle_tree_near.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, _I, _I, _I, ctypes.c_int64, _I, _I, _D, _D]
+            L.oracle_tree_near.restype = None
+            L.oracle_tree_far.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, _I, ctypes.c_int64, _I, _I,
+                                          ctypes.c_int64, _D, _D, _D, _D]
+            L.oracle_tree_far.restype = None
             L.oracle_set_threads.argtypes = [ctypes.c_int]
             L.oracle_set_threads.restype = None
             L.oracle_max_threads.argtypes = []
