@@ -45,6 +45,10 @@ OPS_FP64 = {"one": 69, "sym": 69}
 # ncu capture (profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt); None at any other size, or once
 # the kernels change.
 TRAFFIC_H005 = {"fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
+# Treecode far field (FP32): FMA-pipe lane operations per proxy evaluation counted from the kernel source
+# (tree.cuh, far_terms: 2 sub/mul + 5 fma + 6 mul), plus 2 SFU operations (rsqrt, ex2).
+OPS_FAR = 13
+SFU_FAR = 2
 
 
 def parse():
@@ -58,11 +62,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the baseline sample")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels", "tree"],
                     help="solve: the default single-system line; batch: many molecules in one engine; "
                          "serve: continuous-batching server under Poisson arrivals; kernels: two FP32, two "
                          "float-float and two FP64 operator applications of the ellipsoid at --h (the profiling "
-                         "case)")
+                         "case); tree: the solve step with the far-field treecode on the ellipsoid at --tree-h")
+    ap.add_argument("--tree-h", type=float, default=0.025, help="tree mode: grid spacing (0.025: ~714k nodes)")
+    ap.add_argument("--tree-tol", type=float, default=1e-6,
+                    help="tree mode: solve tolerance (the FP32 far field sets a floor near 2e-7)")
+    ap.add_argument("--tree-direct", action="store_true",
+                    help="tree mode: also time the direct-sum applications at the same size")
     ap.add_argument("--molecules", type=int, default=64, help="batch mode: molecules in the batch")
     ap.add_argument("--max-atoms", type=int, default=2000, help="batch/serve: largest molecule")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per load level")
@@ -391,18 +400,139 @@ def run_kernels(args, ctr):
     print(json.dumps(out), flush=True)
 
 
+def run_tree(args, ctr, world):
+    """The solve step (setup, FP32-refined GMRES, energy) with the treecode far field, timed like the default
+    line; value counts M^2 per operator application, as the direct sum would evaluate."""
+    import torch
+    local = torch.cuda.current_device()
+    prob, cfg = workload(args.tree_h)
+    opts = ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE, tol=args.tree_tol,
+                       farfield=ctr.FARFIELD_TREECODE)
+    cfg["solver"] = f"fp32_refine, GMRES restart {opts.restart}, tol {opts.tol:g}"
+    cfg["farfield"] = (f"treecode degree {opts.tree_degree}, theta {opts.tree_theta}, leaf {opts.tree_leaf}; "
+                       f"value counts M^2 per operator application (the direct sum's pairs)")
+    cfg["l2"] = "256 MiB buffer written between timed steps (L2 flush, outside the step events)"
+    cfg["parallelism"] = f"replicas x{world}"
+    stream = torch.cuda.current_stream()
+    sd_dev = torch.tensor(prob.sdist, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
+            psi, dpsi, info = G.solve(device=True)
+            Gp, _ = G.energy(psi, dpsi)
+            return G.M, info, Gp
+
+    for _ in range(args.warmup):
+        M, info, Gp = step()
+    torch.cuda.synchronize()
+    ev, infos, pairs = [], [], 0.0
+    launches0 = ctr.kernel_launches()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M, info, Gp = step()
+            e1.record(stream)
+            ev.append((e0, e1))
+            infos.append(info)
+            pairs += float(M) ** 2 * (info.matvecs_fp32 + info.matvecs_fp64)
+        torch.cuda.synchronize()
+    launches = ctr.kernel_launches() - launches0
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    value = pairs / t_dev
+    # phases of one application per arithmetic, the treecode's work counts, unit-count peaks
+    with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
+        ph = {pr: G.time_operator(pr, reps=3) for pr in (ctr.FP32_REFINE, ctr.DF64)}
+        ff = {pr: G.farfield_info(pr) for pr in (ctr.FP32_REFINE, ctr.DF64)}
+        Mk = G.M
+    direct = None
+    if args.tree_direct:
+        with ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube), sdist=sd_dev) as D:
+            direct = {"fp32_ms": D.time_operator(ctr.FP32_REFINE, reps=1)["pairs_ms"],
+                      "df64_ms": D.time_operator(ctr.DF64, reps=1)["pairs_ms"]}
+    rate_ffma = ctypes_probe(ctr, 0)
+    rate_ex2 = ctypes_probe(ctr, 2)
+    rate_rsq = ctypes_probe(ctr, 3)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_max = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
+    rate_units = sms * 128 * f_max
+    sfu_evals = 1.0 / (1.0 / rate_ex2 + 1.0 / rate_rsq) if rate_ex2 and rate_rsq else None
+    far_peak = min(rate_units / OPS_FAR, sfu_evals) if sfu_evals else rate_units / OPS_FAR
+    i_last = infos[-1]
+    n_app = {ctr.FP32_REFINE: i_last.matvecs_fp32, ctr.DF64: i_last.matvecs_fp64}
+    step_s = t_dev / args.steps
+    kern = []
+    for pr, tag, ops in ((ctr.FP32_REFINE, "fp32", OPS_FP32["one"]), (ctr.DF64, "df64", OPS_DF64["one"])):
+        near, far = ff[pr]["near_pairs"], ff[pr]["far_evaluations"]
+        t_near, t_far = ph[pr]["pairs_ms"] * 1e-3, ph[pr]["far_ms"] * 1e-3
+        kern.append({"bound": "alu", "kernel": f"sched_kernel<{'Fp32x2' if tag == 'fp32' else 'Df64'}Policy> "
+                                               f"(treecode direct part, {tag})",
+                     "achieved": near / t_near, "peak": rate_units / ops, "unit": "pair-interactions/s",
+                     "frac": near / t_near / (rate_units / ops), "traffic": None,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {ops} lane ops per "
+                                   f"one-sided pair; measured FFMA probe {rate_ffma:.4g}/s",
+                     "t_ms": t_near * 1e3, "pairs": near, "step_share": n_app[pr] * t_near / step_s})
+        kern.append({"bound": "alu", "kernel": f"k_tree_mom + k_tree_momred + k_tree_far<float, 4, "
+                                               f"{256 if tag == 'fp32' else 64}> (treecode far field, {tag} blocks)",
+                     "achieved": far / t_far if t_far > 0 else None, "peak": far_peak,
+                     "unit": "proxy evaluations/s",
+                     "frac": far / t_far / far_peak if t_far > 0 else None, "traffic": None,
+                     "peak_basis": f"min({sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {OPS_FAR} lane ops, "
+                                   f"SFU: 1/(1/ex2 + 1/rsqrt) with the measured probes {rate_ex2:.4g}/s, "
+                                   f"{rate_rsq:.4g}/s) per proxy evaluation",
+                     "t_ms": t_far * 1e3, "evaluations": far, "step_share": n_app[pr] * t_far / step_s})
+    kern.sort(key=lambda k: -k["step_share"])
+    e2e = None
+    if not args.skip_e2e:
+        h2d = prob.sdist.nbytes + prob.charge_xyz.nbytes + prob.charge_q.nbytes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ctr.CtrIbim.from_problem(prob, options=opts) as G:
+            psi, dpsi, info_e = G.solve(device=False)
+            G.energy(psi, dpsi)
+            e2e_pairs = float(G.M) ** 2 * (info_e.matvecs_fp32 + info_e.matvecs_fp64)
+            d2h = psi.nbytes + dpsi.nbytes + 8
+        torch.cuda.synchronize()
+        e2e = {"value": e2e_pairs / (time.perf_counter() - t0), "unit": "pair-interactions/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(prob, args.cpu_seconds)
+    line = {
+        "mode": "tree", "metric": "CTR-IBIM matvec pair-interactions/s", "value": value,
+        "unit": "pair-interactions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pairs + f64", "data": "synthetic",
+        "config": dict(cfg, M=int(Mk), iterations=int(i_last.iterations), refinements=int(i_last.refinements),
+                       matvecs_fp32=int(i_last.matvecs_fp32), matvecs_fp64=int(i_last.matvecs_fp64),
+                       residual=i_last.residual, G_pol=Gp),
+        "phases_ms": {"fp32": ph[ctr.FP32_REFINE], "df64": ph[ctr.DF64]},
+        "farfield": {"fp32": {k: v for k, v in ff[ctr.FP32_REFINE].items() if k != "perm"},
+                     "df64": {k: v for k, v in ff[ctr.DF64].items() if k != "perm"}},
+        "direct_ms": direct,
+        "roofline": kern[0], "roofline_second": kern[1], "kernels": kern,
+        "probes": {"ffma": rate_ffma, "ex2": rate_ex2, "rsqrt": rate_rsq},
+        "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.mode in ("batch", "serve", "kernels"):
+    if args.mode in ("batch", "serve", "kernels", "tree"):
         import torch
         torch.cuda.set_device(local)
         import paper_2210_03699_gb300 as ctr
         if rank == 0:
-            {"batch": run_batch, "serve": run_serve, "kernels": run_kernels}[args.mode](args, ctr)
+            if args.mode == "tree":
+                run_tree(args, ctr, 1)
+            else:
+                {"batch": run_batch, "serve": run_serve, "kernels": run_kernels}[args.mode](args, ctr)
         return
     import torch
     torch.cuda.set_device(local)

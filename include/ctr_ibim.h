@@ -74,6 +74,29 @@ enum { CTR_FP64 = 0, CTR_FP32_REFINE = 1, CTR_DF64 = 2 };
  */
 enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
 
+/*
+ * Evaluation of the dense sum of Eq. (2.30) (Sec. 2.5 accelerates it with a
+ * black-box fast multipole method and gives no parameters):
+ *   CTR_FARFIELD_DIRECT    every pair, M^2 per operator application.
+ *   CTR_FARFIELD_TREECODE  a particle-cluster treecode.  An octree over the
+ *       tube nodes' integer grid indices (leaves of at most tree_leaf nodes)
+ *       orders the nodes; for each target block, a cluster that is well
+ *       separated from it (theta |c_B - c_C| > r_B + r_C on the integer boxes
+ *       widened by ceil(eps/h) grid units, decided exactly), that holds none of
+ *       the block's correction nodes and that has more than (degree+1)^3 nodes
+ *       (a sixteenth of that for the float-float arithmetic, whose direct pairs
+ *       cost about 16 FP32 proxy evaluations each)
+ *       is replaced by (degree+1)^3 tensor Chebyshev points on the tight box of
+ *       its points P carrying interpolated charges (barycentric Lagrange
+ *       interpolation of the kernels' source variable, d/dn_y on the basis);
+ *       every other pair is summed directly with the correction pairs skipped
+ *       exactly.  The error against the direct sum falls geometrically with the
+ *       degree (about 6e-8 relative at degree 10, theta 0.8).  The far field is
+ *       FP32 in the CTR_FP32_REFINE and CTR_DF64 arithmetics and FP64 in
+ *       CTR_FP64; the direct part keeps the arithmetic's pair kernels.
+ */
+enum { CTR_FARFIELD_DIRECT = 0, CTR_FARFIELD_TREECODE = 1 };
+
 typedef struct {
     int64_t n[3];       /* nodes per axis (nx, ny, nz), each >= 5 */
     double origin[3];   /* coordinates of node (0, 0, 0) */
@@ -93,6 +116,10 @@ typedef struct {
     int residual;          /* pair arithmetic of the refinement residual r = g - A x:
                               CTR_DF64 (the default of ctr_default_options) or CTR_FP64 */
     int method;            /* CTR_METHOD_HYB (default) or CTR_METHOD_KREG */
+    int farfield;          /* CTR_FARFIELD_DIRECT (default) or CTR_FARFIELD_TREECODE */
+    int tree_degree;       /* treecode interpolation degree per axis, 2..12; <= 0 selects 10 */
+    double tree_theta;     /* treecode separation parameter, 0 < theta < 1; <= 0 selects 0.8 */
+    int tree_leaf;         /* most nodes of a treecode leaf; <= 0 selects 128 */
 } ctr_options;
 
 typedef struct {
@@ -184,6 +211,53 @@ int ctr_ibim_area(const ctr_ibim* sys, double* area);
  */
 int ctr_ibim_pair_schedule(const ctr_ibim* sys, int precision, int64_t* one_sided_pairs,
                            int64_t* symmetric_pairs, int64_t* items, int64_t* partial_bytes);
+
+/*
+ * The treecode of a handle set up with farfield = CTR_FARFIELD_TREECODE, for
+ * one arithmetic (precision; its target blocks are 1024 tree positions for
+ * CTR_FP32_REFINE and 256 for CTR_DF64 and CTR_FP64).  Outputs (host, any may
+ * be NULL): perm, M int64, the node at each tree position; near_pairs, the
+ * (target, source) pairs summed directly (correction pairs included in the
+ * count, skipped in the sum); far_evaluations, targets x proxy points of
+ * their far clusters; far_interactions, (target block, far cluster) pairs;
+ * far_clusters, clusters that carry charges.  CTR_ERR_INVALID for a handle
+ * without the treecode.
+ */
+int ctr_ibim_farfield_info(const ctr_ibim* sys, int precision, int64_t* perm, int64_t* near_pairs,
+                           int64_t* far_evaluations, int64_t* far_interactions, int64_t* far_clusters);
+
+/*
+ * Profiling: `reps` applications of the operator of Eq. (2.30) in arithmetic
+ * `precision` to the right-hand side g (after one untimed application), timed
+ * with CUDA events on the handle's stream; the mean milliseconds of the
+ * phases: packing the source weights, the pair items (the whole dense sum, or
+ * the treecode's direct part), the treecode's far field (moments, charges,
+ * far items; 0 without the treecode) and the finish (correction, diagonal,
+ * partial sums).  Any output may be NULL.
+ */
+int ctr_ibim_time_operator(ctr_ibim* sys, int precision, int reps, double* pack_ms, double* pairs_ms,
+                           double* far_ms, double* finish_ms);
+
+/*
+ * The tree and interaction lists of the treecode (CTR_FARFIELD_TREECODE) as a
+ * host computation (no GPU): M nodes with integer grid indices ijk (3 int32
+ * per node), their correction sets in CSR form over the node order (excl_ptr
+ * M + 1 int32, excl int32), the box widening `margin` in grid units
+ * (ceil(eps/h)), degree (2..12), theta (0 <= theta < 1; 0 makes every pair
+ * direct), leaf (>= 1), target block size (>= 1) and min_far, the node count a
+ * well-separated cluster must exceed to be approximated (<= 0 selects
+ * (degree+1)^3; a handle uses (degree+1)^3 for its FP32 and FP64 blocks and
+ * (degree+1)^3 / 16 for its float-float blocks).  Outputs (host, any may
+ * be NULL): perm (M), n_near_ranges, n_far, near_ptr (nb + 1 with
+ * nb = ceil(M / block)), near_rng (2 per range: [begin, end) tree positions),
+ * far_ptr (nb + 1), far_begin and far_end (n_far each: the position range of
+ * each far cluster).  Call with the array outputs NULL to learn the sizes.
+ */
+int ctr_farfield_plan(int64_t M, const int32_t* ijk, const int32_t* excl_ptr, const int32_t* excl, int margin,
+                      int degree, double theta, int leaf, int block, int64_t min_far, int64_t* perm,
+                      int64_t* n_near_ranges,
+                      int64_t* n_far, int64_t* near_ptr, int64_t* near_rng, int64_t* far_ptr,
+                      int64_t* far_begin, int64_t* far_end);
 
 /*
  * y = A x for the operator of Eq. (2.30) (rows of Eqs. 2.14-2.15): the

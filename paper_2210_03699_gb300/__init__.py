@@ -28,6 +28,8 @@ FP32_REFINE = 1
 DF64 = 2
 METHOD_HYB = 0
 METHOD_KREG = 1
+FARFIELD_DIRECT = 0
+FARFIELD_TREECODE = 1
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -47,7 +49,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("tube_halfwidth", ctypes.c_double), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int),
-                ("method", ctypes.c_int)]
+                ("method", ctypes.c_int), ("farfield", ctypes.c_int), ("tree_degree", ctypes.c_int),
+                ("tree_theta", ctypes.c_double), ("tree_leaf", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -83,10 +86,15 @@ class Options:
     tile_targets: int = 0
     residual: int = DF64
     method: int = METHOD_HYB
+    farfield: int = FARFIELD_DIRECT
+    tree_degree: int = 10
+    tree_theta: float = 0.8
+    tree_leaf: int = 128
 
     def _c(self) -> _Options:
         return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
-                        self.max_refine, self.inner_tol, self.tile_targets, self.residual, self.method)
+                        self.max_refine, self.inner_tol, self.tile_targets, self.residual, self.method,
+                        self.farfield, self.tree_degree, self.tree_theta, self.tree_leaf)
 
 
 @dataclasses.dataclass
@@ -148,6 +156,11 @@ def _load():
         "ctr_kernel_launches": (ctypes.c_int64, []),
         "ctr_ibim_pair_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 4),
         "ctr_tuning_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)] * 3),
+        "ctr_ibim_farfield_info": (ctypes.c_int, [P, ctypes.c_int, P] + [_I64] * 4),
+        "ctr_ibim_time_operator": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int] + [_D] * 4),
+        "ctr_farfield_plan": (ctypes.c_int, [ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, _I64, _I64, P, P, P,
+                                             P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -290,6 +303,21 @@ class CtrIbim:
         _check(lib.ctr_ibim_pair_schedule(self._h, int(precision), *[ctypes.byref(x) for x in v]))
         return {"one_sided_pairs": v[0].value, "symmetric_pairs": v[1].value, "items": v[2].value,
                 "partial_bytes": v[3].value}
+
+    def farfield_info(self, precision: int = FP32_REFINE) -> dict:
+        """The treecode of this handle for one arithmetic (see ctr_ibim_farfield_info)."""
+        perm = np.empty(self.M, dtype=np.int64)
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib.ctr_ibim_farfield_info(self._h, int(precision), perm.ctypes.data_as(ctypes.c_void_p),
+                                          *[ctypes.byref(x) for x in v]))
+        return {"perm": perm, "near_pairs": v[0].value, "far_evaluations": v[1].value,
+                "far_interactions": v[2].value, "far_clusters": v[3].value}
+
+    def time_operator(self, precision: int = FP32_REFINE, reps: int = 3) -> dict:
+        """Mean milliseconds of the operator's phases over `reps` applications (see ctr_ibim_time_operator)."""
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(lib.ctr_ibim_time_operator(self._h, int(precision), int(reps), *[ctypes.byref(x) for x in v]))
+        return {"pack_ms": v[0].value, "pairs_ms": v[1].value, "far_ms": v[2].value, "finish_ms": v[3].value}
 
     def area(self) -> float:
         a = ctypes.c_double()
@@ -480,6 +508,36 @@ def tuning_info():
     R, V, U = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib.ctr_tuning_info(ctypes.byref(R), ctypes.byref(V), ctypes.byref(U)))
     return int(R.value), int(V.value), int(U.value)
+
+
+def farfield_plan(ijk, excl_ptr, excl, margin: int, degree: int = 10, theta: float = 0.8, leaf: int = 128,
+                  block: int = 256, min_far: int = 0) -> dict:
+    """Host-only tree and interaction lists of the treecode (see ctr_farfield_plan); no GPU needed.
+
+    ijk: (M, 3) integer grid indices of the nodes; excl_ptr / excl: their correction sets (CSR);
+    min_far <= 0 selects (degree + 1)^3."""
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    ep = np.ascontiguousarray(excl_ptr, dtype=np.int32)
+    ex = np.ascontiguousarray(excl, dtype=np.int32)
+    M = ijk.shape[0]
+    if ex.size == 0:
+        ex = np.zeros(1, dtype=np.int32)
+    c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    n_near, n_far = ctypes.c_int64(), ctypes.c_int64()
+    args = (M, c(ijk), c(ep), c(ex), int(margin), int(degree), float(theta), int(leaf), int(block), int(min_far))
+    _check(lib.ctr_farfield_plan(*args, None, ctypes.byref(n_near), ctypes.byref(n_far), None, None, None, None,
+                                 None))
+    nb = (M + block - 1) // block
+    perm = np.empty(M, dtype=np.int64)
+    near_ptr = np.empty(nb + 1, dtype=np.int64)
+    near_rng = np.empty(2 * max(1, n_near.value), dtype=np.int64)
+    far_ptr = np.empty(nb + 1, dtype=np.int64)
+    fb = np.empty(max(1, n_far.value), dtype=np.int64)
+    fe = np.empty(max(1, n_far.value), dtype=np.int64)
+    _check(lib.ctr_farfield_plan(*args, c(perm), ctypes.byref(n_near), ctypes.byref(n_far), c(near_ptr),
+                                 c(near_rng), c(far_ptr), c(fb), c(fe)))
+    return {"perm": perm, "near_ptr": near_ptr, "near_rng": near_rng[:2 * n_near.value].reshape(-1, 2),
+            "far_ptr": far_ptr, "far_begin": fb[:n_far.value], "far_end": fe[:n_far.value]}
 
 
 def kernel_launches() -> int:

@@ -75,6 +75,10 @@ void ctr_default_options(ctr_options* o) {
     o->tile_targets = 0;
     o->residual = CTR_DF64;
     o->method = CTR_METHOD_HYB;
+    o->farfield = CTR_FARFIELD_DIRECT;
+    o->tree_degree = 10;
+    o->tree_theta = 0.8;
+    o->tree_leaf = 128;
 }
 
 const char* ctr_status_string(int st) {
@@ -143,6 +147,14 @@ int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_devic
                 return fail(CTR_ERR_INVALID, "residual must be CTR_FP64 or CTR_DF64");
             if (o.method != CTR_METHOD_HYB && o.method != CTR_METHOD_KREG)
                 return fail(CTR_ERR_INVALID, "method must be CTR_METHOD_HYB or CTR_METHOD_KREG");
+            if (o.farfield != CTR_FARFIELD_DIRECT && o.farfield != CTR_FARFIELD_TREECODE)
+                return fail(CTR_ERR_INVALID, "farfield must be CTR_FARFIELD_DIRECT or CTR_FARFIELD_TREECODE");
+            if (o.tree_degree <= 0) o.tree_degree = 10;
+            if (!(o.tree_theta > 0.0)) o.tree_theta = 0.8;
+            if (o.tree_leaf <= 0) o.tree_leaf = 128;
+            if (o.tree_degree < 2 || o.tree_degree > 12) return fail(CTR_ERR_INVALID, "tree_degree must be 2..12");
+            if (!(o.tree_theta < 1.0)) return fail(CTR_ERR_INVALID, "tree_theta must be below 1");
+            if (o.tree_leaf > (1 << 20)) return fail(CTR_ERR_INVALID, "tree_leaf must be <= 2^20");
         }
         if (o.restart > 1000) return fail(CTR_ERR_INVALID, "restart must be <= 1000");
         ctr_ibim* s = new ctr_ibim();
@@ -297,6 +309,57 @@ int ctr_ibim_pair_schedule(const ctr_ibim* s, int precision, int64_t* one_sided,
     if (items) *items = (int64_t)p.items.size();
     if (partial_bytes) *partial_bytes = p.part_doubles * (int64_t)sizeof(double);
     return CTR_OK;
+}
+
+int ctr_ibim_farfield_info(const ctr_ibim* s, int precision, int64_t* perm, int64_t* near_pairs,
+                           int64_t* far_evaluations, int64_t* far_interactions, int64_t* far_clusters) {
+    if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
+    if (!s->tree) return fail(CTR_ERR_INVALID, "handle was set up without the treecode");
+    if (precision != CTR_FP32_REFINE && precision != CTR_DF64 && precision != CTR_FP64)
+        return fail(CTR_ERR_INVALID, "precision");
+    const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
+    const ctr::TreeData& t = *s->tree;
+    if (perm)
+        for (int64_t p = 0; p < s->M; ++p) perm[p] = t.perm[(size_t)p];
+    if (near_pairs) *near_pairs = t.pol[pol].near_pairs;
+    if (far_evaluations) *far_evaluations = t.pol[pol].far_evals;
+    if (far_interactions) *far_interactions = t.pol[pol].far_pairs;
+    if (far_clusters) *far_clusters = t.pol[pol].nq;
+    return CTR_OK;
+}
+
+int ctr_ibim_time_operator(ctr_ibim* s, int precision, int reps, double* pack_ms, double* pairs_ms,
+                           double* far_ms, double* finish_ms) {
+    return guarded([&]() -> int {
+        if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
+        if (reps < 1) return fail(CTR_ERR_INVALID, "reps must be >= 1");
+        if (precision != CTR_FP32_REFINE && precision != CTR_DF64 && precision != CTR_FP64)
+            return fail(CTR_ERR_INVALID, "precision");
+        CTR_TRY(use_device(s));
+        const int64_t n = 2 * s->M;
+        double* y = s->vecs.as<double>() + 5 * n;   // the last solver vector as scratch
+        cudaEvent_t ev[5];
+        for (auto& e : ev) CTR_CUDA_TRY(cudaEventCreate(&e));
+        double acc[4] = {0, 0, 0, 0};
+        int st = CTR_OK;
+        for (int r = 0; r <= reps && st == CTR_OK; ++r) {   // the first application warms up
+            st = apply_operator_timed(s, s->rhs.as<double>(), y, precision, ev);
+            if (st == CTR_OK && cudaEventSynchronize(ev[4]) != cudaSuccess) st = fail(CTR_ERR_CUDA, "event sync");
+            for (int k = 0; k < 4 && st == CTR_OK && r > 0; ++k) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) st = fail(CTR_ERR_CUDA, "event time");
+                acc[k] += ms;
+            }
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        CTR_TRY(st);
+        CTR_TRY(check_device_error(s, "time_operator"));
+        if (pack_ms) *pack_ms = acc[0] / reps;
+        if (pairs_ms) *pairs_ms = acc[1] / reps;
+        if (far_ms) *far_ms = acc[2] / reps;
+        if (finish_ms) *finish_ms = acc[3] / reps;
+        return CTR_OK;
+    });
 }
 
 int ctr_ibim_area(const ctr_ibim* s, double* area) {

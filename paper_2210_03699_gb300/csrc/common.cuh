@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdio>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -138,6 +139,66 @@ struct PairSchedule {
     DevBuf d_items, d_rptr, d_recs;
 };
 
+// ---------------------------------------------------------------- far field (treecode)
+constexpr int kTreeMaxN1 = 13;                                        // degree <= 12
+constexpr int kTreeMaxNp = kTreeMaxN1 * kTreeMaxN1 * kTreeMaxN1;
+
+// Far item: target block I against the far clusters flist[l0 .. l1); sums to the
+// partial region at ibase (2 x BS doubles, like a one-sided pair item).
+struct FarItem {
+    int32_t I, l0, l1, pad;
+    int64_t ibase;
+};
+// Moment chunk: the tree positions [j0, j1) of far cluster q (compact index).
+struct MomChunk {
+    int32_t q, j0, j1, pad;
+};
+
+// Device view of a handle's far-field data, per pair arithmetic p (0 FP32,
+// 1 float-float, 2 FP64; charges and far sums are FP32 for p < 2, FP64 for p = 2).
+struct TreeView {
+    int on = 0;
+    int M = 0, n1 = 0, np = 0;
+    const int32_t* tinv = nullptr;        // node -> tree position
+    const double* xref = nullptr;         // n1 Chebyshev points cos(m pi / n)
+    const double* bw = nullptr;           // n1 barycentric weights
+    const double* dref = nullptr;         // n1 x n1 differentiation matrix, D[m * n1 + q] = l_q'(x_m)
+    const double* box[3] = {};            // per far cluster: centre[3], half-width[3]
+    const MomChunk* chunks[3] = {};
+    const int32_t* cptr[3] = {};          // chunks of far cluster q: [cptr[q], cptr[q+1])
+    void* mpart[3] = {};                  // per chunk: D[np], S[np]
+    void* mom[3] = {};                    // per far cluster: Q0[np], Qk[np], Qk'[np]
+    const FarItem* far[3] = {};
+    const int32_t* flist[3] = {};         // far cluster (compact index) lists
+    const float4* src32 = nullptr;        // the handle's packed sources, tree order
+    const float4* srcdf = nullptr;
+    const double4* src64 = nullptr;
+    double* part = nullptr;               // partial regions (shared with the pair items)
+    int BS[3] = {};
+    double c1 = 1.0, c2 = 1.0, kappa = 0.0;
+};
+
+// Host side of a handle's treecode (owns the device buffers the view points to).
+struct TreeData {
+    int degree = 10, leaf = 128, g = 2, n1 = 11, np = 1331;
+    double theta = 0.8;
+    int64_t n_clusters = 0;
+    std::vector<int32_t> perm;            // node at each tree position
+    DevBuf d_tinv, d_eptr, d_excl;        // node -> position; exclusion CSR in tree positions
+    DevBuf d_xref, d_bw, d_dref, d_counters, d_view;
+    struct Pol {
+        int nq = 0;                                      // far clusters with charges
+        int64_t near_pairs = 0, far_evals = 0, far_pairs = 0;
+        std::vector<FarItem> far;                        // device order (decreasing cost)
+        std::vector<double> far_cost;
+        std::vector<MomChunk> chunks;                    // device order (decreasing cost)
+        std::vector<double> chunk_cost;
+        DevBuf d_box, d_chunks, d_cptr, d_mpart, d_mom, d_far, d_flist;
+        DevBuf d_ent_mom, d_ent_red, d_ent_far;          // single-system work entries {0, index}
+    } pol[3];
+    TreeView view;                        // host copy of d_view
+};
+
 // Per-handle GMRES workspace.
 struct Krylov {
     int m = 0;           // restart length
@@ -184,6 +245,7 @@ struct ctr_ibim {
     ctr::PairSchedule sched[3];   // pair schedules: [0] FP32, [1] float-float, [2] FP64
     ctr::DevBuf counter;          // int [4] work counters of the single-system launches
     ctr::Krylov kr;
+    std::unique_ptr<ctr::TreeData> tree;   // far-field acceleration (farfield = CTR_FARFIELD_TREECODE)
 };
 
 namespace ctr {
@@ -197,9 +259,15 @@ int weight_tables_cached(int device, cudaStream_t st, const double** out);
 int setup_corrections(ctr_ibim* s, const double* d_tables, const int32_t* d_node_of);
 // pairsum.cu
 int plan_pairs(ctr_ibim* s);
+// tree.cu: the treecode of a handle (tree order, schedules, far-field data) and its
+// single-system far-field launches for pair arithmetic pol
+int build_tree_schedules(ctr_ibim* s, const int slots[3]);
+int launch_tree(ctr_ibim* s, int pol);
+int64_t tree_bytes(const ctr_ibim* s);
 // schedule.cu: symmetric / one-sided pair schedules of a handle
 int build_schedules(ctr_ibim* s, const int slots[3]);
 int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision);
+int apply_operator_timed(ctr_ibim* s, const double* d_x, double* d_y, int precision, cudaEvent_t* ev);
 // krylov.cu: solver workspace
 // energy.cu
 int reaction_potential(ctr_ibim* s, const double* d_psi, const double* d_dpsi, int64_t npts,

@@ -30,6 +30,7 @@
 
 #include "engine.cuh"
 #include "pairkern.cuh"
+#include "tree.cuh"
 
 namespace ctr {
 
@@ -81,7 +82,7 @@ __global__ void k_prep_inner(SlotDev* S) {
         const double z1 = v[t] * s.il1, z2 = v[M + t] * s.il2;
         s.z[t] = z1;
         s.z[M + t] = z2;
-        pack_weights(s, s.inner_prec, t, s.scale * s.W[t] * z1, s.scale * s.W[t] * z2);
+        pack_weights(s, s.inner_prec, s.tinv ? (int64_t)s.tinv[t] : t, s.scale * s.W[t] * z1, s.scale * s.W[t] * z2);
     }
 }
 
@@ -100,7 +101,7 @@ __global__ void k_update_x(SlotDev* S) {
         const double x1 = s.x[t] + v1 * s.il1, x2 = s.x[M + t] + v2 * s.il2;
         s.x[t] = x1;
         s.x[M + t] = x2;
-        pack_weights(s, s.res_prec, t, s.scale * s.W[t] * x1, s.scale * s.W[t] * x2);
+        pack_weights(s, s.res_prec, s.tinv ? (int64_t)s.tinv[t] : t, s.scale * s.W[t] * x1, s.scale * s.W[t] * x2);
     }
 }
 
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
         if constexpr (kShared) {
-            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, pkc, err, sm.ring,
+            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.part, pkc, err, sm.ring,
                                            sm.jred, sm.tab, bar, gt))
                 return;
         } else {
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
             }
             __syncthreads();
             const PairConsts k = kc;   // block-uniform register copy: no shared loads in the pair loops
-            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.cptr, s.excl, s.part, k, err, sm.ring,
+            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.part, k, err, sm.ring,
                                            sm.jred, sm.tab, bar, gt))
                 return;
         }
@@ -170,7 +171,7 @@ __global__ void k_finish(SlotDev* S, int half) {
     double* out = (half == 0) ? s.V + (size_t)(s.j + 1) * s.n : s.r;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         double s1 = 0.0, s2 = 0.0;
-        gather_partials(s.recs[pol], s.rptr[pol], s.BS[pol], s.part, i, s1, s2);
+        gather_partials(s.recs[pol], s.rptr[pol], s.BS[pol], s.part, s.tinv ? (int64_t)s.tinv[i] : i, s1, s2);
         double c1 = 0.0, c2 = 0.0;
         for (int e = s.cptr[i]; e < s.cptr[i + 1]; ++e) {
             const int m = s.cnode[e];
@@ -391,6 +392,59 @@ int launch_persistent(Engine* e, int pol, int half, int prec) {
                              : launch_persistent_k<Policy, R, V, U, false>(e, pol, half, prec);
 }
 
+// Treecode entries of a slot in this half's arithmetic (filtered by the slot's state at run time).
+struct EngineTreeAcc {
+    const SlotDev* S;
+    int half, prec;
+    __device__ const TreeView* view(int q) const {
+        const SlotDev& s = S[q];
+        const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec) : (update_active(s) && s.res_prec == prec);
+        return (want && s.tv.on) ? &s.tv : nullptr;
+    }
+};
+
+template <typename Real, int R, int NT>
+int launch_tree_engine(Engine* e, int pol, int half, int prec) {
+    static std::mutex mu;
+    static int per_dev[64] = {0};
+    int dev = 0;
+    CTR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
+    const int smem = (int)tree_far_smem<Real>();
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (per_dev[dev] == 0) {
+            CTR_CUDA_TRY(cudaFuncSetAttribute(k_tree_far<Real, R, NT, EngineTreeAcc>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            int b = 0;
+            CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tree_far<Real, R, NT, EngineTreeAcc>,
+                                                                       NT, smem));
+            per_dev[dev] = std::max(1, b);
+        }
+    }
+    const EngineTreeAcc acc{e->slots.as<SlotDev>(), half, prec};
+    const int* cnt = e->tree_cnt.as<int>() + 3 * pol;
+    int* ctr = e->tree_counters.as<int>() + 4 * pol + 2 * half;
+    k_tree_mom<Real, EngineTreeAcc><<<2 * e->sms, kThreads, 0, e->stream>>>(acc, e->tree_ent[pol][0].as<int2>(), cnt,
+                                                                          ctr, pol);
+    CTR_LAUNCHED();
+    k_tree_momred<Real, EngineTreeAcc><<<4 * e->sms, kThreads, 0, e->stream>>>(acc, e->tree_ent[pol][1].as<int2>(),
+                                                                             cnt + 1, pol);
+    CTR_LAUNCHED();
+    k_tree_far<Real, R, NT, EngineTreeAcc><<<per_dev[dev] * e->sms, NT, smem, e->stream>>>(
+        acc, e->tree_ent[pol][2].as<int2>(), cnt + 2, ctr + 1, pol);
+    CTR_LAUNCHED();
+    return CTR_OK;
+}
+
+int launch_trees(Engine* e, int half) {
+    if (!e->any_tree) return CTR_OK;
+    CTR_TRY((launch_tree_engine<float, kTreeR[0], kTreeNT[0]>(e, 0, half, CTR_FP32_REFINE)));
+    CTR_TRY((launch_tree_engine<float, kTreeR[1], kTreeNT[1]>(e, 1, half, CTR_DF64)));
+    CTR_TRY((launch_tree_engine<double, kTreeR[2], kTreeNT[2]>(e, 2, half, CTR_FP64)));
+    return CTR_OK;
+}
+
 int launch_fp32(Engine* e, int half) {
     switch (e->var32) {
         case 1: return launch_persistent<Fp32x2Policy, kR32, 4, 1>(e, 0, half, CTR_FP32_REFINE);
@@ -449,6 +503,10 @@ int engine_create(int device, int cap, Engine** out) {
     if ((st = e->stats.alloc(sizeof(SlotStat) * cap)) < 0) return bad(st);
     if ((st = e->n_items.alloc(sizeof(int) * 4)) < 0) return bad(st);
     if ((st = e->counters.alloc(sizeof(int) * 8)) < 0) return bad(st);
+    if ((st = e->tree_cnt.alloc(sizeof(int) * 9)) < 0) return bad(st);
+    if ((st = e->tree_counters.alloc(sizeof(int) * 12)) < 0) return bad(st);
+    if (cudaMemsetAsync(e->tree_cnt.p, 0, sizeof(int) * 9, stream) != cudaSuccess)
+        return bad(fail(CTR_ERR_CUDA, "memset"));
     if ((st = e->err.alloc(sizeof(int))) < 0) return bad(st);
     if (cudaMemsetAsync(e->err.p, 0, sizeof(int), stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "memset"));
     if (cudaMemsetAsync(e->n_items.p, 0, sizeof(int) * 4, stream) != cudaSuccess)
@@ -466,6 +524,53 @@ int engine_create(int device, int cap, Engine** out) {
     if ((st = exp_table(device, &e->exp_tab)) < 0) return bad(st);
     if (cudaStreamSynchronize(stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "sync"));
     *out = e;
+    return CTR_OK;
+}
+
+// Treecode work lists per pair arithmetic (moment chunks, far clusters, far items of every occupied
+// treecode slot), sorted by decreasing cost like the pair items.
+static int rebuild_tree_items(Engine* e) {
+    bool any = false;
+    int counts[9] = {0};
+    for (int p = 0; p < 3; ++p) {
+        struct It {
+            int2 v;
+            double cost;
+        };
+        std::vector<It> lists[3];
+        for (int q = 0; q < e->cap; ++q) {
+            ctr_ibim* h = e->owner[q];
+            if (!h || !h->tree) continue;
+            any = true;
+            const SlotDev& s = e->host[q];
+            if (policy_index(s.inner_prec) != p && policy_index(s.res_prec) != p) continue;
+            const TreeData::Pol& P = h->tree->pol[p];
+            for (size_t k = 0; k < P.chunks.size(); ++k) lists[0].push_back(It{make_int2(q, (int)k), P.chunk_cost[k]});
+            for (int k = 0; k < P.nq; ++k) lists[1].push_back(It{make_int2(q, k), 1.0});
+            for (size_t k = 0; k < P.far.size(); ++k) lists[2].push_back(It{make_int2(q, (int)k), P.far_cost[k]});
+        }
+        for (int k = 0; k < 3; ++k) {
+            std::stable_sort(lists[k].begin(), lists[k].end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+            std::vector<int2> v(lists[k].size());
+            for (size_t i = 0; i < v.size(); ++i) v[i] = lists[k][i].v;
+            if ((int64_t)v.size() > e->tree_cap[p][k] || !e->tree_ent[p][k].p) {
+                const int64_t capn = std::max<int64_t>(256, (int64_t)v.size() * 2);
+                CTR_TRY(e->tree_ent[p][k].alloc(sizeof(int2) * capn));
+                e->tree_cap[p][k] = capn;
+                e->graph_dirty = true;   // the entry buffer moved
+            }
+            if (!v.empty())
+                CTR_CUDA_TRY(cudaMemcpyAsync(e->tree_ent[p][k].p, v.data(), sizeof(int2) * v.size(),
+                                             cudaMemcpyHostToDevice, e->stream));
+            counts[3 * p + k] = (int)v.size();
+        }
+    }
+    CTR_CUDA_TRY(cudaMemcpyAsync(e->tree_cnt.p, counts, sizeof(counts), cudaMemcpyHostToDevice, e->stream));
+    CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (any != e->any_tree) {
+        e->any_tree = any;
+        e->graph_dirty = true;   // the step gains or loses the treecode launches
+    }
     return CTR_OK;
 }
 
@@ -524,7 +629,7 @@ static int rebuild_items(Engine* e) {
         CTR_CUDA_TRY(cudaMemcpyAsync(e->n_items.as<int>() + p, &cnt, sizeof(int), cudaMemcpyHostToDevice, e->stream));
         CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
     }
-    return CTR_OK;
+    return rebuild_tree_items(e);
 }
 
 // The kernels of one engine step, in stream order (captured into the graph).
@@ -539,9 +644,11 @@ static int enqueue_step(Engine* e) {
     k_prep_inner<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
     CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, st));
+    if (e->any_tree) CTR_CUDA_TRY(cudaMemsetAsync(e->tree_counters.p, 0, sizeof(int) * 12, st));
     CTR_TRY(launch_fp32(e, 0));
     CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, CTR_DF64)));
     CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, CTR_FP64)));
+    CTR_TRY(launch_trees(e, 0));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 0);
     CTR_LAUNCHED();
     for (int pass = 0; pass < 2; ++pass) {
@@ -570,6 +677,7 @@ static int enqueue_step(Engine* e) {
     CTR_TRY(launch_fp32(e, 1));
     CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 1, CTR_DF64)));
     CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 1, CTR_FP64)));
+    CTR_TRY(launch_trees(e, 1));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 1);
     CTR_LAUNCHED();
     k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, 3);
@@ -631,7 +739,10 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     d.cptr = s->corr_ptr.as<int32_t>();
     d.cnode = s->corr_node.as<int32_t>();
     d.cw = s->corr_w.as<double>();
-    d.excl = s->excl.as<int32_t>();
+    d.excl = s->tree ? s->tree->d_excl.as<int32_t>() : s->excl.as<int32_t>();
+    d.eptr = s->tree ? s->tree->d_eptr.as<int32_t>() : s->corr_ptr.as<int32_t>();
+    d.tinv = s->tree ? s->tree->d_tinv.as<int32_t>() : nullptr;
+    if (s->tree) d.tv = s->tree->view;
     d.src32 = s->src32.as<float4>();
     d.src64 = s->src64.as<double4>();
     d.srcdf = s->srcdf.as<float4>();

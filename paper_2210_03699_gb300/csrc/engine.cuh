@@ -34,7 +34,9 @@ struct SlotDev {
     const int32_t* cptr;
     const int32_t* cnode;
     const double* cw;
-    const int32_t* excl;
+    const int32_t* excl;     // excluded sources of each target, in the order of the packed sources
+    const int32_t* eptr;     // ... and their row pointers (cptr, or the treecode's tree-order lists)
+    const int32_t* tinv;     // treecode: node -> tree position of the packed sources (else NULL)
     float4* src32;
     double4* src64;
     float4* srcdf;
@@ -47,6 +49,7 @@ struct SlotDev {
     const PairRec* recs[3];
     const int32_t* rptr[3];
     int BS[3];
+    TreeView tv;             // far-field data of a treecode handle (tv.on = 0 otherwise)
     // solver workspace (owned by the handle)
     double *x, *r, *z, *V, *H, *cs, *sn, *sv, *y, *cgs, *cgs2, *dpart, *scal;
     double gnorm, beta, tol_out, inner_tol, tol_cycle;
@@ -74,6 +77,10 @@ struct Engine {
     std::vector<SlotDev> host;
     std::vector<ctr_ibim*> owner;
     DevBuf slots, stats, items[3], n_items, counters, err;
+    // treecode work entries (slot, index) per pair arithmetic: moment chunks, far clusters, far items
+    bool any_tree = false;
+    int64_t tree_cap[3][3] = {};
+    DevBuf tree_ent[3][3], tree_cnt, tree_counters;
     cudaGraphExec_t graph_exec = nullptr;
     ~Engine();
 };

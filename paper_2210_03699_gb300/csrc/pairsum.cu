@@ -55,12 +55,15 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(const typename Policy::S
 }
 
 // a = h^3 W rho1/(4 pi), b = h^3 W rho2/(4 pi) into the weight slots of the packed sources
+// (at the node's tree position when the treecode has reordered the sources)
 __global__ void pack_kernel(const double* __restrict__ x, const double* __restrict__ W, int64_t M, double scale,
-                            float4* __restrict__ s32, double4* __restrict__ s64, float4* __restrict__ sdf) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
-    const double a = scale * W[j] * x[j];
-    const double b = scale * W[j] * x[M + j];
+                            float4* __restrict__ s32, double4* __restrict__ s64, float4* __restrict__ sdf,
+                            const int32_t* __restrict__ tinv) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    const double a = scale * W[t] * x[t];
+    const double b = scale * W[t] * x[M + t];
+    const int64_t j = tinv ? (int64_t)tinv[t] : t;
     if (s32) {   // duplicated pairs: a and -b
         s32[4 * j + 1].z = s32[4 * j + 1].w = (float)a;
         s32[4 * j + 3].z = s32[4 * j + 3].w = -(float)b;
@@ -83,11 +86,11 @@ __global__ void finish_kernel(int64_t M, const PairRec* __restrict__ recs, const
                               const double* __restrict__ partial, const double* __restrict__ x,
                               double* __restrict__ y, const double* __restrict__ W, const int32_t* __restrict__ ptr,
                               const int32_t* __restrict__ node, const double* __restrict__ w, int64_t E,
-                              double lam1, double lam2, double h2, double h3) {
+                              double lam1, double lam2, double h2, double h3, const int32_t* __restrict__ tinv) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     double s1 = 0.0, s2 = 0.0;
-    gather_partials(recs, rptr, BS, partial, i, s1, s2);
+    gather_partials(recs, rptr, BS, partial, tinv ? (int64_t)tinv[i] : i, s1, s2);
     double c1 = 0.0, c2 = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
         const int m = node[e];
@@ -216,27 +219,43 @@ int plan_pairs(ctr_ibim* s) {
     CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
     int slots[3] = {0, 0, 0};
     CTR_TRY(schedule_slots(sms, slots));
-    CTR_TRY(build_schedules(s, slots));
     CTR_TRY(s->srcdf.alloc(sizeof(float4) * 4 * (size_t)s->M));
     df_static_kernel<<<grid_for(s->M, 256), 256, 0, s->stream>>>(s->na, s->M, s->srcdf.as<float4>());
     CTR_LAUNCHED();
-    return CTR_OK;
+    if (s->opt.farfield == CTR_FARFIELD_TREECODE) return build_tree_schedules(s, slots);
+    return build_schedules(s, slots);
 }
 
 int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision) {
+    return apply_operator_timed(s, d_x, d_y, precision, nullptr);
+}
+
+// The operator with, when ev is not NULL, events recorded on the handle's stream before packing, the
+// pair items, the far field, the finish and after it (ev[0..4]).
+int apply_operator_timed(ctr_ibim* s, const double* d_x, double* d_y, int precision, cudaEvent_t* ev) {
     const int64_t M = s->M;
     cudaStream_t st = s->stream;
+    auto mark = [&](int k) -> int {
+        if (ev) CTR_CUDA_TRY(cudaEventRecord(ev[k], st));
+        return CTR_OK;
+    };
+    CTR_TRY(mark(0));
     const double scale = s->h * s->h * s->h / (4.0 * kPi);
     float4* s32 = (precision == CTR_FP32_REFINE) ? s->src32.as<float4>() : nullptr;
     double4* s64 = (precision == CTR_FP64) ? s->src64.as<double4>() : nullptr;
     float4* sdf = (precision == CTR_DF64) ? s->srcdf.as<float4>() : nullptr;
-    pack_kernel<<<grid_for(M, 256), 256, 0, st>>>(d_x, s->na.W, M, scale, s32, s64, sdf);
+    const int32_t* tinv = s->tree ? s->tree->d_tinv.as<int32_t>() : nullptr;
+    pack_kernel<<<grid_for(M, 256), 256, 0, st>>>(d_x, s->na.W, M, scale, s32, s64, sdf, tinv);
     CTR_LAUNCHED();
     PairConsts kc;
     CTR_TRY(pair_consts(s, precision == CTR_DF64, &kc));
     const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
     const void* src = s32 ? (const void*)s32 : (sdf ? (const void*)sdf : (const void*)s64);
+    CTR_TRY(mark(1));
     CTR_TRY(launch_schedule(s, pol, src, kc));
+    CTR_TRY(mark(2));
+    CTR_TRY(launch_tree(s, pol));
+    CTR_TRY(mark(3));
     const PairSchedule& p = s->sched[pol];
     const double h2 = s->h * s->h;
     const double h3 = s->h * s->h * s->h;
@@ -245,8 +264,9 @@ int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision) {
                                                    s->corr_ptr.as<int32_t>(), s->corr_node.as<int32_t>(),
                                                    s->corr_w.as<double>(), s->E,
                                                    0.5 * (1.0 + s->eps_out / s->eps_in),
-                                                   0.5 * (1.0 + s->eps_in / s->eps_out), h2, h3);
+                                                   0.5 * (1.0 + s->eps_in / s->eps_out), h2, h3, tinv);
     CTR_LAUNCHED();
+    CTR_TRY(mark(4));
     return CTR_OK;
 }
 

@@ -104,9 +104,10 @@ int sched_launch(ctr_ibim* s, int pol, const void* src, const PairConsts& kc, in
     int* counter = s->counter.as<int>() + pol;
     CTR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s->stream));
     sched_kernel<Policy, R, V, U><<<grid, kThreads, pair_smem_bytes<Policy>(), s->stream>>>(
-        reinterpret_cast<const typename Policy::Src*>(src), (int)s->M, s->corr_ptr.as<int32_t>(),
-        s->excl.as<int32_t>(), p.d_items.as<PairItem>(), (int)p.items.size(), counter, s->partial.as<double>(), kc,
-        s->err.as<int>());
+        reinterpret_cast<const typename Policy::Src*>(src), (int)s->M,
+        s->tree ? s->tree->d_eptr.as<int32_t>() : s->corr_ptr.as<int32_t>(),
+        s->tree ? s->tree->d_excl.as<int32_t>() : s->excl.as<int32_t>(), p.d_items.as<PairItem>(),
+        (int)p.items.size(), counter, s->partial.as<double>(), kc, s->err.as<int>());
     CTR_LAUNCHED();
     return CTR_OK;
 }

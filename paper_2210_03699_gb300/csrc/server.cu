@@ -65,6 +65,7 @@ size_t handle_bytes(const ctr_ibim* s) {
     for (const DevBuf* d : bufs) b += d->bytes;
     for (const PairSchedule& p : s->sched) b += p.d_items.bytes + p.d_rptr.bytes + p.d_recs.bytes;
     b += s->counter.bytes;
+    b += (size_t)tree_bytes(s);
     return b;
 }
 
@@ -108,7 +109,10 @@ int64_t estimate_bytes(const Request& r) {
     // pair partial regions: the source sums of the symmetric items, M^2 / 256 doubles for the
     // 256-node blocks of the float-float and FP64 schedules, plus the target sums (a few MB)
     const int64_t per_node = 16 * 8 + 160 + 50 * 36 + 12 * 8 + (int64_t)(m + 1) * 16;
-    const int64_t regions = M * M / 32 + ((int64_t)16 << 20);
+    // with the treecode: the near and far items of the three arithmetics (a few dozen regions per
+    // target block), the tree-order exclusion lists and the cluster charges
+    const int64_t regions = (r.opt.farfield == CTR_FARFIELD_TREECODE) ? M * 4096 + ((int64_t)64 << 20)
+                                                                      : M * M / 32 + ((int64_t)16 << 20);
     const int64_t grid_bytes = (int64_t)r.sdist.size() * (8 + 4);   // staging copy + node map during setup
     return M * per_node + regions + grid_bytes;
 }

@@ -1,0 +1,330 @@
+// Far-field acceleration of the dense sum (the fast summation of K v inside
+// GMRES, Sec. 2.5): the device kernels of the particle-cluster treecode.
+//
+// A far cluster C of a target block is replaced by the tensor Chebyshev
+// points s_k of its box (k = (k3 n1 + k2) n1 + k1) carrying the charges of
+// the interpolated source variable, G(x, y) ~ sum_k G(x, s_k) L_k(y):
+//   Dk = sum_j a_j n_j . grad L_k(P_j),   Sk = sum_j b_j L_k(P_j)
+//   (a = h^3 W rho1 / 4 pi, b = h^3 W rho2 / 4 pi, the packed source weights),
+//   Q0 = Dk - Sk,  Qk = -(eps_E/eps_I) Dk + Sk,  Qk' = -Dk + (eps_I/eps_E) Sk,
+// and a target (x, n_x) of the block receives, from K11..K22 of Eq. (1.4),
+//   out1 += sum_k Q0/r + Qk e^{-kappa r}/r,
+//   out2 += sum_k -(d . n_x)/r^3 (Q0 + (1 + kappa r) e^{-kappa r} Qk'),
+// with d = x - s_k, r = |d|.  Three kernels per pair arithmetic:
+//   k_tree_mom     Dk, Sk of one chunk of a cluster's sources (per-source
+//                  barycentric basis and derivative in shared memory; each
+//                  thread owns one (k2, k3) row of proxies);
+//   k_tree_momred  the chunks of a cluster added in a fixed order, Q formed;
+//   k_tree_far     far items (target block x a run of its far clusters; NT
+//                  threads with R targets each): the cluster's proxies and
+//                  charges in shared memory, FP32 sums
+//                  per cluster folded into FP64 per target, written to the
+//                  item's partial region like a one-sided pair item.
+// The blocks of each kernel take work entries (handle, index) from a list
+// through an atomic counter; `Acc` maps an entry's handle to its TreeView (or
+// to nothing when that handle is not in this pass).
+#pragma once
+
+#include "common.cuh"
+#include "pairkern.cuh"
+
+namespace ctr {
+
+using pk::kThreads;
+
+constexpr int kMomTile = 32;      // sources per shared tile of the moment kernel
+// far kernel shape per pair arithmetic: R targets per thread x NT threads = the target block
+constexpr int kTreeR[3] = {4, 4, 1};
+constexpr int kTreeNT[3] = {256, 64, 256};
+constexpr int kChunkSrc = 2048;   // sources per moment chunk
+
+template <typename Real>
+__device__ __forceinline__ void tree_source(const TreeView& t, int pol, int64_t p, Real P[3], Real n[3], Real& a,
+                                            Real& b) {
+    if (pol == 2) {
+        const double4 u = t.src64[2 * p], v = t.src64[2 * p + 1];
+        P[0] = (Real)u.x, P[1] = (Real)u.y, P[2] = (Real)u.z, a = (Real)u.w;
+        n[0] = (Real)v.x, n[1] = (Real)v.y, n[2] = (Real)v.z, b = (Real)v.w;
+    } else if (pol == 1) {   // float-float sources: the leading floats
+        const float4 u = t.srcdf[4 * p], v = t.srcdf[4 * p + 2];
+        P[0] = (Real)u.x, P[1] = (Real)u.y, P[2] = (Real)u.z, a = (Real)u.w;
+        n[0] = (Real)v.x, n[1] = (Real)v.y, n[2] = (Real)v.z, b = (Real)v.w;
+    } else {                 // duplicated f32x2 layout {x,x,y,y}{z,z,a,a}{nx,nx,ny,ny}{nz,nz,-b,-b}
+        const float4 u0 = t.src32[4 * p], u1 = t.src32[4 * p + 1], u2 = t.src32[4 * p + 2],
+                     u3 = t.src32[4 * p + 3];
+        P[0] = (Real)u0.x, P[1] = (Real)u0.z, P[2] = (Real)u1.x, a = (Real)u1.z;
+        n[0] = (Real)u2.x, n[1] = (Real)u2.z, n[2] = (Real)u3.x, b = -(Real)u3.z;
+    }
+}
+
+template <typename Acc>
+__device__ __forceinline__ int tree_next(int* counter, int* cur) {
+    if (threadIdx.x == 0) *cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = *cur;
+    __syncthreads();
+    return it;
+}
+
+// ---------------------------------------------------------------- moments of one chunk
+template <typename Real, class Acc>
+__global__ void __launch_bounds__(kThreads) k_tree_mom(Acc acc, const int2* __restrict__ ent,
+                                                    const int* __restrict__ n_ent, int* __restrict__ counter,
+                                                    int pol) {
+    __shared__ Real xr[kTreeMaxN1], bw[kTreeMaxN1], dr[kTreeMaxN1 * kTreeMaxN1];
+    __shared__ Real L[3][kMomTile][kTreeMaxN1], G[3][kMomTile][kTreeMaxN1], BL[kMomTile][kTreeMaxN1];
+    __shared__ int cur;
+    const int tid = threadIdx.x;
+    const int total = *n_ent;
+    for (;;) {
+        const int it = tree_next<Acc>(counter, &cur);
+        if (it >= total) break;
+        const int2 w = ent[it];
+        const TreeView* tp = acc.view(w.x);
+        if (!tp) continue;   // block-uniform
+        const TreeView& t = *tp;
+        const int n1 = t.n1, np = t.np;
+        const MomChunk ch = t.chunks[pol][w.y];
+        for (int i = tid; i < n1; i += kThreads) {
+            xr[i] = (Real)t.xref[i];
+            bw[i] = (Real)t.bw[i];
+        }
+        for (int i = tid; i < n1 * n1; i += kThreads) dr[i] = (Real)t.dref[i];
+        const double* bx = t.box[pol] + 6 * (int64_t)ch.q;
+        Real accD[kTreeMaxN1], accS[kTreeMaxN1];
+#pragma unroll
+        for (int k = 0; k < kTreeMaxN1; ++k) accD[k] = accS[k] = (Real)0;
+        const int row = tid;                  // proxy row (k2, k3) = (row % n1, row / n1)
+        const bool owner = row < n1 * n1;
+        const int k2 = owner ? row % n1 : 0, k3 = owner ? row / n1 : 0;
+        __syncthreads();
+        for (int j0 = ch.j0; j0 < ch.j1; j0 += kMomTile) {
+            const int nt = min(kMomTile, ch.j1 - j0);
+            if (tid < 3 * kMomTile) {
+                const int s = tid % kMomTile, ax = tid / kMomTile;
+                Real l[kTreeMaxN1];
+                Real coef = (Real)0, bcoef = (Real)0;
+#pragma unroll
+                for (int m = 0; m < kTreeMaxN1; ++m) l[m] = (Real)0;
+                if (s < nt) {
+                    Real P[3], n[3], a, b;
+                    tree_source<Real>(t, pol, j0 + s, P, n, a, b);
+                    const Real c = (Real)bx[ax], wd = (Real)bx[3 + ax];
+                    const Real u = (P[ax] - c) / wd;
+                    int hit = -1;
+#pragma unroll
+                    for (int m = 0; m < kTreeMaxN1; ++m)
+                        if (m < n1 && u == xr[m]) hit = m;
+                    if (hit >= 0) {
+#pragma unroll
+                        for (int m = 0; m < kTreeMaxN1; ++m) l[m] = (m == hit) ? (Real)1 : (Real)0;
+                    } else {
+                        Real den = (Real)0;
+#pragma unroll
+                        for (int m = 0; m < kTreeMaxN1; ++m)
+                            if (m < n1) {
+                                l[m] = bw[m] / (u - xr[m]);
+                                den += l[m];
+                            }
+#pragma unroll
+                        for (int m = 0; m < kTreeMaxN1; ++m)
+                            if (m < n1) l[m] = l[m] / den;
+                    }
+                    coef = a * n[ax] / wd;
+                    bcoef = b;
+                }
+                // basis, derivative (l' = l D / w, weighted by a n_ax) and b-weighted basis
+#pragma unroll
+                for (int q = 0; q < kTreeMaxN1; ++q) {
+                    if (q >= n1) break;
+                    Real gq = (Real)0;
+#pragma unroll
+                    for (int m = 0; m < kTreeMaxN1; ++m)
+                        if (m < n1) gq += l[m] * dr[m * n1 + q];
+                    L[ax][s][q] = l[q];
+                    G[ax][s][q] = coef * gq;
+                    if (ax == 0) BL[s][q] = bcoef * l[q];
+                }
+            }
+            __syncthreads();
+            if (owner) {
+                for (int s = 0; s < nt; ++s) {
+                    const Real l1 = L[1][s][k2], g1 = G[1][s][k2], l2 = L[2][s][k3], g2 = G[2][s][k3];
+                    const Real y12 = l1 * l2;
+                    const Real tt = g1 * l2 + l1 * g2;
+#pragma unroll
+                    for (int k1 = 0; k1 < kTreeMaxN1; ++k1) {
+                        if (k1 < n1) {
+                            accS[k1] += BL[s][k1] * y12;
+                            accD[k1] += G[0][s][k1] * y12 + L[0][s][k1] * tt;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (owner) {
+            Real* out = static_cast<Real*>(t.mpart[pol]) + (size_t)w.y * 2 * np;
+#pragma unroll
+            for (int k1 = 0; k1 < kTreeMaxN1; ++k1) {
+                if (k1 < n1) {
+                    out[row * n1 + k1] = accD[k1];
+                    out[np + row * n1 + k1] = accS[k1];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- chunk sums -> charges
+template <typename Real, class Acc>
+__global__ void __launch_bounds__(kThreads) k_tree_momred(Acc acc, const int2* __restrict__ ent,
+                                                       const int* __restrict__ n_ent, int pol) {
+    const int total = *n_ent;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int2 w = ent[it];
+        const TreeView* tp = acc.view(w.x);
+        if (!tp) continue;
+        const TreeView& t = *tp;
+        const int np = t.np, q = w.y;
+        const int c0 = t.cptr[pol][q], c1 = t.cptr[pol][q + 1];
+        const Real* mp = static_cast<const Real*>(t.mpart[pol]);
+        Real* Q = static_cast<Real*>(t.mom[pol]) + (size_t)q * 3 * np;
+        for (int k = threadIdx.x; k < np; k += blockDim.x) {
+            double D = 0.0, S = 0.0;
+            for (int c = c0; c < c1; ++c) {
+                D += (double)mp[(size_t)c * 2 * np + k];
+                S += (double)mp[(size_t)c * 2 * np + np + k];
+            }
+            Q[k] = (Real)(D - S);
+            Q[np + k] = (Real)(-t.c1 * D + S);
+            Q[2 * np + k] = (Real)(-D + t.c2 * S);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- far items
+template <typename Real>
+__device__ __forceinline__ void far_terms(Real dx, Real ryz, Real dyzn, Real nx, Real q0, Real qk, Real qk2,
+                                          Real kappa, Real kl2, Real& a1, Real& a2) {
+    const Real r2 = fma(dx, dx, ryz);
+    const Real dn = fma(dx, nx, dyzn);
+    Real ri, E;
+    if constexpr (sizeof(Real) == 4) {
+        ri = pk::rsqrt_sfu(r2);
+        E = pk::ex2_sfu(kl2 * (r2 * ri));
+    } else {
+        ri = rsqrt(r2);
+        E = exp(-kappa * (r2 * ri));
+    }
+    const Real r = r2 * ri;
+    a1 = fma(ri, fma(E, qk, q0), a1);
+    const Real f = E * fma(kappa, r, (Real)1);
+    a2 = fma(-dn * (ri * ri * ri), fma(f, qk2, q0), a2);
+}
+
+template <typename Real>
+constexpr size_t tree_far_smem() {
+    return sizeof(Real) * (3 * kTreeMaxN1 + 3 * kTreeMaxNp);
+}
+
+// NT threads x R targets per thread cover one target block (NT * R = the arithmetic's block size).
+template <typename Real, int R, int NT, class Acc>
+__global__ void __launch_bounds__(NT) k_tree_far(Acc acc, const int2* __restrict__ ent,
+                                              const int* __restrict__ n_ent, int* __restrict__ counter, int pol) {
+    extern __shared__ __align__(16) unsigned char tree_smem[];
+    Real* sx = reinterpret_cast<Real*>(tree_smem);         // [3][kTreeMaxN1]
+    Real* sq = sx + 3 * kTreeMaxN1;                        // [3][np]
+    __shared__ int cur;
+    const int tid = threadIdx.x;
+    const int total = *n_ent;
+    for (;;) {
+        const int it = tree_next<Acc>(counter, &cur);
+        if (it >= total) break;
+        const int2 w = ent[it];
+        const TreeView* tp = acc.view(w.x);
+        if (!tp) continue;
+        const TreeView& t = *tp;
+        const int n1 = t.n1, np = t.np, M = t.M, BS = t.BS[pol];
+        const FarItem f = t.far[pol][w.y];
+        const Real kappa = (Real)t.kappa;
+        const Real kl2 = (Real)(-t.kappa * 1.4426950408889634);
+        Real px[R], py[R], pz[R], nx[R], ny[R], nz[R];
+        double o1[R], o2[R];
+        int64_t pp[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            pp[r] = (int64_t)f.I * BS + r * NT + tid;
+            Real P[3], n[3], a, b;
+            tree_source<Real>(t, pol, min(pp[r], (int64_t)M - 1), P, n, a, b);
+            px[r] = P[0], py[r] = P[1], pz[r] = P[2];
+            nx[r] = n[0], ny[r] = n[1], nz[r] = n[2];
+            o1[r] = 0.0, o2[r] = 0.0;
+        }
+        for (int l = f.l0; l < f.l1; ++l) {
+            const int q = t.flist[pol][l];
+            __syncthreads();   // the previous cluster's proxies are no longer read
+            const double* bx = t.box[pol] + 6 * (int64_t)q;
+            for (int i = tid; i < 3 * n1; i += NT) {
+                const int ax = i / n1, m = i % n1;
+                sx[ax * kTreeMaxN1 + m] = (Real)(bx[ax] + bx[3 + ax] * t.xref[m]);
+            }
+            const Real* Q = static_cast<const Real*>(t.mom[pol]) + (size_t)q * 3 * np;
+            for (int i = tid; i < 3 * np; i += NT) sq[i] = Q[i];
+            __syncthreads();
+            Real a1[R], a2[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) a1[r] = a2[r] = (Real)0;
+            for (int k3 = 0; k3 < n1; ++k3) {
+                const Real sz = sx[2 * kTreeMaxN1 + k3];
+                Real dz2[R], dzn[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const Real dz = pz[r] - sz;
+                    dz2[r] = dz * dz;
+                    dzn[r] = dz * nz[r];
+                }
+                for (int k2 = 0; k2 < n1; ++k2) {
+                    const Real sy = sx[kTreeMaxN1 + k2];
+                    Real ryz[R], dyzn[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const Real dy = py[r] - sy;
+                        ryz[r] = fma(dy, dy, dz2[r]);
+                        dyzn[r] = fma(dy, ny[r], dzn[r]);
+                    }
+                    const int kb = (k3 * n1 + k2) * n1;
+                    for (int k1 = 0; k1 < n1; ++k1) {
+                        const Real sxk = sx[k1];
+                        const Real q0 = sq[kb + k1], qk = sq[np + kb + k1], qk2 = sq[2 * np + kb + k1];
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            far_terms<Real>(px[r] - sxk, ryz[r], dyzn[r], nx[r], q0, qk, qk2, kappa, kl2, a1[r],
+                                            a2[r]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                o1[r] += (double)a1[r];
+                o2[r] += (double)a2[r];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (pp[r] < M) {
+                const int64_t off = pp[r] - (int64_t)f.I * BS;
+                t.part[f.ibase + off] = o1[r];
+                t.part[f.ibase + BS + off] = o2[r];
+            }
+        }
+    }
+}
+
+// Work entries of one handle alone: every entry belongs to it.
+struct OneTreeAcc {
+    const TreeView* t;
+    __device__ const TreeView* view(int) const { return t; }
+};
+
+}  // namespace ctr
