@@ -45,9 +45,10 @@ OPS_FP64 = {"one": 69, "sym": 69}
 # ncu capture (profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt); None at any other size, or once
 # the kernels change.
 TRAFFIC_H005 = {"fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
-# Treecode far field (FP32): FMA-pipe lane operations per proxy evaluation counted from the kernel source
-# (tree.cuh, far_terms: 2 sub/mul + 5 fma + 6 mul), plus 2 SFU operations (rsqrt, ex2).
-OPS_FAR = 13
+# Treecode far field (FP32 charges): FMA-pipe lane operations per proxy evaluation counted from the kernel
+# source (tree.cuh, k_tree_far2: 1 sub, 6 fma, 7 mul; an f32x2 instruction does two), plus 2 SFU operations
+# (rsqrt, ex2).
+OPS_FAR = 14
 SFU_FAR = 2
 
 
@@ -475,8 +476,9 @@ def run_tree(args, ctr, world):
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {ops} lane ops per "
                                    f"one-sided pair; measured FFMA probe {rate_ffma:.4g}/s",
                      "t_ms": t_near * 1e3, "pairs": near, "step_share": n_app[pr] * t_near / step_s})
-        kern.append({"bound": "alu", "kernel": f"k_tree_mom + k_tree_momred + k_tree_far<float, 4, "
-                                               f"{256 if tag == 'fp32' else 64}> (treecode far field, {tag} blocks)",
+        kern.append({"bound": "alu", "kernel": f"k_tree_mom + k_tree_momred + k_tree_far2<"
+                                               f"{'2, 256' if tag == 'fp32' else '1, 128'}> (treecode far field, "
+                                               f"{tag} blocks)",
                      "achieved": far / t_far if t_far > 0 else None, "peak": far_peak,
                      "unit": "proxy evaluations/s",
                      "frac": far / t_far / far_peak if t_far > 0 else None, "traffic": None,

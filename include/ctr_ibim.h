@@ -91,7 +91,9 @@ enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
  *       interpolation of the kernels' source variable, d/dn_y on the basis);
  *       every other pair is summed directly with the correction pairs skipped
  *       exactly.  The error against the direct sum falls geometrically with the
- *       degree (about 6e-8 relative at degree 10, theta 0.8).  The far field is
+ *       degree (about 6e-8 relative at degree 10, theta 0.8; the CTR_FP32_REFINE
+ *       operator, which only drives the inner GMRES, uses its own degree and
+ *       theta, 6 and 0.9 by default: about 7e-6).  The far field is
  *       FP32 in the CTR_FP32_REFINE and CTR_DF64 arithmetics and FP64 in
  *       CTR_FP64; the direct part keeps the arithmetic's pair kernels.
  */
@@ -120,6 +122,9 @@ typedef struct {
     int tree_degree;       /* treecode interpolation degree per axis, 2..12; <= 0 selects 10 */
     double tree_theta;     /* treecode separation parameter, 0 < theta < 1; <= 0 selects 0.8 */
     int tree_leaf;         /* most nodes of a treecode leaf; <= 0 selects 128 */
+    int tree_degree_fp32;  /* degree of the CTR_FP32_REFINE operator (the inner GMRES, whose own
+                              rounding is ~2e-5); <= 0 selects 6 */
+    double tree_theta_fp32;/* theta of the CTR_FP32_REFINE operator; <= 0 selects 0.9 */
 } ctr_options;
 
 typedef struct {

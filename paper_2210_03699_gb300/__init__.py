@@ -50,7 +50,8 @@ class _Options(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int),
                 ("method", ctypes.c_int), ("farfield", ctypes.c_int), ("tree_degree", ctypes.c_int),
-                ("tree_theta", ctypes.c_double), ("tree_leaf", ctypes.c_int)]
+                ("tree_theta", ctypes.c_double), ("tree_leaf", ctypes.c_int), ("tree_degree_fp32", ctypes.c_int),
+                ("tree_theta_fp32", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -90,11 +91,14 @@ class Options:
     tree_degree: int = 10
     tree_theta: float = 0.8
     tree_leaf: int = 128
+    tree_degree_fp32: int = 6
+    tree_theta_fp32: float = 0.9
 
     def _c(self) -> _Options:
         return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
                         self.max_refine, self.inner_tol, self.tile_targets, self.residual, self.method,
-                        self.farfield, self.tree_degree, self.tree_theta, self.tree_leaf)
+                        self.farfield, self.tree_degree, self.tree_theta, self.tree_leaf, self.tree_degree_fp32,
+                        self.tree_theta_fp32)
 
 
 @dataclasses.dataclass

@@ -79,6 +79,8 @@ void ctr_default_options(ctr_options* o) {
     o->tree_degree = 10;
     o->tree_theta = 0.8;
     o->tree_leaf = 128;
+    o->tree_degree_fp32 = 6;
+    o->tree_theta_fp32 = 0.9;
 }
 
 const char* ctr_status_string(int st) {
@@ -152,8 +154,12 @@ int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_devic
             if (o.tree_degree <= 0) o.tree_degree = 10;
             if (!(o.tree_theta > 0.0)) o.tree_theta = 0.8;
             if (o.tree_leaf <= 0) o.tree_leaf = 128;
-            if (o.tree_degree < 2 || o.tree_degree > 12) return fail(CTR_ERR_INVALID, "tree_degree must be 2..12");
-            if (!(o.tree_theta < 1.0)) return fail(CTR_ERR_INVALID, "tree_theta must be below 1");
+            if (o.tree_degree_fp32 <= 0) o.tree_degree_fp32 = 6;
+            if (!(o.tree_theta_fp32 > 0.0)) o.tree_theta_fp32 = 0.9;
+            if (o.tree_degree < 2 || o.tree_degree > 12 || o.tree_degree_fp32 < 2 || o.tree_degree_fp32 > 12)
+                return fail(CTR_ERR_INVALID, "tree degrees must be 2..12");
+            if (!(o.tree_theta < 1.0) || !(o.tree_theta_fp32 < 1.0))
+                return fail(CTR_ERR_INVALID, "tree theta must be below 1");
             if (o.tree_leaf > (1 << 20)) return fail(CTR_ERR_INVALID, "tree_leaf must be <= 2^20");
         }
         if (o.restart > 1000) return fail(CTR_ERR_INVALID, "restart must be <= 1000");

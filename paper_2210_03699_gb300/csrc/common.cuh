@@ -155,14 +155,16 @@ struct MomChunk {
 };
 
 // Device view of a handle's far-field data, per pair arithmetic p (0 FP32,
-// 1 float-float, 2 FP64; charges and far sums are FP32 for p < 2, FP64 for p = 2).
+// 1 float-float, 2 FP64; charges and far sums are FP32 for p < 2, FP64 for p = 2;
+// each arithmetic has its own interpolation degree n = n1 - 1).
 struct TreeView {
     int on = 0;
-    int M = 0, n1 = 0, np = 0;
+    int M = 0;
+    int n1[3] = {}, np[3] = {};           // points per axis, proxies per cluster
     const int32_t* tinv = nullptr;        // node -> tree position
-    const double* xref = nullptr;         // n1 Chebyshev points cos(m pi / n)
-    const double* bw = nullptr;           // n1 barycentric weights
-    const double* dref = nullptr;         // n1 x n1 differentiation matrix, D[m * n1 + q] = l_q'(x_m)
+    const double* xref[3] = {};           // n1 Chebyshev points cos(m pi / n)
+    const double* bw[3] = {};             // n1 barycentric weights
+    const double* dref[3] = {};           // n1 x n1 differentiation matrix, D[m * n1 + q] = l_q'(x_m)
     const double* box[3] = {};            // per far cluster: centre[3], half-width[3]
     const MomChunk* chunks[3] = {};
     const int32_t* cptr[3] = {};          // chunks of far cluster q: [cptr[q], cptr[q+1])
@@ -180,13 +182,15 @@ struct TreeView {
 
 // Host side of a handle's treecode (owns the device buffers the view points to).
 struct TreeData {
-    int degree = 10, leaf = 128, g = 2, n1 = 11, np = 1331;
-    double theta = 0.8;
+    int leaf = 128, g = 2;
     int64_t n_clusters = 0;
     std::vector<int32_t> perm;            // node at each tree position
     DevBuf d_tinv, d_eptr, d_excl;        // node -> position; exclusion CSR in tree positions
-    DevBuf d_xref, d_bw, d_dref, d_counters, d_view;
+    DevBuf d_counters, d_view;
     struct Pol {
+        int degree = 10, n1 = 11, np = 1331;
+        double theta = 0.8;
+        DevBuf d_xref, d_bw, d_dref;
         int nq = 0;                                      // far clusters with charges
         int64_t near_pairs = 0, far_evals = 0, far_pairs = 0;
         std::vector<FarItem> far;                        // device order (decreasing cost)

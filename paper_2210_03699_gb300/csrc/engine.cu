@@ -405,23 +405,7 @@ struct EngineTreeAcc {
 
 template <typename Real, int R, int NT>
 int launch_tree_engine(Engine* e, int pol, int half, int prec) {
-    static std::mutex mu;
-    static int per_dev[64] = {0};
-    int dev = 0;
-    CTR_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
-    const int smem = (int)tree_far_smem<Real>();
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (per_dev[dev] == 0) {
-            CTR_CUDA_TRY(cudaFuncSetAttribute(k_tree_far<Real, R, NT, EngineTreeAcc>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            int b = 0;
-            CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tree_far<Real, R, NT, EngineTreeAcc>,
-                                                                       NT, smem));
-            per_dev[dev] = std::max(1, b);
-        }
-    }
+    static std::map<std::pair<int, int>, int> cache;
     const EngineTreeAcc acc{e->slots.as<SlotDev>(), half, prec};
     const int* cnt = e->tree_cnt.as<int>() + 3 * pol;
     int* ctr = e->tree_counters.as<int>() + 4 * pol + 2 * half;
@@ -431,8 +415,19 @@ int launch_tree_engine(Engine* e, int pol, int half, int prec) {
     k_tree_momred<Real, EngineTreeAcc><<<4 * e->sms, kThreads, 0, e->stream>>>(acc, e->tree_ent[pol][1].as<int2>(),
                                                                              cnt + 1, pol);
     CTR_LAUNCHED();
-    k_tree_far<Real, R, NT, EngineTreeAcc><<<per_dev[dev] * e->sms, NT, smem, e->stream>>>(
-        acc, e->tree_ent[pol][2].as<int2>(), cnt + 2, ctr + 1, pol);
+    if constexpr (sizeof(Real) == 4) {
+        auto kern = k_tree_far2<R / 2, NT, EngineTreeAcc>;
+        const int smem = (int)tree_far2_smem(std::max(1, e->tree_np[pol]));   // the largest proxy count admitted
+        const int per_sm = far_per_sm(kern, NT, smem, (int)tree_far2_smem(), cache);
+        if (per_sm < 0) return per_sm;
+        kern<<<per_sm * e->sms, NT, smem, e->stream>>>(acc, e->tree_ent[pol][2].as<int2>(), cnt + 2, ctr + 1, pol);
+    } else {
+        auto kern = k_tree_far<Real, R, NT, EngineTreeAcc>;
+        const int per_sm = far_per_sm(kern, NT, (int)tree_far_smem<Real>(), (int)tree_far_smem<Real>(), cache);
+        if (per_sm < 0) return per_sm;
+        kern<<<per_sm * e->sms, NT, tree_far_smem<Real>(), e->stream>>>(acc, e->tree_ent[pol][2].as<int2>(),
+                                                                       cnt + 2, ctr + 1, pol);
+    }
     CTR_LAUNCHED();
     return CTR_OK;
 }
@@ -532,6 +527,7 @@ int engine_create(int device, int cap, Engine** out) {
 static int rebuild_tree_items(Engine* e) {
     bool any = false;
     int counts[9] = {0};
+    int np_max[3] = {0, 0, 0};
     for (int p = 0; p < 3; ++p) {
         struct It {
             int2 v;
@@ -545,6 +541,7 @@ static int rebuild_tree_items(Engine* e) {
             const SlotDev& s = e->host[q];
             if (policy_index(s.inner_prec) != p && policy_index(s.res_prec) != p) continue;
             const TreeData::Pol& P = h->tree->pol[p];
+            np_max[p] = std::max(np_max[p], P.np);
             for (size_t k = 0; k < P.chunks.size(); ++k) lists[0].push_back(It{make_int2(q, (int)k), P.chunk_cost[k]});
             for (int k = 0; k < P.nq; ++k) lists[1].push_back(It{make_int2(q, k), 1.0});
             for (size_t k = 0; k < P.far.size(); ++k) lists[2].push_back(It{make_int2(q, (int)k), P.far_cost[k]});
@@ -571,6 +568,11 @@ static int rebuild_tree_items(Engine* e) {
         e->any_tree = any;
         e->graph_dirty = true;   // the step gains or loses the treecode launches
     }
+    for (int p = 0; p < 3; ++p)
+        if (np_max[p] != e->tree_np[p]) {
+            e->tree_np[p] = np_max[p];
+            e->graph_dirty = true;   // the far kernels' shared memory changes
+        }
     return CTR_OK;
 }
 

@@ -79,6 +79,7 @@ struct Engine {
     DevBuf slots, stats, items[3], n_items, counters, err;
     // treecode work entries (slot, index) per pair arithmetic: moment chunks, far clusters, far items
     bool any_tree = false;
+    int tree_np[3] = {0, 0, 0};   // largest proxy count per arithmetic among the treecode slots
     int64_t tree_cap[3][3] = {};
     DevBuf tree_ent[3][3], tree_cnt, tree_counters;
     cudaGraphExec_t graph_exec = nullptr;

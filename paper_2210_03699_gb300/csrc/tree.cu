@@ -63,26 +63,7 @@ int download(std::vector<T>& h, const void* d, size_t n, cudaStream_t st) {
     return CTR_OK;
 }
 
-// occupancy of the far kernels (dynamic shared memory above 48 KB needs the opt-in), per device
-template <typename Real, int R, int NT>
-int far_per_sm() {
-    static std::mutex mu;
-    static int per_dev[64] = {0};
-    int dev = 0;
-    CTR_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(CTR_ERR_INVALID, "device index");
-    std::lock_guard<std::mutex> lk(mu);
-    if (per_dev[dev] == 0) {
-        const int smem = (int)tree_far_smem<Real>();
-        CTR_CUDA_TRY(cudaFuncSetAttribute(k_tree_far<Real, R, NT, OneTreeAcc>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        int b = 0;
-        CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tree_far<Real, R, NT, OneTreeAcc>, NT,
-                                                                   smem));
-        per_dev[dev] = std::max(1, b);
-    }
-    return per_dev[dev];
-}
+
 
 template <typename Real, int R, int NT>
 int launch_tree_t(ctr_ibim* s, int pol) {
@@ -104,11 +85,21 @@ int launch_tree_t(ctr_ibim* s, int pol) {
                                                                                 counts + 1, pol);
     CTR_LAUNCHED();
     if (R * NT != s->sched[pol].BS) return fail(CTR_ERR_INVALID, "treecode: far kernel shape != target block");
-    const int per_sm = far_per_sm<Real, R, NT>();
-    if (per_sm < 0) return per_sm;
-    k_tree_far<Real, R, NT, OneTreeAcc><<<std::min<int64_t>((int64_t)per_sm * sms, (int64_t)P.far.size()), NT,
-                                          tree_far_smem<Real>(), st>>>(acc, P.d_ent_far.as<int2>(), counts + 2,
-                                                                       counters + 1, pol);
+    static std::map<std::pair<int, int>, int> cache;
+    if constexpr (sizeof(Real) == 4) {
+        auto kern = k_tree_far2<R / 2, NT, OneTreeAcc>;
+        const int smem = (int)tree_far2_smem(P.np);
+        const int per_sm = far_per_sm(kern, NT, smem, (int)tree_far2_smem(), cache);
+        if (per_sm < 0) return per_sm;
+        kern<<<std::min<int64_t>((int64_t)per_sm * sms, (int64_t)P.far.size()), NT, smem, st>>>(
+            acc, P.d_ent_far.as<int2>(), counts + 2, counters + 1, pol);
+    } else {
+        auto kern = k_tree_far<Real, R, NT, OneTreeAcc>;
+        const int per_sm = far_per_sm(kern, NT, (int)tree_far_smem<Real>(), (int)tree_far_smem<Real>(), cache);
+        if (per_sm < 0) return per_sm;
+        kern<<<std::min<int64_t>((int64_t)per_sm * sms, (int64_t)P.far.size()), NT, tree_far_smem<Real>(), st>>>(
+            acc, P.d_ent_far.as<int2>(), counts + 2, counters + 1, pol);
+    }
     CTR_LAUNCHED();
     return CTR_OK;
 }
@@ -125,11 +116,11 @@ int launch_tree(ctr_ibim* s, int pol) {
 int64_t tree_bytes(const ctr_ibim* s) {
     if (!s->tree) return 0;
     const TreeData& t = *s->tree;
-    int64_t b = (int64_t)(t.d_tinv.bytes + t.d_eptr.bytes + t.d_excl.bytes + t.d_xref.bytes + t.d_bw.bytes +
-                          t.d_dref.bytes + t.d_counters.bytes + t.d_view.bytes);
+    int64_t b = (int64_t)(t.d_tinv.bytes + t.d_eptr.bytes + t.d_excl.bytes + t.d_counters.bytes + t.d_view.bytes);
     for (const auto& P : t.pol)
-        b += (int64_t)(P.d_box.bytes + P.d_chunks.bytes + P.d_cptr.bytes + P.d_mpart.bytes + P.d_mom.bytes +
-                       P.d_far.bytes + P.d_flist.bytes + P.d_ent_mom.bytes + P.d_ent_red.bytes + P.d_ent_far.bytes);
+        b += (int64_t)(P.d_xref.bytes + P.d_bw.bytes + P.d_dref.bytes + P.d_box.bytes + P.d_chunks.bytes +
+                       P.d_cptr.bytes + P.d_mpart.bytes + P.d_mom.bytes + P.d_far.bytes + P.d_flist.bytes +
+                       P.d_ent_mom.bytes + P.d_ent_red.bytes + P.d_ent_far.bytes);
     return b;
 }
 
@@ -139,12 +130,15 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
     if (M > INT32_MAX / 4) return fail(CTR_ERR_CAPACITY, "treecode: too many nodes");
     auto T = std::make_unique<TreeData>();
     TreeData& t = *T;
-    t.degree = s->opt.tree_degree;
-    t.theta = s->opt.tree_theta;
     t.leaf = s->opt.tree_leaf;
-    t.n1 = t.degree + 1;
-    t.np = t.n1 * t.n1 * t.n1;
     t.g = (int)std::ceil(s->eps / s->h);
+    for (int p = 0; p < 3; ++p) {   // the FP32 operator (inner GMRES) has its own degree and theta
+        TreeData::Pol& P = t.pol[p];
+        P.degree = p == 0 ? s->opt.tree_degree_fp32 : s->opt.tree_degree;
+        P.theta = p == 0 ? s->opt.tree_theta_fp32 : s->opt.tree_theta;
+        P.n1 = P.degree + 1;
+        P.np = P.n1 * P.n1 * P.n1;
+    }
     // ---- node indices, closest points, correction sets (host copies)
     std::vector<int64_t> lin;
     std::vector<double> Px, Py, Pz;
@@ -188,30 +182,33 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
     CTR_TRY(permute_rows<float4>(s->src32, d_perm, M, 4, st));
     CTR_TRY(permute_rows<double4>(s->src64, d_perm, M, 2, st));
     CTR_TRY(permute_rows<float4>(s->srcdf, d_perm, M, 4, st));
-    // ---- Chebyshev points of the second kind, barycentric weights, differentiation matrix
-    const int n = t.degree, n1 = t.n1;
-    std::vector<double> xr(n1), bw(n1), dr((size_t)n1 * n1, 0.0);
-    for (int m = 0; m < n1; ++m) {
-        xr[m] = std::cos(kPi * m / n);
-        bw[m] = ((m % 2) ? -1.0 : 1.0) * ((m == 0 || m == n) ? 0.5 : 1.0);
+    // ---- per arithmetic: Chebyshev points of the second kind, barycentric weights, differentiation matrix
+    for (int p = 0; p < 3; ++p) {
+        TreeData::Pol& P = t.pol[p];
+        const int n = P.degree, n1 = P.n1;
+        std::vector<double> xr(n1), bw(n1), dr((size_t)n1 * n1, 0.0);
+        for (int m = 0; m < n1; ++m) {
+            xr[m] = std::cos(kPi * m / n);
+            bw[m] = ((m % 2) ? -1.0 : 1.0) * ((m == 0 || m == n) ? 0.5 : 1.0);
+        }
+        for (int m = 0; m < n1; ++m) {
+            double diag = 0.0;
+            for (int q = 0; q < n1; ++q)
+                if (q != m) {
+                    dr[(size_t)m * n1 + q] = (bw[q] / bw[m]) / (xr[m] - xr[q]);
+                    diag += dr[(size_t)m * n1 + q];
+                }
+            dr[(size_t)m * n1 + m] = -diag;
+        }
+        CTR_TRY(upload(P.d_xref, xr, st));
+        CTR_TRY(upload(P.d_bw, bw, st));
+        CTR_TRY(upload(P.d_dref, dr, st));
+        CTR_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    for (int m = 0; m < n1; ++m) {
-        double diag = 0.0;
-        for (int q = 0; q < n1; ++q)
-            if (q != m) {
-                dr[(size_t)m * n1 + q] = (bw[q] / bw[m]) / (xr[m] - xr[q]);
-                diag += dr[(size_t)m * n1 + q];
-            }
-        dr[(size_t)m * n1 + m] = -diag;
-    }
-    CTR_TRY(upload(t.d_xref, xr, st));
-    CTR_TRY(upload(t.d_bw, bw, st));
-    CTR_TRY(upload(t.d_dref, dr, st));
     // ---- per pair arithmetic: lists, items, chunks, regions
     const int Rs[3] = {kR32 * Fp32x2Policy::kPack, kRdf, kR64};
     const int tiles[3] = {Fp32x2Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
     const size_t real_bytes[3] = {sizeof(float), sizeof(float), sizeof(double)};
-    const int tq = tree::theta_q(t.theta);
     int64_t need = 1;
     std::vector<int> counts(15, 0);
     for (int p = 0; p < 3; ++p) {
@@ -227,8 +224,8 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         const int nb = (int)((M + BS - 1) / BS);
         sc.nb = nb;
         tree::Lists L;
-        tree::interaction_lists(oct, ijk.data(), cptr.data(), excl.data(), BS, tq, (int64_t)(t.np / kMinFarDiv[p]),
-                                t.g, L);
+        tree::interaction_lists(oct, ijk.data(), cptr.data(), excl.data(), BS, tree::theta_q(P.theta),
+                                (int64_t)(P.np / kMinFarDiv[p]), t.g, L);
         // far clusters that carry charges, in increasing cluster id
         std::vector<int32_t> ids(L.far_cl);
         std::sort(ids.begin(), ids.end());
@@ -268,7 +265,7 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
             const int64_t nt = std::min<int64_t>(BS, M - (int64_t)I * BS);
             for (int64_t r = L.near_ptr[(size_t)I]; r < L.near_ptr[(size_t)I + 1]; ++r)
                 near_total += (double)BS * (L.near_rng[2 * (size_t)r + 1] - L.near_rng[2 * (size_t)r]);
-            far_total += (double)BS * t.np * kFarCost[p] * (double)(L.far_ptr[(size_t)I + 1] - L.far_ptr[(size_t)I]);
+            far_total += (double)BS * P.np * kFarCost[p] * (double)(L.far_ptr[(size_t)I + 1] - L.far_ptr[(size_t)I]);
             (void)nt;
         }
         const double near_cmax = std::max(1.0, near_total / ((double)kTreeItemsPerSlot * std::max(1, slots[p])));
@@ -310,8 +307,8 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
             const int64_t nt = std::min<int64_t>(BS, M - (int64_t)I * BS);
             const int64_t f0 = L.far_ptr[(size_t)I], f1 = L.far_ptr[(size_t)I + 1];
             P.far_pairs += f1 - f0;
-            P.far_evals += nt * (f1 - f0) * t.np;
-            const double unit = (double)BS * t.np * kFarCost[p];
+            P.far_evals += nt * (f1 - f0) * P.np;
+            const double unit = (double)BS * P.np * kFarCost[p];
             const int64_t per_item = std::max<int64_t>(1, (int64_t)std::floor(far_cmax / unit));
             for (int64_t a = f0; a < f1; a += per_item) {
                 const int64_t b = std::min<int64_t>(f1, a + per_item);
@@ -356,8 +353,8 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         CTR_TRY(upload(P.d_cptr, ccp, st));
         CTR_TRY(upload(P.d_far, P.far, st));
         CTR_TRY(upload(P.d_flist, flist, st));
-        CTR_TRY(P.d_mpart.alloc(real_bytes[p] * 2 * (size_t)t.np * std::max<size_t>(1, P.chunks.size())));
-        CTR_TRY(P.d_mom.alloc(real_bytes[p] * 3 * (size_t)t.np * std::max<size_t>(1, ids.size())));
+        CTR_TRY(P.d_mpart.alloc(real_bytes[p] * 2 * (size_t)P.np * std::max<size_t>(1, P.chunks.size())));
+        CTR_TRY(P.d_mom.alloc(real_bytes[p] * 3 * (size_t)P.np * std::max<size_t>(1, ids.size())));
         auto entries = [](const std::vector<double>& cost) {
             std::vector<int> o(cost.size());
             std::iota(o.begin(), o.end(), 0);
@@ -387,14 +384,14 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
     TreeView& v = t.view;
     v.on = 1;
     v.M = (int)M;
-    v.n1 = t.n1;
-    v.np = t.np;
     v.tinv = t.d_tinv.as<int32_t>();
-    v.xref = t.d_xref.as<double>();
-    v.bw = t.d_bw.as<double>();
-    v.dref = t.d_dref.as<double>();
     for (int p = 0; p < 3; ++p) {
         TreeData::Pol& P = t.pol[p];
+        v.n1[p] = P.n1;
+        v.np[p] = P.np;
+        v.xref[p] = P.d_xref.as<double>();
+        v.bw[p] = P.d_bw.as<double>();
+        v.dref[p] = P.d_dref.as<double>();
         v.box[p] = P.d_box.as<double>();
         v.chunks[p] = P.d_chunks.as<MomChunk>();
         v.cptr[p] = P.d_cptr.as<int32_t>();

@@ -25,6 +25,9 @@
 // to nothing when that handle is not in this pass).
 #pragma once
 
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "pairkern.cuh"
 
@@ -34,8 +37,9 @@ using pk::kThreads;
 
 constexpr int kMomTile = 32;      // sources per shared tile of the moment kernel
 // far kernel shape per pair arithmetic: R targets per thread x NT threads = the target block
-constexpr int kTreeR[3] = {4, 4, 1};
-constexpr int kTreeNT[3] = {256, 64, 256};
+// (FP32 charges: packed pairs of targets, R / 2 per thread; FP64: scalar)
+constexpr int kTreeR[3] = {4, 2, 1};
+constexpr int kTreeNT[3] = {256, 128, 256};
 constexpr int kChunkSrc = 2048;   // sources per moment chunk
 
 template <typename Real>
@@ -83,13 +87,13 @@ __global__ void __launch_bounds__(kThreads) k_tree_mom(Acc acc, const int2* __re
         const TreeView* tp = acc.view(w.x);
         if (!tp) continue;   // block-uniform
         const TreeView& t = *tp;
-        const int n1 = t.n1, np = t.np;
+        const int n1 = t.n1[pol], np = t.np[pol];
         const MomChunk ch = t.chunks[pol][w.y];
         for (int i = tid; i < n1; i += kThreads) {
-            xr[i] = (Real)t.xref[i];
-            bw[i] = (Real)t.bw[i];
+            xr[i] = (Real)t.xref[pol][i];
+            bw[i] = (Real)t.bw[pol][i];
         }
-        for (int i = tid; i < n1 * n1; i += kThreads) dr[i] = (Real)t.dref[i];
+        for (int i = tid; i < n1 * n1; i += kThreads) dr[i] = (Real)t.dref[pol][i];
         const double* bx = t.box[pol] + 6 * (int64_t)ch.q;
         Real accD[kTreeMaxN1], accS[kTreeMaxN1];
 #pragma unroll
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_momred(Acc acc, const int2* _
         const TreeView* tp = acc.view(w.x);
         if (!tp) continue;
         const TreeView& t = *tp;
-        const int np = t.np, q = w.y;
+        const int np = t.np[pol], q = w.y;
         const int c0 = t.cptr[pol][q], c1 = t.cptr[pol][q + 1];
         const Real* mp = static_cast<const Real*>(t.mpart[pol]);
         Real* Q = static_cast<Real*>(t.mom[pol]) + (size_t)q * 3 * np;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(NT) k_tree_far(Acc acc, const int2* __restrict
         const TreeView* tp = acc.view(w.x);
         if (!tp) continue;
         const TreeView& t = *tp;
-        const int n1 = t.n1, np = t.np, M = t.M, BS = t.BS[pol];
+        const int n1 = t.n1[pol], np = t.np[pol], M = t.M, BS = t.BS[pol];
         const FarItem f = t.far[pol][w.y];
         const Real kappa = (Real)t.kappa;
         const Real kl2 = (Real)(-t.kappa * 1.4426950408889634);
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(NT) k_tree_far(Acc acc, const int2* __restrict
             const double* bx = t.box[pol] + 6 * (int64_t)q;
             for (int i = tid; i < 3 * n1; i += NT) {
                 const int ax = i / n1, m = i % n1;
-                sx[ax * kTreeMaxN1 + m] = (Real)(bx[ax] + bx[3 + ax] * t.xref[m]);
+                sx[ax * kTreeMaxN1 + m] = (Real)(bx[ax] + bx[3 + ax] * t.xref[pol][m]);
             }
             const Real* Q = static_cast<const Real*>(t.mom[pol]) + (size_t)q * 3 * np;
             for (int i = tid; i < 3 * np; i += NT) sq[i] = Q[i];
@@ -321,10 +325,153 @@ __global__ void __launch_bounds__(NT) k_tree_far(Acc acc, const int2* __restrict
     }
 }
 
+// FP32 far items with two targets per f32x2 register pair (RP pairs per thread): the
+// FMA-pipe work of two evaluations in one instruction, rsqrt and ex2 per half on
+// the SFU; proxies and charges are duplicated into 64-bit words in shared memory.
+// Dynamic shared memory of k_tree_far2 for clusters of np proxies.
+constexpr size_t tree_far2_smem(int np = kTreeMaxNp) { return sizeof(unsigned long long) * (3 * kTreeMaxN1 + 3 * np); }
+
+template <int RP, int NT, class Acc>
+__global__ void __launch_bounds__(NT) k_tree_far2(Acc acc, const int2* __restrict__ ent,
+                                               const int* __restrict__ n_ent, int* __restrict__ counter, int pol) {
+    using pk::u64;
+    extern __shared__ __align__(16) unsigned char tree_smem[];
+    u64* sx = reinterpret_cast<u64*>(tree_smem);   // [3][kTreeMaxN1]
+    u64* sq = sx + 3 * kTreeMaxN1;                 // [3][np]
+    __shared__ int cur;
+    const int tid = threadIdx.x;
+    const int total = *n_ent;
+    for (;;) {
+        const int it = tree_next<Acc>(counter, &cur);
+        if (it >= total) break;
+        const int2 w = ent[it];
+        const TreeView* tp = acc.view(w.x);
+        if (!tp) continue;
+        const TreeView& t = *tp;
+        const int n1 = t.n1[pol], np = t.np[pol], M = t.M, BS = t.BS[pol];
+        const FarItem f = t.far[pol][w.y];
+        const float kap = (float)t.kappa;
+        const float kl2 = (float)(-t.kappa * 1.4426950408889634);
+        const u64 kap2 = pk::pk2(kap, kap), kl2x2 = pk::pk2(kl2, kl2), one2 = pk::pk2(1.f, 1.f);
+        u64 px[RP], py[RP], pz[RP], nx[RP], ny[RP], nz[RP];
+        double o1[2 * RP], o2[2 * RP];
+        int64_t pp[2 * RP];
+#pragma unroll
+        for (int j = 0; j < RP; ++j) {
+            float P[2][3], n[2][3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 2 * j + h;
+                pp[r] = (int64_t)f.I * BS + r * NT + tid;
+                float a, b;
+                tree_source<float>(t, pol, pp[r] < M ? pp[r] : (int64_t)M - 1, P[h], n[h], a, b);
+                o1[r] = 0.0, o2[r] = 0.0;
+            }
+            px[j] = pk::pk2(P[0][0], P[1][0]), py[j] = pk::pk2(P[0][1], P[1][1]), pz[j] = pk::pk2(P[0][2], P[1][2]);
+            nx[j] = pk::pk2(n[0][0], n[1][0]), ny[j] = pk::pk2(n[0][1], n[1][1]), nz[j] = pk::pk2(n[0][2], n[1][2]);
+        }
+        for (int l = f.l0; l < f.l1; ++l) {
+            const int q = t.flist[pol][l];
+            __syncthreads();   // the previous cluster's proxies are no longer read
+            const double* bx = t.box[pol] + 6 * (int64_t)q;
+            for (int i = tid; i < 3 * n1; i += NT) {
+                const int ax = i / n1, m = i % n1;
+                const float v = (float)(bx[ax] + bx[3 + ax] * t.xref[pol][m]);
+                sx[ax * kTreeMaxN1 + m] = pk::pk2(v, v);
+            }
+            const float* Q = static_cast<const float*>(t.mom[pol]) + (size_t)q * 3 * np;
+            for (int i = tid; i < 3 * np; i += NT) {
+                const float v = Q[i];
+                sq[i] = pk::pk2(v, v);
+            }
+            __syncthreads();
+            u64 a1[RP], a2[RP];
+#pragma unroll
+            for (int j = 0; j < RP; ++j) a1[j] = a2[j] = 0ull;   // +0.0f in both halves
+            for (int k3 = 0; k3 < n1; ++k3) {
+                const u64 sz = sx[2 * kTreeMaxN1 + k3];
+                u64 dz2[RP], dzn[RP];
+#pragma unroll
+                for (int j = 0; j < RP; ++j) {
+                    const u64 dz = pk::sub2(pz[j], sz);
+                    dz2[j] = pk::mul2(dz, dz);
+                    dzn[j] = pk::mul2(dz, nz[j]);
+                }
+                for (int k2 = 0; k2 < n1; ++k2) {
+                    const u64 sy = sx[kTreeMaxN1 + k2];
+                    u64 ryz[RP], dyzn[RP];
+#pragma unroll
+                    for (int j = 0; j < RP; ++j) {
+                        const u64 dy = pk::sub2(py[j], sy);
+                        ryz[j] = pk::fma2(dy, dy, dz2[j]);
+                        dyzn[j] = pk::fma2(dy, ny[j], dzn[j]);
+                    }
+                    const int kb = (k3 * n1 + k2) * n1;
+                    for (int k1 = 0; k1 < n1; ++k1) {
+                        const u64 sxk = sx[k1];
+                        const u64 q0 = sq[kb + k1], qk = sq[np + kb + k1], qkp = sq[2 * np + kb + k1];
+#pragma unroll
+                        for (int j = 0; j < RP; ++j) {
+                            const u64 dx = pk::sub2(px[j], sxk);
+                            const u64 r2 = pk::fma2(dx, dx, ryz[j]);
+                            const u64 dn = pk::fma2(dx, nx[j], dyzn[j]);
+                            const u64 ri = pk::rsqrt2(r2);
+                            const u64 r = pk::mul2(r2, ri);
+                            const u64 E = pk::ex2_2(pk::mul2(kl2x2, r));
+                            a1[j] = pk::fma2(ri, pk::fma2(E, qk, q0), a1[j]);
+                            const u64 Ef = pk::mul2(E, pk::fma2(kap2, r, one2));
+                            const u64 ri3 = pk::mul2(pk::mul2(ri, ri), ri);
+                            a2[j] = pk::fma2(pk::mul2(dn, ri3), pk::fma2(Ef, qkp, q0), a2[j]);   // -(out2)
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RP; ++j) {
+                float x0, x1, y0, y1;
+                pk::up2(a1[j], x0, x1);
+                pk::up2(a2[j], y0, y1);
+                o1[2 * j] += (double)x0, o1[2 * j + 1] += (double)x1;
+                o2[2 * j] -= (double)y0, o2[2 * j + 1] -= (double)y1;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2 * RP; ++r) {
+            if (pp[r] < M) {
+                const int64_t off = pp[r] - (int64_t)f.I * BS;
+                t.part[f.ibase + off] = o1[r];
+                t.part[f.ibase + BS + off] = o2[r];
+            }
+        }
+    }
+}
+
 // Work entries of one handle alone: every entry belongs to it.
 struct OneTreeAcc {
     const TreeView* t;
     __device__ const TreeView* view(int) const { return t; }
 };
+
+// Resident blocks per SM of a far kernel instantiation with `smem` bytes of dynamic shared memory (host):
+// the kernel's opt-in to `smem_max` (above 48 KB) is set once per device; results are cached per
+// (device, smem) in `cache`.
+template <typename K>
+int far_per_sm(K kernel, int threads, int smem, int smem_max, std::map<std::pair<int, int>, int>& cache) {
+    static std::mutex mu;
+    int dev = 0;
+    CTR_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({dev, smem});
+    if (it != cache.end()) return it->second;
+    if (cache.find({dev, -1}) == cache.end()) {
+        CTR_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+        cache[{dev, -1}] = 1;
+    }
+    int b = 0;
+    CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem));
+    b = std::max(1, b);
+    cache[{dev, smem}] = b;
+    return b;
+}
 
 }  // namespace ctr

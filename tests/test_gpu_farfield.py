@@ -7,8 +7,10 @@ Tolerances:
   * float-float operator (near field float-float, far field FP32): 1e-6;
   * FP32 operator: 2e-5, as for the direct sum;
   * against the exact punctured sum (the approximation itself): 1e-6 at the default
-    degree 10, theta 0.8 (the oracle measures ~6e-8);
-  * solves: polarization energy within 1e-6 of the direct solve.
+    degree 10, theta 0.8 (the oracle measures ~6e-8); 4e-5 for the FP32 operator (its own
+    degree 6, theta 0.9: ~7e-6, plus the FP32 rounding);
+  * solves (to 1e-6, above the floor the FP32 far field puts under the residual): polarization
+    energy within 1e-6 of the direct solve.
 """
 import math
 
@@ -21,7 +23,8 @@ from oracle.system import OracleSystem
 
 pytestmark = pytest.mark.gpu
 
-SMALL = dict(tree_degree=4, tree_theta=0.7, tree_leaf=32)   # a large far field at test sizes
+SMALL = dict(tree_degree=4, tree_theta=0.7, tree_leaf=32, tree_degree_fp32=4,
+             tree_theta_fp32=0.7)   # a large far field at test sizes, the same degree in every arithmetic
 
 
 def _rel(a, b):
@@ -97,7 +100,8 @@ def test_tree_fp64_on_molecule_matches_oracle(ctr, oracle_tables):
 
 
 def test_tree_default_parameters_close_to_direct(ctr, ellipsoid):
-    """Default degree 10, theta 0.8: the accelerated operator within 1e-6 of the direct one."""
+    """Default degree 10, theta 0.8: the accelerated operator within 1e-6 of the direct one; the FP32 operator
+    (degree 6, theta 0.9, ~7e-6, below its own rounding) within 4e-5."""
     prob, S, _ = ellipsoid
     G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube,
                                                            farfield=ctr.FARFIELD_TREECODE))
@@ -106,16 +110,17 @@ def test_tree_default_parameters_close_to_direct(ctr, ellipsoid):
     yd = D.matvec(p, ctr.FP64)
     assert _rel(G.matvec(p, ctr.FP64), yd) < 1e-6
     assert _rel(G.matvec(p, ctr.DF64), yd) < 1e-6
-    assert _rel(G.matvec(p, ctr.FP32_REFINE), yd) < 3e-5
+    assert _rel(G.matvec(p, ctr.FP32_REFINE), yd) < 4e-5
     G.close()
     D.close()
 
 
 def test_tree_solve_energy_and_batching(ctr, ellipsoid):
-    """FP32-refined solve on the treecode (the engine's treecode kernels): energy within 1e-6 of the direct
-    solve; solving it in one engine with a direct-sum system changes neither result."""
+    """FP32-refined solve on the treecode (the engine's treecode kernels) to 1e-6 (the FP32 far field of the
+    residual sets a floor near 1e-7 to 3e-7): energy within 1e-6 of the direct solve; solving it in one
+    engine with a direct-sum system changes neither result."""
     prob, S, _ = ellipsoid
-    opt = dict(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE, tol=1e-7)
+    opt = dict(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE, tol=1e-6)
     T = ctr.CtrIbim.from_problem(prob, options=ctr.Options(farfield=ctr.FARFIELD_TREECODE, **opt))
     D = ctr.CtrIbim.from_problem(prob, options=ctr.Options(**opt))
     psi_t, dpsi_t, it = T.solve()
@@ -147,5 +152,5 @@ def test_tree_full_size_sampled_rows(ctr, oracle_tables):
     y32 = G.matvec(p, ctr.FP32_REFINE)
     assert np.all(np.isfinite(ydf)) and np.all(np.isfinite(y32))
     assert _rel(ydf[sel], ref) < 1e-6
-    assert _rel(y32[sel], ref) < 3e-5
+    assert _rel(y32[sel], ref) < 4e-5
     G.close()
