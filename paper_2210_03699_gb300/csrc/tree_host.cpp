@@ -182,6 +182,7 @@ extern "C" int ctr_farfield_plan(int64_t M, const int32_t* ijk, const int32_t* e
     using namespace ctr;
     try {
         if (M <= 0 || !ijk || !excl_ptr || !excl) return fail(CTR_ERR_INVALID, "farfield plan: bad nodes");
+        if (M > INT32_MAX / 4) return fail(CTR_ERR_CAPACITY, "farfield plan: too many nodes");
         if (degree < 2 || degree > 12 || leaf < 1 || block < 1 || margin < 0 || !(theta >= 0.0 && theta < 1.0))
             return fail(CTR_ERR_INVALID, "farfield plan: bad parameters");
         tree::Octree t;

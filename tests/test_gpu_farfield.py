@@ -154,3 +154,35 @@ def test_tree_full_size_sampled_rows(ctr, oracle_tables):
     assert _rel(ydf[sel], ref) < 1e-6
     assert _rel(y32[sel], ref) < 4e-5
     G.close()
+
+
+def test_server_mixes_treecode_and_direct_requests(ctr):
+    """The server admits treecode requests beside direct-sum ones (the engine runs both kinds of pair
+    work and the far-field kernels in one step); each result equals the system solved alone, bitwise."""
+    import time
+    probs = [syn.ellipsoid_problem(h=0.1), syn.ellipsoid_problem(h=0.2, seed=1),
+             syn.molecule_problem(n_atoms=40, seed=5, h=0.5), syn.ellipsoid_problem(h=0.1, seed=2)]
+    tree = dict(farfield=ctr.FARFIELD_TREECODE, tol=1e-6, **SMALL)
+    opts = [ctr.Options(tube_halfwidth=probs[0].tube, precision=ctr.FP32_REFINE, **tree),
+            ctr.Options(tube_halfwidth=probs[1].tube, precision=ctr.FP32_REFINE),
+            ctr.Options(tube_halfwidth=probs[2].tube, precision=ctr.FP32_REFINE, farfield=ctr.FARFIELD_TREECODE,
+                        tol=1e-6),
+            ctr.Options(tube_halfwidth=probs[3].tube, precision=ctr.FP64, **tree)]
+    alone = []
+    for p, o in zip(probs, opts):
+        G = ctr.CtrIbim.from_problem(p, options=o)
+        psi, dpsi, info = G.solve()
+        alone.append((psi, dpsi, G.energy(psi, dpsi)[0], info))
+        G.close()
+    with ctr.Server(max_slots=3) as sv:
+        tickets = []
+        for k, (p, o) in enumerate(zip(probs, opts)):
+            tickets.append(sv.submit_problem(p, o))
+            time.sleep(0.01 * k)
+        results = [sv.wait(t, timeout=600) for t in tickets]
+        for t, r, (psi, dpsi, Gp, info) in zip(tickets, results, alone):
+            assert r.status == 0 and r.info.converged, r
+            bpsi, bdpsi = sv.fetch(t, r.M)
+            assert np.array_equal(bpsi, psi) and np.array_equal(bdpsi, dpsi)
+            assert r.G_pol == Gp
+            sv.release(t)
