@@ -262,11 +262,9 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         // near items (one-sided pair items over tree positions) and far items, with their regions
         double near_total = 0.0, far_total = 0.0;
         for (int I = 0; I < nb; ++I) {
-            const int64_t nt = std::min<int64_t>(BS, M - (int64_t)I * BS);
             for (int64_t r = L.near_ptr[(size_t)I]; r < L.near_ptr[(size_t)I + 1]; ++r)
                 near_total += (double)BS * (L.near_rng[2 * (size_t)r + 1] - L.near_rng[2 * (size_t)r]);
             far_total += (double)BS * P.np * kFarCost[p] * (double)(L.far_ptr[(size_t)I + 1] - L.far_ptr[(size_t)I]);
-            (void)nt;
         }
         const double near_cmax = std::max(1.0, near_total / ((double)kTreeItemsPerSlot * std::max(1, slots[p])));
         const double far_cmax = std::max(1.0, far_total / ((double)kTreeItemsPerSlot * std::max(1, slots[p])));

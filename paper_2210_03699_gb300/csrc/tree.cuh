@@ -15,11 +15,12 @@
 //                  barycentric basis and derivative in shared memory; each
 //                  thread owns one (k2, k3) row of proxies);
 //   k_tree_momred  the chunks of a cluster added in a fixed order, Q formed;
-//   k_tree_far     far items (target block x a run of its far clusters; NT
-//                  threads with R targets each): the cluster's proxies and
-//                  charges in shared memory, FP32 sums
+//   k_tree_far2    far items (target block x a run of its far clusters) with
+//                  FP32 charges, two targets per f32x2 instruction; the
+//                  cluster's proxies and charges in shared memory, FP32 sums
 //                  per cluster folded into FP64 per target, written to the
-//                  item's partial region like a one-sided pair item.
+//                  item's partial region like a one-sided pair item;
+//   k_tree_far     the same in scalar arithmetic, used for FP64 charges.
 // The blocks of each kernel take work entries (handle, index) from a list
 // through an atomic counter; `Acc` maps an entry's handle to its TreeView (or
 // to nothing when that handle is not in this pass).
@@ -61,7 +62,7 @@ __device__ __forceinline__ void tree_source(const TreeView& t, int pol, int64_t 
     }
 }
 
-template <typename Acc>
+// The next work entry of this block from the atomic counter (block-uniform).
 __device__ __forceinline__ int tree_next(int* counter, int* cur) {
     if (threadIdx.x == 0) *cur = atomicAdd(counter, 1);
     __syncthreads();
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_mom(Acc acc, const int2* __re
     const int tid = threadIdx.x;
     const int total = *n_ent;
     for (;;) {
-        const int it = tree_next<Acc>(counter, &cur);
+        const int it = tree_next(counter, &cur);
         if (it >= total) break;
         const int2 w = ent[it];
         const TreeView* tp = acc.view(w.x);
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(NT) k_tree_far(Acc acc, const int2* __restrict
     const int tid = threadIdx.x;
     const int total = *n_ent;
     for (;;) {
-        const int it = tree_next<Acc>(counter, &cur);
+        const int it = tree_next(counter, &cur);
         if (it >= total) break;
         const int2 w = ent[it];
         const TreeView* tp = acc.view(w.x);
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(NT) k_tree_far2(Acc acc, const int2* __restric
     const int tid = threadIdx.x;
     const int total = *n_ent;
     for (;;) {
-        const int it = tree_next<Acc>(counter, &cur);
+        const int it = tree_next(counter, &cur);
         if (it >= total) break;
         const int2 w = ent[it];
         const TreeView* tp = acc.view(w.x);
