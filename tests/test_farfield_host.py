@@ -55,3 +55,39 @@ def test_plan_theta_zero_and_bad_arguments(systems):
         ctr.farfield_plan(S.geo.ijk, S.excl_ptr, S.excl_idx, 2, 13, 0.8, 64, 256)
     with pytest.raises(ctr.CtrError):
         ctr.farfield_plan(S.geo.ijk, S.excl_ptr, S.excl_idx, 2, 10, 1.0, 64, 256)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plan_matches_oracle_on_random_point_sets(seed):
+    """Random integer point sets (a dense blob, a flat slab one cell thick, scattered points) with random
+    exclusion sets: cells that cannot be split along every axis, uneven octants, empty ones."""
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    blob = rng.integers(0, 24, size=(1500, 3))
+    slab = np.column_stack([rng.integers(30, 90, 1200), rng.integers(0, 60, 1200), np.full(1200, 7)])
+    far = rng.integers(-200, 200, size=(300, 3))
+    pts = np.unique(np.concatenate([blob, slab, far]), axis=0)
+    pts = pts[rng.permutation(pts.shape[0])]
+    M = pts.shape[0]
+    cnt = rng.integers(0, 6, size=M) * (rng.random(M) < 0.02)   # scattered exclusions: most clusters stay free
+    ptr = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    idx = np.concatenate([np.sort(rng.choice(M, size=c, replace=False)) for c in cnt]).astype(np.int64)
+    n_far = 0
+    for block, degree, theta, leaf, g in [(64, 2, 0.5, 8, 1), (256, 3, 0.8, 16, 2), (32, 2, 0.95, 4, 0)]:
+        plan = ctr.farfield_plan(pts, ptr, idx, g, degree, theta, leaf, block, 20)
+        tree = tc.build_tree(pts, leaf)
+        L = tc.interaction_lists(tree, pts, ptr, idx, block, theta, degree, g, min_far=20)
+        assert np.array_equal(plan["perm"], tree.perm)
+        assert np.array_equal(plan["near_ptr"], L.near_ptr)
+        assert np.array_equal(plan["near_rng"], L.near_rng)
+        assert np.array_equal(plan["far_ptr"], L.far_ptr)
+        assert np.array_equal(plan["far_begin"], np.array([tree.begin[c] for c in L.far_cl], dtype=np.int64))
+        n_far += L.far_cl.size
+    assert n_far > 0
+
+
+def test_separation_ties_are_not_separated():
+    """theta |c_B - c_C| = r_B + r_C exactly is not separated (strict inequality), on both sides of it."""
+    # radii 3 and 3 in doubled units (R2 = 9), theta = 1/2: separated iff the doubled distance exceeds 12
+    assert not tc.separated([0, 0, 0], 9, [12, 0, 0], 9, 512)
+    assert tc.separated([0, 0, 0], 9, [13, 0, 0], 9, 512)
+    assert not tc.separated([0, 0, 0], 9, [0, 0, 0], 9, 1023)
