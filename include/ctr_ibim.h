@@ -95,7 +95,10 @@ enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
  *       operator, which only drives the inner GMRES, uses its own degree and
  *       theta, 6 and 0.9 by default: about 7e-6).  The far field is
  *       FP32 in the CTR_FP32_REFINE and CTR_DF64 arithmetics and FP64 in
- *       CTR_FP64; the direct part keeps the arithmetic's pair kernels.
+ *       CTR_FP64; the direct part keeps the arithmetic's pair kernels.  So a
+ *       CTR_FP32_REFINE solve on the treecode reaches a relative residual near
+ *       1e-7 at best (its float-float residual has an FP32 far field): use a
+ *       tolerance of about 1e-6; CTR_FP64 solves have no such floor.
  */
 enum { CTR_FARFIELD_DIRECT = 0, CTR_FARFIELD_TREECODE = 1 };
 

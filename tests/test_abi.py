@@ -45,6 +45,12 @@ def test_status_strings_and_defaults(library):
     o = ctr._Options()
     ctr.lib.ctr_default_options(ctypes.byref(o))
     assert o.tol == 1e-10 and o.restart == 64 and o.precision == ctr.FP64
+    assert o.farfield == ctr.FARFIELD_DIRECT and o.tree_degree == 10 and o.tree_theta == 0.8
+    assert o.tree_leaf == 128 and o.tree_degree_fp32 == 6 and o.tree_theta_fp32 == 0.9
+    # the binding's mirror of ctr_options has the C layout: its defaults match the library's
+    d = ctr.Options()
+    assert (d.tree_degree, d.tree_theta, d.tree_leaf, d.tree_degree_fp32, d.tree_theta_fp32) == (
+        o.tree_degree, o.tree_theta, o.tree_leaf, o.tree_degree_fp32, o.tree_theta_fp32)
 
 
 def test_invalid_arguments_rejected_without_gpu(library):
@@ -59,3 +65,8 @@ def test_invalid_arguments_rejected_without_gpu(library):
     v = ctypes.c_int()
     assert ctr.lib.ctr_tuning_info(None, ctypes.byref(v), ctypes.byref(v)) == -1
     assert ctr.lib.ctr_ibim_matvec(None, None, None, ctr.FP32_REFINE, 0) == -1
+    assert ctr.lib.ctr_ibim_farfield_info(None, ctr.FP32_REFINE, None, None, None, None, None) == -1
+    d = ctypes.c_double()
+    assert ctr.lib.ctr_ibim_time_operator(None, ctr.FP32_REFINE, 1, ctypes.byref(d), None, None, None) == -1
+    assert ctr.lib.ctr_farfield_plan(0, None, None, None, 2, 10, 0.8, 128, 256, 0, None, None, None, None, None,
+                                     None, None, None) == -1

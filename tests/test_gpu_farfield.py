@@ -99,6 +99,17 @@ def test_tree_fp64_on_molecule_matches_oracle(ctr, oracle_tables):
     G.close()
 
 
+def test_time_operator_phases(ctr, ellipsoid):
+    """ctr_ibim_time_operator: the far phase is timed for a treecode handle, zero without one."""
+    prob, S, G = ellipsoid
+    t = G.time_operator(ctr.FP32_REFINE, reps=2)
+    assert t["far_ms"] > 0 and t["pairs_ms"] > 0 and t["pack_ms"] >= 0 and t["finish_ms"] > 0
+    D = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube))
+    d = D.time_operator(ctr.DF64, reps=1)
+    assert d["far_ms"] < 0.05 and d["pairs_ms"] > 0
+    D.close()
+
+
 def test_tree_default_parameters_close_to_direct(ctr, ellipsoid):
     """Default degree 10, theta 0.8: the accelerated operator within 1e-6 of the direct one; the FP32 operator
     (degree 6, theta 0.9, ~7e-6, below its own rounding) within 4e-5."""
