@@ -26,6 +26,8 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -158,7 +160,12 @@ def ellipsoid_sdist(grid: Grid, axes, band: float) -> np.ndarray:
     out = est.copy()
     sel = np.abs(est) < band
     Ps = P[sel]
-    xc = _ellipsoid_root(a, Ps)
+    # the root solve is elementwise: chunks on a thread pool (numpy releases the GIL) give the same bits
+    chunk = 65536
+    starts = range(0, Ps.shape[0], chunk)
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        parts = list(ex.map(lambda i: _ellipsoid_root(a, Ps[i:i + chunk]), starts))
+    xc = np.concatenate(parts) if parts else np.zeros((0, 3))
     dist = np.sqrt(np.sum((np.abs(Ps) - xc) ** 2, axis=1))
     sign = np.where(F[sel] > 0, 1.0, -1.0)
     out[sel] = sign * dist
