@@ -519,7 +519,8 @@ def farfield_plan(ijk, excl_ptr, excl, margin: int, degree: int = 10, theta: flo
     """Host-only tree and interaction lists of the treecode (see ctr_farfield_plan); no GPU needed.
 
     ijk: (M, 3) integer grid indices of the nodes; excl_ptr / excl: their correction sets (CSR);
-    min_far <= 0 selects (degree + 1)^3."""
+    min_far <= 0 selects (degree + 1)^3.  Besides the lists, returns the work of one application:
+    near_pairs (targets x directly summed sources) and far_evaluations (targets x proxy points)."""
     ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
     ep = np.ascontiguousarray(excl_ptr, dtype=np.int32)
     ex = np.ascontiguousarray(excl, dtype=np.int32)
@@ -540,8 +541,15 @@ def farfield_plan(ijk, excl_ptr, excl, margin: int, degree: int = 10, theta: flo
     fe = np.empty(max(1, n_far.value), dtype=np.int64)
     _check(lib.ctr_farfield_plan(*args, c(perm), ctypes.byref(n_near), ctypes.byref(n_far), c(near_ptr),
                                  c(near_rng), c(far_ptr), c(fb), c(fe)))
-    return {"perm": perm, "near_ptr": near_ptr, "near_rng": near_rng[:2 * n_near.value].reshape(-1, 2),
-            "far_ptr": far_ptr, "far_begin": fb[:n_far.value], "far_end": fe[:n_far.value]}
+    rng = near_rng[:2 * n_near.value].reshape(-1, 2)
+    # work of one application: targets per block x (direct sources, proxies of the far clusters)
+    nt = np.minimum(block, M - block * np.arange(nb)).astype(np.int64)
+    cs = np.concatenate([[0], np.cumsum(rng[:, 1] - rng[:, 0])])
+    near_per_block = cs[near_ptr[1:]] - cs[near_ptr[:-1]]
+    far_per_block = np.diff(far_ptr)
+    return {"perm": perm, "near_ptr": near_ptr, "near_rng": rng, "far_ptr": far_ptr, "far_begin": fb[:n_far.value],
+            "far_end": fe[:n_far.value], "near_pairs": int(np.sum(nt * near_per_block)),
+            "far_evaluations": int(np.sum(nt * far_per_block)) * (degree + 1) ** 3}
 
 
 def kernel_launches() -> int:

@@ -43,6 +43,13 @@ def test_plan_matches_oracle(systems, name, block, degree, theta, leaf, min_far)
     assert np.array_equal(plan["far_end"], np.array([tree.end[c] for c in L.far_cl], dtype=np.int64))
     if degree <= 4:
         assert L.far_cl.size > 0
+    op_near = op_far = 0
+    for I in range(L.near_ptr.size - 1):
+        nt = min(S.M, (I + 1) * block) - I * block
+        r = L.near_rng[L.near_ptr[I]:L.near_ptr[I + 1]]
+        op_near += nt * int(np.sum(r[:, 1] - r[:, 0]))
+        op_far += nt * int(L.far_ptr[I + 1] - L.far_ptr[I]) * (degree + 1) ** 3
+    assert plan["near_pairs"] == op_near and plan["far_evaluations"] == op_far
 
 
 def test_plan_theta_zero_and_bad_arguments(systems):
