@@ -73,6 +73,9 @@ def parse():
                     help="tree mode: solve tolerance (the FP32 far field sets a floor near 2e-7)")
     ap.add_argument("--tree-direct", action="store_true",
                     help="tree mode: also time the direct-sum applications at the same size")
+    ap.add_argument("--oracle-solves", action="store_true",
+                    help="with --impl reference: time whole oracle solves (sphere h=0.25, ellipsoid h=0.2) and one "
+                         "full oracle matvec of the 500-atom molecule on the host cores, one JSON line")
     ap.add_argument("--molecules", type=int, default=64, help="batch mode: molecules in the batch")
     ap.add_argument("--max-atoms", type=int, default=2000, help="batch/serve: largest molecule")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per load level")
@@ -224,9 +227,41 @@ def cpu_baseline(prob, seconds, threads=None):
     return OracleSample(prob, seconds, threads).run()
 
 
+def run_oracle_solves():
+    """Whole FP64 oracle solves (setup, GMRES to 1e-10, energy) and one full oracle matvec, host cores."""
+    import synthetic as syn
+    from oracle import energy, native
+    from oracle.system import OracleSystem
+    cache = os.path.join(ROOT, "oracle", "_build", "cache")
+    out = []
+    for name, prob in (("sphere R=2, h=0.25", syn.sphere_problem(h=0.25)),
+                       ("ellipsoid 4x3x2, h=0.2", syn.ellipsoid_problem(h=0.2))):
+        t0 = time.perf_counter()
+        S = OracleSystem.from_problem(prob, table_cache=cache)
+        t1 = time.perf_counter()
+        psi, dpsi, info = S.solve(tol=1e-10)
+        G, _ = energy.polarization_energy(S, psi, dpsi)
+        t2 = time.perf_counter()
+        out.append({"workload": name, "M": S.M, "setup_s": t1 - t0, "solve_s": t2 - t1, "G_pol": G,
+                    "iterations": int(info.get("iterations", -1)) if isinstance(info, dict) else None})
+    prob = syn.molecule_problem(n_atoms=500, seed=0, h=0.5)
+    S = OracleSystem.from_problem(prob, table_cache=cache)
+    p = syn.random_density(S.M, seed=2)
+    t0 = time.perf_counter()
+    S.punctured_sum(p)
+    dt = time.perf_counter() - t0
+    out.append({"workload": "molecule 500 atoms, h=0.5: one full punctured sum", "M": S.M, "matvec_s": dt,
+                "pairs_per_s": S.M * S.M / dt})
+    print(json.dumps({"impl": "reference", "mode": "oracle_solves", "cores": native.max_threads(), "results": out}),
+          flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle as it stands, timed on the host cores, as the reference arm."""
     if rank != 0:
+        return
+    if args.oracle_solves:
+        run_oracle_solves()
         return
     prob, cfg = workload(args.h)
     sample = OracleSample(prob, seconds=max(2.0, min(args.cpu_seconds, 20.0)))
