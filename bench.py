@@ -16,6 +16,7 @@ data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -30,7 +31,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# FP32-pipe lane operations per pair evaluation, counted from the kernel source (see the design notes):
+# Algorithmic work per pair interaction (one target, one source, one orientation): the minimal FP32 form of
+# the four kernels of Eq. (1.4) with their weights, an FMA counted as one FP32-pipe lane operation -- 3 sub,
+# 3 for r^2, 1 for r, 1 kappa r, 9 for the three dot products, 2 inverse powers, 3 for the Yukawa factor,
+# 4 for K11/K22, 1 for K12, about 11 for K21, 4 accumulations -- plus 2 SFU operations (rsqrt, ex2).  A
+# launch's algorithmic work is this times M^2 interactions; the same count serves every arithmetic
+# (float-float spends about ten FP32 operations per counted one, which its fraction shows).
+ALG_OPS = 43
+# The timed solve: GMRES restart length, FP32 inner tolerance and the solve tolerance
+RESTART, INNER_TOL, SOLVE_TOL = 64, 1e-5, 1e-10
+# FP32-pipe lane operations per pair evaluation as the kernels execute them, counted from the kernel source:
 # one-sided evaluations (one orientation) and symmetric ones (both orientations, with the share of the
 # in-warp transposed sums), for the packed FP32 and the float-float pair arithmetics (a packed f32x2
 # instruction counts as two lane operations, the FMA pipe's throughput being the same either way).
@@ -41,15 +51,34 @@ OPS_DF64 = {"one": 507, "sym": 501}
 # ncu count sm__inst_executed_pipe_fp64 x 32 / evaluations over one launch at h = 0.1 (69); its peak is the
 # measured DFMA probe rate, there being no FP64 unit count to go by.
 OPS_FP64 = {"one": 69, "sym": 69}
-# DRAM bytes (read + write) per launch of the schedule kernels at the default workload (h = 0.05), from one
-# ncu capture (profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt); None at any other size, or once
-# the kernels change.
-TRAFFIC_H005 = {"fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
+# DRAM bytes (read + write) per launch of the schedule kernels at the default workload (h = 0.05) from one
+# ncu capture, valid only while the kernel sources hash to `sources` (otherwise reported as null).
+TRAFFIC = {"profile": "profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt", "h": 0.05,
+           "sources": None, "fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
+KERNEL_SOURCES = ("paper_2210_03699_gb300/csrc/pairkern.cuh", "paper_2210_03699_gb300/csrc/schedule.cu")
 # Treecode far field (FP32 charges): FMA-pipe lane operations per proxy evaluation counted from the kernel
 # source (tree.cuh, k_tree_far2: 1 sub, 6 fma, 7 mul; an f32x2 instruction does two), plus 2 SFU operations
 # (rsqrt, ex2).
 OPS_FAR = 14
 SFU_FAR = 2
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(key, h):
+    """Measured DRAM bytes per launch of kernel `key`, when the record matches this workload and source."""
+    if abs(h - TRAFFIC["h"]) > 1e-12 or TRAFFIC.get(key) is None:
+        return None, None
+    if TRAFFIC["sources"] != kernel_sources_hash():
+        return None, f"{TRAFFIC['profile']} (stale: kernel sources changed since the capture)"
+    return TRAFFIC[key], TRAFFIC["profile"]
 
 
 def parse():
@@ -63,6 +92,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the baseline sample")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fp64-check", action="store_true",
+                    help="do not solve the workload in plain FP64 for the error_vs_fp64 object")
+    ap.add_argument("--skip-serve", action="store_true", help="do not run the bounded serving object")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels", "tree"],
                     help="solve: the default single-system line; batch: many molecules in one engine; "
                          "serve: continuous-batching server under Poisson arrivals; kernels: two FP32, two "
@@ -78,10 +110,15 @@ def parse():
                          "full oracle matvec of the 500-atom molecule on the host cores, one JSON line")
     ap.add_argument("--molecules", type=int, default=64, help="batch mode: molecules in the batch")
     ap.add_argument("--max-atoms", type=int, default=2000, help="batch/serve: largest molecule")
-    ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per load level")
-    ap.add_argument("--loads", default="0.5,0.8,0.95", help="serve mode: offered load / measured capacity")
+    ap.add_argument("--requests", type=int, default=1000, help="serve mode: requests per load level")
+    ap.add_argument("--capacity-requests", type=int, default=200,
+                    help="serve mode: requests of the saturated run that measures capacity")
+    ap.add_argument("--loads", default="0.8", help="serve mode: offered load / measured capacity (comma list)")
     ap.add_argument("--pool", type=int, default=12, help="serve mode: distinct problems requests draw from")
     ap.add_argument("--slots", type=int, default=16, help="serve mode: server slots")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per run of the default line's serve object")
+    ap.add_argument("--fp64-max-M", type=int, default=120000,
+                    help="serve mode: pool problems up to this size are also solved in plain FP64 one at a time")
     return ap.parse_args()
 
 
@@ -264,6 +301,7 @@ def run_reference(args, world, rank):
         run_oracle_solves()
         return
     prob, cfg = workload(args.h)
+    cfg = dict(cfg, **solver_config(args, world))
     sample = OracleSample(prob, seconds=max(2.0, min(args.cpu_seconds, 20.0)))
     steps = []
     res = None
@@ -328,29 +366,21 @@ def run_batch(args, ctr):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args, ctr):
-    """Serving: Poisson arrivals at fractions of the measured capacity; latency and throughput."""
+def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, cap_requests=None):
+    """Continuous-batching server over a pool of problems: capacity with every request submitted at once,
+    then Poisson arrivals at each fraction of it; per load solves/s and p50/p99 latency (submission to
+    result).  Served energies are compared with the plain FP64 one-at-a-time GPU path on every pool problem
+    of at most fp64_max_M nodes (the fixed sample), whose rate is reported as fp64_solves_per_s."""
     import threading as th
     import torch
-    import synthetic as syn
-    rng = np.random.Generator(np.random.PCG64(0))
-    n_mol = max(1, args.pool // 3)
-    mol_specs = syn.batch_specs(n_mol, seed=100, max_atoms=min(args.max_atoms, 600))
-    pool = list(syn.molecules_parallel(mol_specs))
-    for k in range(max(1, args.pool // 3)):
-        pool.append(syn.sphere_with_nodes(int(np.exp(rng.uniform(np.log(5e3), np.log(4e5)))),
-                                          q=float(rng.choice([-1.0, 1.0]))))
-    for k, hh in enumerate([0.2, 0.1, 0.05][:max(1, args.pool - len(pool))]):
-        pool.append(syn.ellipsoid_problem(h=hh, seed=k))
-    opts = ctr.Options(precision=ctr.FP32_REFINE, tol=1e-10)
 
-    def run_load(rate, n, seed):
+    def run_load(rate, n, sd):
         arrivals = None
         if rate is not None:
-            gaps = np.random.Generator(np.random.PCG64(seed)).exponential(1.0 / rate, size=n)
+            gaps = np.random.Generator(np.random.PCG64(sd)).exponential(1.0 / rate, size=n)
             arrivals = np.cumsum(gaps) - gaps[0]
-        picks = np.random.Generator(np.random.PCG64(seed + 1)).integers(0, len(pool), size=n)
-        with ctr.Server(max_slots=args.slots) as sv:
+        picks = np.random.Generator(np.random.PCG64(sd + 1)).integers(0, len(pool), size=n)
+        with ctr.Server(max_slots=slots) as sv:
             tickets = [None] * n
             t0 = time.perf_counter()
 
@@ -361,8 +391,8 @@ def run_serve(args, ctr):
                         if dt > 0:
                             time.sleep(dt)
                     p = pool[picks[i]]
-                    tickets[i] = sv.submit_problem(p, ctr.Options(tube_halfwidth=p.tube, precision=opts.precision,
-                                                                  tol=opts.tol))
+                    tickets[i] = sv.submit_problem(p, ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP32_REFINE,
+                                                                  tol=SOLVE_TOL))
 
             thr = th.Thread(target=submitter)
             thr.start()
@@ -372,45 +402,88 @@ def run_serve(args, ctr):
         lat = np.array([r.latency for r in res])
         t_first = min(r.t_submit for r in res)
         t_last = max(r.t_done for r in res)
-        ok = all(r.status == 0 for r in res)
-        return {"solves_per_s": n / (t_last - t_first), "p50_latency_s": float(np.percentile(lat, 50)),
-                "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
-                "all_ok": ok, "peak_slots": st["peak_slots"], "peak_used_GB": st["peak_used_bytes"] / 1e9,
-                "steps": st["steps"], "G": {int(picks[i]): res[i].G_pol for i in range(n)}}
+        return {"requests": n, "solves_per_s": n / (t_last - t_first), "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+                "all_ok": all(r.status == 0 for r in res), "peak_slots": st["peak_slots"],
+                "peak_used_GB": st["peak_used_bytes"] / 1e9, "steps": st["steps"],
+                "energies": [(int(picks[i]), res[i].G_pol) for i in range(n)]}
 
-    warm = run_load(None, min(len(pool), 4), 7)      # warm-up (autotuning, first-touch)
-    cap = run_load(None, args.requests, 11)          # saturated: everything submitted at once
+    run_load(None, min(len(pool), 4), 7)              # warm-up (autotuning, first touch)
+    cap = run_load(None, cap_requests or n_requests, seed)   # saturated: everything submitted at once
     capacity = cap["solves_per_s"]
-    levels = {}
-    for f in [float(v) for v in args.loads.split(",") if v]:
-        levels[str(f)] = run_load(f * capacity, args.requests, 13)
-    # the plain FP64 one-at-a-time GPU path on the same pool (energies for the error check)
-    t0 = time.perf_counter()
-    G64 = {}
+    levels = {f"{f:g}": run_load(f * capacity, n_requests, seed + 2) for f in loads}
+    # the plain FP64 one-at-a-time GPU path on the sample
+    Ms, G64, t64, n64 = [], {}, 0.0, 0
     for k, p in enumerate(pool):
-        with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP64,
-                                                               tol=1e-10)) as G:
-            psi, dpsi, _ = G.solve(device=True)
-            G64[k] = G.energy(psi, dpsi)[0]
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t0
-    errs = [abs(levels[str(f)]["G"][k] / G64[k] - 1) for f in levels for k in levels[str(f)]["G"]]
-    Ms = []
-    for p in pool:
         with ctr.CtrIbim.from_problem(p) as G:
             Ms.append(G.M)
+        if G.M > fp64_max_M:
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP64,
+                                                             tol=SOLVE_TOL)) as G:
+            psi, dpsi, _ = G.solve(device=True)
+            G64[k] = G.energy(psi, dpsi)[0]
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t0
+        n64 += 1
+    errs = [abs(e / G64[k] - 1) for lv in list(levels.values()) + [cap] for k, e in lv["energies"] if k in G64]
     for lv in list(levels.values()) + [cap]:
-        lv.pop("G", None)
-    line = {"metric": "CTR-IBIM served solves/s", "value": levels[max(levels, key=float)]["solves_per_s"],
+        lv.pop("energies")
+    return {"capacity_solves_per_s": capacity, "saturated": cap, "levels": levels,
+            "M_min": int(min(Ms)), "M_max": int(max(Ms)), "pool": len(pool), "slots": slots,
+            "fp64_solves_per_s": n64 / t64 if t64 > 0 else None,
+            "fp64_sample": f"{n64} of the {len(pool)} pool problems (those with M <= {fp64_max_M}), one at a time",
+            "max_energy_err": float(max(errs)) if errs else None, "checked_requests": len(errs)}
+
+
+def c5_pool(n_mol, n_sph, n_ell, max_atoms, seed=0):
+    """Problems of the serving workload: SES molecules of the batched distribution (atoms log-uniform,
+    h in {0.5, 0.35}), spheres of 5k-400k nodes with +-1 charges, ellipsoids at h 0.2 ... 0.035."""
+    import synthetic as syn
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pool = list(syn.molecules_parallel(syn.batch_specs(n_mol, seed=100 + seed, max_atoms=max_atoms))) if n_mol else []
+    for _ in range(n_sph):
+        pool.append(syn.sphere_with_nodes(int(np.exp(rng.uniform(np.log(5e3), np.log(4e5)))),
+                                          q=float(rng.choice([-1.0, 1.0]))))
+    for k, hh in enumerate([0.2, 0.1, 0.05, 0.035][:n_ell]):
+        pool.append(syn.ellipsoid_problem(h=hh, seed=k))
+    return pool
+
+
+def run_serve_bounded(ctr, args):
+    """The serving object of the default line: a pool of six problems of up to ~45k nodes (two molecules,
+    two spheres, two ellipsoids), 48 requests at 0.8 of the measured capacity."""
+    import synthetic as syn
+    rng = np.random.Generator(np.random.PCG64(5))
+    pool = list(syn.molecules_parallel([(60, 201, 0.5), (150, 202, 0.35)]))
+    for M in (6000, 30000):
+        pool.append(syn.sphere_with_nodes(M, q=float(rng.choice([-1.0, 1.0]))))
+    pool += [syn.ellipsoid_problem(h=0.2, seed=1), syn.ellipsoid_problem(h=0.1, seed=2)]
+    out = serve_experiment(ctr, pool, n_requests=args.serve_requests, loads=[0.8], slots=args.slots,
+                           fp64_max_M=10 ** 9)
+    out["workload"] = (f"{args.serve_requests} requests per run drawn from a pool of {len(pool)} problems (SES "
+                       f"molecules of 60 and 150 atoms at h 0.5 / 0.35, spheres of 6k and 30k nodes, ellipsoids at "
+                       f"h 0.2 / 0.1), FP32 pairs + float-float refinement to {SOLVE_TOL:g}; capacity with all "
+                       f"requests submitted at once, then Poisson arrivals at 0.8 of it")
+    return out
+
+
+def run_serve(args, ctr):
+    """Serving workload (C5): Poisson arrivals at fractions of the measured capacity; latency and throughput."""
+    pool = c5_pool(max(1, args.pool // 3), max(1, args.pool // 3), max(1, args.pool - 2 * (args.pool // 3)),
+                   args.max_atoms)
+    out = serve_experiment(ctr, pool, n_requests=args.requests, loads=[float(v) for v in args.loads.split(",") if v],
+                           slots=args.slots, fp64_max_M=args.fp64_max_M, cap_requests=args.capacity_requests)
+    line = {"metric": "CTR-IBIM served solves/s", "value": out["levels"][max(out["levels"], key=float)]["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 pairs + f64",
             "data": "synthetic",
             "config": {"workload": f"{args.requests} requests per load level, Poisson arrivals, drawn from a pool of "
                                    f"{len(pool)} problems (SES molecules, spheres, ellipsoids), FP32 pairs + "
-                                   f"float-float refinement to 1e-10", "M_min": int(min(Ms)), "M_max": int(max(Ms)),
-                       "slots": args.slots},
-            "capacity_solves_per_s": capacity, "saturated": cap, "levels": levels,
-            "fp64_one_at_a_time_solves_per_s": len(pool) / t64,
-            "max_rel_energy_error_vs_fp64_path": float(max(errs)) if errs else None}
+                                   f"float-float refinement to {SOLVE_TOL:g}", "M_min": out["M_min"],
+                       "M_max": out["M_max"], "slots": args.slots}}
+    line.update(out)
     print(json.dumps(line), flush=True)
 
 
@@ -489,9 +562,10 @@ def run_tree(args, ctr, world):
         with ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube), sdist=sd_dev) as D:
             direct = {"fp32_ms": D.time_operator(ctr.FP32_REFINE, reps=1)["pairs_ms"],
                       "df64_ms": D.time_operator(ctr.DF64, reps=1)["pairs_ms"]}
-    rate_ffma = ctypes_probe(ctr, 0)
-    rate_ex2 = ctypes_probe(ctr, 2)
-    rate_rsq = ctypes_probe(ctr, 3)
+    probes = Probes()
+    rate_ffma = probes.rate(0)
+    rate_ex2 = probes.rate(2)
+    rate_rsq = probes.rate(3)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_max = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
     rate_units = sms * 128 * f_max
@@ -577,10 +651,9 @@ def main():
 
     prob, cfg = workload(args.h)
     prec = ctr.FP32_REFINE if args.precision == "fp32_refine" else ctr.FP64
-    opts = ctr.Options(tube_halfwidth=prob.tube, precision=prec, tol=1e-10)
-    cfg["solver"] = f"{args.precision}, GMRES restart {opts.restart}, tol {opts.tol:g}"
-    cfg["l2"] = "256 MiB buffer written between timed steps (L2 flush, outside the step events)"
-    cfg["parallelism"] = f"replicas x{world}"
+    opts = ctr.Options(tube_halfwidth=prob.tube, precision=prec, tol=SOLVE_TOL, restart=RESTART,
+                       inner_tol=INNER_TOL)
+    cfg = dict(cfg, **solver_config(args, world))
     stream = torch.cuda.current_stream()
     sd_dev = torch.tensor(prob.sdist, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
@@ -589,10 +662,10 @@ def main():
         with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
             psi, dpsi, info = G.solve(device=True)
             Gp, _ = G.energy(psi, dpsi)
-            return G.M, info, Gp
+            return G.M, info, Gp, psi, dpsi
 
     for _ in range(args.warmup):
-        M, info, Gp = step()
+        M, info, Gp, _, _ = step()
     torch.cuda.synchronize()
     barrier(world)
     ev = []
@@ -606,7 +679,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            M, info, Gp = step()
+            M, info, Gp, psi, dpsi = step()
             e1.record(stream)
             ev.append((e0, e1))
             infos.append(info)
@@ -619,8 +692,9 @@ def main():
     t_max = max_over_ranks(t_dev, world)
     pairs_all = sum_over_ranks(pairs, world)
     value = pairs_all / t_max
+    steps_all = sum_over_ranks(float(args.steps), world)
 
-    # kernel-level rooflines: FP32 and float-float operator applications, timed on the stream
+    # kernel-level rooflines: one operator application per arithmetic, timed on the stream
     t_mv, sched = {}, {}
     with ctr.CtrIbim.from_problem(prob, options=opts, sdist=sd_dev) as G:
         x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, 2 * G.M), device="cuda")
@@ -638,50 +712,60 @@ def main():
             t_mv[pr] = e0.elapsed_time(e1) * 1e-3 / reps
             sched[pr] = G.pair_schedule(pr)
         Mk = G.M
-    rate_ffma = ctypes_probe(ctr, 0)
-    rate_ex2 = ctypes_probe(ctr, 2)
-    rate_dfma = ctypes_probe(ctr, 4)
+        # accuracy of the timed step's result: the residual recomputed with the float-float operator
+        g = torch.empty(2 * Mk, dtype=torch.float64, device="cuda")
+        ctr.lib.ctr_ibim_rhs(G._h, ctypes.c_void_p(g.data_ptr()), 1)
+        xs = torch.cat([psi, dpsi])
+        r_true = float(torch.linalg.vector_norm(g - G.matvec(xs, ctr.DF64)) / torch.linalg.vector_norm(g))
+    probes = Probes()
+    rate_ffma = probes.rate(0)
+    rate_ex2 = probes.rate(2)
+    rate_dfma = probes.rate(4)
     # FMA-pipe lane operations per second from unit counts and clocks: SMs x 128 FP32 lanes x the SM clock
     # ceiling (sampled by nvidia-smi; 2070 MHz when unavailable).  The FFMA probe's measured rate is reported
     # beside it.
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_max = (clk.summary().get("sm_max_mhz") or 2070.0) * 1e6
     rate_units = sms * 128 * f_max
-
-    def roof(pr, ops, name, key, rate=None):
-        sc = sched[pr]
-        n_ops = ops["one"] * sc["one_sided_pairs"] + ops["sym"] * sc["symmetric_pairs"]
-        peak = (rate or rate_units) * Mk * Mk / n_ops
-        ach = Mk * Mk / t_mv[pr]
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "pair-interactions/s",
-                "frac": ach / peak, "traffic": TRAFFIC_H005[key] if abs(args.h - 0.05) < 1e-12 else None,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz = {rate_units:.4g} lane ops/s "
-                              f"x M^2 / FMA-pipe lane ops of the schedule ({ops['one']} per one-sided and "
-                              f"{ops['sym']} per symmetric pair evaluation); measured FFMA probe {rate_ffma:.4g}/s",
-                "t_matvec_ms": t_mv[pr] * 1e3, "one_sided_pairs": sc["one_sided_pairs"],
-                "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"]}
-
     i_last = infos[-1]
+    step_s = t_max / args.steps
+
+    def roof(pr, ops, name, key, n_app, rate=None, what="FP32"):
+        sc = sched[pr]
+        peak = rate or rate_units
+        alg = ALG_OPS * Mk * Mk / t_mv[pr]
+        n_exec = ops["one"] * sc["one_sided_pairs"] + ops["sym"] * sc["symmetric_pairs"]
+        traffic, tsrc = traffic_for(key, args.h)
+        return {"bound": "alu", "kernel": name, "achieved": alg, "peak": peak,
+                "unit": f"{what}-pipe lane ops/s", "frac": alg / peak, "traffic": traffic,
+                "traffic_source": tsrc,
+                "achieved_basis": f"algorithmic: {ALG_OPS} {what}-pipe lane ops per pair interaction x M^2 = "
+                                  f"{Mk}^2 interactions per launch / the launch's CUDA-event time",
+                "peak_basis": (f"{sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz = {rate_units:.4g} lane ops/s "
+                               f"(unit counts and clocks); measured FFMA probe {rate_ffma:.4g}/s") if rate is None
+                else f"measured DFMA probe {rate:.4g}/s",
+                "pairs_per_s": Mk * Mk / t_mv[pr],
+                "frac_executed": n_exec / t_mv[pr] / peak,
+                "executed_basis": f"lane ops the schedule executes: {ops['one']} per one-sided and {ops['sym']} "
+                                  f"per symmetric pair evaluation (both orientations)",
+                "t_matvec_ms": t_mv[pr] * 1e3, "one_sided_pairs": sc["one_sided_pairs"],
+                "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"],
+                "partial_bytes": sc["partial_bytes"], "applications_per_step": n_app,
+                "step_share": n_app * t_mv[pr] / step_s}
+
     if prec == ctr.FP32_REFINE:
-        r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32x2Policy> (packed FP32 pair sum, inner GMRES)",
-                   "fp32")
+        r32 = roof(ctr.FP32_REFINE, OPS_FP32, "sched_kernel<Fp32x2Policy> (packed FP32 pair sum: inner GMRES and "
+                   "residual updates)", "fp32", i_last.matvecs_fp32)
         rdf = roof(ctr.DF64, OPS_DF64, "sched_kernel<Df64Policy> (float-float pair sum, refinement residual)",
-                   "df64")
-        share32 = i_last.matvecs_fp32 * t_mv[ctr.FP32_REFINE]
-        sharedf = i_last.matvecs_fp64 * t_mv[ctr.DF64]
-        dominant, other = (rdf, r32) if sharedf >= share32 else (r32, rdf)
-        dominant = dict(dominant, ex2_rate=rate_ex2, dfma_rate=rate_dfma,
-                        step_share=max(share32, sharedf) / (t_max / args.steps))
-        other = dict(other, step_share=min(share32, sharedf) / (t_max / args.steps))
+                   "df64", i_last.matvecs_fp64)
+        dominant, other = (rdf, r32) if rdf["step_share"] >= r32["step_share"] else (r32, rdf)
+        dominant = dict(dominant, ex2_rate=rate_ex2, dfma_rate=rate_dfma)
     else:   # plain FP64 solves: every application is the FP64 schedule, bound by the DFMA pipe
-        dominant = roof(ctr.FP64, OPS_FP64, "sched_kernel<Fp64Policy> (FP64 pair sum)", "fp64", rate=rate_dfma)
-        dominant["bound"] = "alu"
-        dominant["peak_basis"] = (f"measured DFMA probe {rate_dfma:.4g}/s x M^2 / FP64-pipe lane ops of the "
-                                  f"schedule ({OPS_FP64['one']} per pair evaluation, ncu count)")
-        dominant = dict(dominant, step_share=i_last.matvecs_fp64 * t_mv[ctr.FP64] / (t_max / args.steps))
+        dominant = roof(ctr.FP64, OPS_FP64, "sched_kernel<Fp64Policy> (FP64 pair sum)", "fp64",
+                        i_last.matvecs_fp64, rate=rate_dfma, what="FP64")
         other = None
 
-    # e2e through the public API with host buffers
+    # the same workload through the public API with host buffers
     e2e = None
     if not args.skip_e2e:
         h2d = prob.sdist.nbytes + prob.charge_xyz.nbytes + prob.charge_q.nbytes
@@ -690,14 +774,24 @@ def main():
         e2e_pairs = 0.0
         for _ in range(max(1, args.steps)):
             with ctr.CtrIbim.from_problem(prob, options=opts) as G:
-                psi, dpsi, info = G.solve(device=False)
-                Gp, _ = G.energy(psi, dpsi)
-                e2e_pairs += float(G.M) ** 2 * (info.matvecs_fp32 + info.matvecs_fp64)
-                d2h = psi.nbytes + dpsi.nbytes + 8
+                psi_h, dpsi_h, info_h = G.solve(device=False)
+                Gh, _ = G.energy(psi_h, dpsi_h)
+                e2e_pairs += float(G.M) ** 2 * (info_h.matvecs_fp32 + info_h.matvecs_fp64)
+                d2h = psi_h.nbytes + dpsi_h.nbytes + 8
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": sum_over_ranks(e2e_pairs, world) / t_e2e, "unit": "pair-interactions/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "solves_per_s": sum_over_ranks(float(max(1, args.steps)), world) / t_e2e}
+
+    # the error of the timed result against the plain FP64 GPU solve of the same system (once, untimed)
+    accuracy = None
+    if rank == 0 and prec == ctr.FP32_REFINE and not args.skip_fp64_check:
+        accuracy = fp64_check(ctr, prob, sd_dev, psi, dpsi, Gp, opts)
+
+    serve = None
+    if rank == 0 and world == 1 and not args.skip_serve:
+        serve = run_serve_bounded(ctr, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -710,9 +804,13 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 pairs + f64" if prec == ctr.FP32_REFINE else "f64", "data": "synthetic",
-            "config": dict(cfg, M=int(M), unknowns=int(2 * M), iterations=int(i0.iterations),
-                           refinements=int(i0.refinements), matvecs_fp32=int(i0.matvecs_fp32),
-                           matvecs_fp64=int(i0.matvecs_fp64), residual=i0.residual, G_pol=Gp),
+            "config": cfg,
+            "solves_per_s": steps_all / t_max,
+            "solve": {"M": int(M), "unknowns": int(2 * M), "iterations": int(i0.iterations),
+                      "refinements": int(i0.refinements), "matvecs_fp32": int(i0.matvecs_fp32),
+                      "matvecs_fp64": int(i0.matvecs_fp64), "residual": i0.residual,
+                      "residual_recomputed_df64": r_true, "G_pol": Gp},
+            "error_vs_fp64": accuracy,
             "roofline": dominant,
             "roofline_second": other,
             "clocks": clk.summary(),
@@ -720,6 +818,7 @@ def main():
             "gpu_launches": int(launches),
             "wall_s": t_wall,
             "cpu_baseline": cpu,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -727,16 +826,59 @@ def main():
         dist.destroy_process_group()
 
 
-def ctypes_probe(ctr, kind, iters=20000):
-    import ctypes
-    L = ctr.lib
-    L.ctr_probe_rate.restype = ctypes.c_int
-    L.ctr_probe_rate.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
-                                 ctypes.POINTER(ctypes.c_double)]
-    r = ctypes.c_double()
-    s = ctypes.c_double()
-    st = L.ctr_probe_rate(kind, iters, ctypes.byref(r), ctypes.byref(s))
-    return float(r.value) if st == 0 else None
+def solver_config(args, world):
+    """The static description of the timed solve (the same keys in both arms of the benchmark)."""
+    if args.precision == "fp32_refine":
+        solver = (f"fp32_refine: FP32 pairs in GMRES(restart {RESTART}, inner tol {INNER_TOL:g}), "
+                  f"refinement to tol {SOLVE_TOL:g}; residual arithmetic float-float, first residual g - A x, "
+                  f"later ones updated r - A d with the FP32 operator")
+        residual = "float-float"
+        mode = "update"
+    else:
+        solver = f"fp64, GMRES restart {RESTART}, tol {SOLVE_TOL:g}"
+        residual = "fp64"
+        mode = "full"
+    return {"solver": solver, "residual": residual, "residual_mode": mode,
+            "l2": "256 MiB buffer written between timed steps (L2 flush, outside the step events)",
+            "parallelism": f"replicas x{world}"}
+
+
+def fp64_check(ctr, prob, sd_dev, psi, dpsi, Gp, opts):
+    """Plain FP64 GPU solve of the same system to the same tolerance; relative errors of the timed result."""
+    import torch
+    t0 = time.perf_counter()
+    with ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP64,
+                                                            tol=opts.tol), sdist=sd_dev) as G:
+        p64, d64, info = G.solve(device=True)
+        G64, _ = G.energy(p64, d64)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+
+    def rel(a, b):
+        return float(torch.max(torch.abs(a - b)) / torch.max(torch.abs(b)))
+
+    return {"reference": f"plain FP64 GPU solve of the same system (CTR_FP64 pairs, GMRES to {opts.tol:g}), once",
+            "G_pol_rel": abs(Gp / G64 - 1), "psi_rel_max": rel(psi, p64), "dpsi_rel_max": rel(dpsi, d64),
+            "G_pol_fp64": G64, "fp64_iterations": int(info.iterations), "fp64_solve_s": t,
+            "fp64_solves_per_s": 1.0 / t}
+
+
+class Probes:
+    """The arithmetic-throughput probes (libctr_probe.so, built beside the solver library): rates of
+    dependent FFMA, f32x2 FMA, ex2, rsqrt and DFMA chains on every SM."""
+
+    def __init__(self):
+        from paper_2210_03699_gb300 import build
+        self.lib = ctypes.CDLL(build.PROBE_LIB)
+        self.lib.ctr_probe_rate.restype = ctypes.c_int
+        self.lib.ctr_probe_rate.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
+
+    def rate(self, kind, iters=20000):
+        r = ctypes.c_double()
+        t = ctypes.c_double()
+        st = self.lib.ctr_probe_rate(kind, iters, ctypes.byref(r), ctypes.byref(t))
+        return float(r.value) if st == 0 else None
 
 
 if __name__ == "__main__":

@@ -48,6 +48,7 @@ extern "C" {
 #define CTR_ERR_NUMERIC (-6)       /* a non-finite value appeared (geometry or solve) */
 #define CTR_ERR_DEVICE_WAIT (-7)   /* a kernel gave up a bounded wait (internal error) */
 #define CTR_ERR_CAPACITY (-8)      /* request larger than a fixed capacity */
+#define CTR_ERR_CANCELLED (-9)     /* a server request was cancelled before it finished */
 
 /*
  * Arithmetic of the dense pair sums (the correction, the diagonal, vectors
@@ -102,6 +103,20 @@ enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
  */
 enum { CTR_FARFIELD_DIRECT = 0, CTR_FARFIELD_TREECODE = 1 };
 
+/*
+ * How a CTR_FP32_REFINE solve forms the residuals of its refinement steps
+ * (x_{k+1} = x_k + d_k, d_k from an FP32-operator GMRES solve of A d = r_k):
+ *   CTR_RESIDUAL_UPDATE  r_1 = g - A x_1 in the residual arithmetic (opt.residual);
+ *       every later r_{k+1} = r_k - A d_k with the FP32-pair operator, once
+ *       |r_k| <= 1e-4 |g| (before that, g - A x again).  A is linear, so this is
+ *       g - A x_{k+1} with the FP32 operator's error (about 1e-7 relative,
+ *       measured) applied to the small correction d_k only: for |r_k| ~ 1e-5 |g|
+ *       the residual is off by about 1e-12 |g|.  One application of the
+ *       FP64-accurate operator per solve instead of one per refinement step.
+ *   CTR_RESIDUAL_FULL    every r_k = g - A x_k in the residual arithmetic.
+ */
+enum { CTR_RESIDUAL_UPDATE = 0, CTR_RESIDUAL_FULL = 1 };
+
 typedef struct {
     int64_t n[3];       /* nodes per axis (nx, ny, nz), each >= 5 */
     double origin[3];   /* coordinates of node (0, 0, 0) */
@@ -128,14 +143,16 @@ typedef struct {
     int tree_degree_fp32;  /* degree of the CTR_FP32_REFINE operator (the inner GMRES, whose own
                               rounding is ~2e-5); <= 0 selects 6 */
     double tree_theta_fp32;/* theta of the CTR_FP32_REFINE operator; <= 0 selects 0.9 */
+    int residual_mode;     /* CTR_RESIDUAL_UPDATE (default) or CTR_RESIDUAL_FULL (see above) */
 } ctr_options;
 
 typedef struct {
     int64_t iterations;    /* GMRES iterations, all cycles and refinements */
     int64_t refinements;   /* refinement steps (FP64-accurate residual evaluations) */
-    int64_t matvecs_fp32;  /* FP32-pair operator applications */
+    int64_t matvecs_fp32;  /* FP32-pair operator applications (GMRES and residual updates) */
     int64_t matvecs_fp64;  /* FP64-accurate (CTR_FP64 or CTR_DF64) operator applications */
-    double residual;       /* final |g - A x| / |g| with the FP64-accurate operator */
+    double residual;       /* final |g - A x| / |g|: with the FP64-accurate operator, or, after a
+                              residual update (CTR_RESIDUAL_UPDATE), the updated residual */
     int converged;         /* 1 when residual <= tol */
 } ctr_solve_info;
 
@@ -162,7 +179,9 @@ void ctr_default_options(ctr_options* opt);
  *   stream     cudaStream_t to run on (NULL: the legacy default stream).
  *   out        receives the handle; set to NULL on failure.
  * Errors: CTR_ERR_INVALID, CTR_ERR_EMPTY_TUBE, CTR_ERR_GRID_MARGIN,
- * CTR_ERR_NUMERIC (non-finite geometry), CTR_ERR_NOMEM, CTR_ERR_CUDA.
+ * CTR_ERR_NUMERIC (a non-finite signed-distance value anywhere in the grid, a
+ * non-finite charge position or value, or non-finite geometry), CTR_ERR_NOMEM,
+ * CTR_ERR_CUDA.
  */
 int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_device,
                    double eps_in, double eps_out, double kappa,
@@ -215,7 +234,10 @@ int ctr_ibim_area(const ctr_ibim* sys, double* area);
  * its one-sided items evaluate (the near band, correction pairs masked), how
  * many its symmetric items evaluate once for both orientations (each counts
  * once here and stands for two of the M^2 - |N| interactions), its work items
- * and the bytes of its partial-sum regions.  Any output may be NULL.
+ * and the bytes of the device buffer its items add their sums into (exact
+ * per-node accumulators, 200 bytes per node, shared by the three
+ * arithmetics; the sums do not depend on the order of the additions).  Any
+ * output may be NULL.
  */
 int ctr_ibim_pair_schedule(const ctr_ibim* sys, int precision, int64_t* one_sided_pairs,
                            int64_t* symmetric_pairs, int64_t* items, int64_t* partial_bytes);
@@ -260,6 +282,9 @@ int ctr_ibim_time_operator(ctr_ibim* sys, int precision, int reps, double* pack_
  * nb = ceil(M / block)), near_rng (2 per range: [begin, end) tree positions),
  * far_ptr (nb + 1), far_begin and far_end (n_far each: the position range of
  * each far cluster).  Call with the array outputs NULL to learn the sizes.
+ * CTR_ERR_INVALID, before anything is built, when an index lies outside
+ * (-2^30, 2^30), excl_ptr[0] != 0, excl_ptr decreases, or an excluded node
+ * lies outside [0, M).
  */
 int ctr_farfield_plan(int64_t M, const int32_t* ijk, const int32_t* excl_ptr, const int32_t* excl, int margin,
                       int degree, double theta, int leaf, int block, int64_t min_far, int64_t* perm,
@@ -355,6 +380,16 @@ int ctr_server_fetch(ctr_server* sv, uint64_t ticket, double* psi, double* dpsi_
 /* Forgets a finished request and its stored result. */
 int ctr_server_release(ctr_server* sv, uint64_t ticket);
 int ctr_server_stats(ctr_server* sv, ctr_server_stats_t* out);
+/*
+ * Cancels a request that has not finished: a queued one leaves the queue, one
+ * in setup is dropped when its setup ends, a running one leaves its engine
+ * slot between two engine steps (the other systems go on unaffected).  The
+ * request then finishes with status CTR_ERR_CANCELLED and no result (wait,
+ * poll and release work as for any finished request).  Returns
+ * CTR_ERR_INVALID for an unknown ticket or a request that has already
+ * finished.
+ */
+int ctr_server_cancel(ctr_server* sv, uint64_t ticket);
 /* Stops the server's threads (waiting requests are dropped) and frees everything. */
 void ctr_server_destroy(ctr_server* sv);
 
@@ -368,11 +403,36 @@ int ctr_ibim_energy(ctr_ibim* sys, const double* psi, const double* dpsi_n, int 
                     double* G_pol, double* psi_rxn);
 
 /*
- * psi_rxn of Eq. (2.31) at arbitrary points z (away from the surface):
- * n_points points, xyz 3*n_points doubles (host), out n_points doubles (host).
+ * psi_rxn of Eq. (2.31) at arbitrary points z (away from the surface), in
+ * FP64: n_points points, xyz 3*n_points doubles (host), out n_points doubles
+ * (host); psi, dpsi_n host or device (on_device).  The same tiled kernel as
+ * ctr_ibim_potential_map with precision CTR_FP64.
  */
 int ctr_ibim_reaction_potential(ctr_ibim* sys, const double* psi, const double* dpsi_n, int on_device,
                                 int64_t n_points, const double* xyz, double* out);
+
+/*
+ * Potential map: psi_rxn of Eq. (2.31) (the trapezoidal rule on the tube,
+ * valid at points away from the surface) at n_points arbitrary points, as a
+ * tiled pair sum of the points against the M tube nodes.
+ *   psi, dpsi_n  M doubles each (a solution of ctr_ibim_solve).
+ *   xyz          3*n_points doubles (x, y, z per point).
+ *   out          n_points doubles.
+ *   precision    CTR_FP32_REFINE: FP32 pair terms, two points per f32x2
+ *                instruction, per-tile sums added in FP64 (about 1e-7
+ *                relative); CTR_DF64: float-float terms (about 1e-13);
+ *                CTR_FP64: IEEE FP64.
+ *   on_device    0: every array is host memory; 1: every array is device
+ *                memory of the handle's device.
+ * The split partial sums (and, for host arrays, device copies of the
+ * arguments) live in buffers the handle keeps: a call allocates only when it
+ * needs more than an earlier call did.  The handle's packed source weights
+ * are overwritten (as by ctr_ibim_matvec).  Errors: CTR_ERR_INVALID,
+ * CTR_ERR_CAPACITY (n_points >= 2^31), CTR_ERR_NOMEM, CTR_ERR_CUDA,
+ * CTR_ERR_DEVICE_WAIT.
+ */
+int ctr_ibim_potential_map(ctr_ibim* sys, const double* psi, const double* dpsi_n, int64_t n_points,
+                           const double* xyz, double* out, int precision, int on_device);
 
 /*
  * The correction-weight tables of Sec. 2.4.2 as this library computes them
@@ -417,6 +477,18 @@ int ctr_weight_tables(double* out);
 #define CTR_STATIC_SCRATCH_NODES 1048576
 int ctr_pair_sum_fp32_static(int64_t M, const float* src, const int32_t* row_ptr, const int32_t* excluded,
                              double eps_ratio, double kappa, double* out, void* stream);
+
+/*
+ * Diagnostic: the number of polls after which the pair kernels give up
+ * waiting for a source tile's bulk copy (default 2^22; polls < 0 restores
+ * it).  On giving up, a block sets the handle's error word, lets the copies
+ * it has in flight land, and returns; the call then fails with
+ * CTR_ERR_DEVICE_WAIT and its outputs are not usable, while the device and
+ * the handle stay usable.  A limit of 0 makes every wait give up at once,
+ * which exercises that path without any fault.  Applies to the operator
+ * applications and solves that start after the call, in every thread.
+ */
+int ctr_set_wait_limit(int64_t polls);
 
 /* Status code -> short description (static string). */
 const char* ctr_status_string(int status);

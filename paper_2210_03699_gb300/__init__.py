@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Options", "SolveInfo", "CtrIbim", "CtrError", "weight_tables", "kernel_launches", "batch_solve",
-           "Server", "RequestResult",
+           "Server", "RequestResult", "set_wait_limit",
            "library_path", "lib",
            "FP64", "FP32_REFINE", "DF64", "METHOD_HYB", "METHOD_KREG"]
 
@@ -30,6 +30,10 @@ METHOD_HYB = 0
 METHOD_KREG = 1
 FARFIELD_DIRECT = 0
 FARFIELD_TREECODE = 1
+RESIDUAL_UPDATE = 0
+RESIDUAL_FULL = 1
+ERR_DEVICE_WAIT = -7
+ERR_CANCELLED = -9
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -51,7 +55,7 @@ class _Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int),
                 ("method", ctypes.c_int), ("farfield", ctypes.c_int), ("tree_degree", ctypes.c_int),
                 ("tree_theta", ctypes.c_double), ("tree_leaf", ctypes.c_int), ("tree_degree_fp32", ctypes.c_int),
-                ("tree_theta_fp32", ctypes.c_double)]
+                ("tree_theta_fp32", ctypes.c_double), ("residual_mode", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -93,12 +97,13 @@ class Options:
     tree_leaf: int = 128
     tree_degree_fp32: int = 6
     tree_theta_fp32: float = 0.9
+    residual_mode: int = RESIDUAL_UPDATE
 
     def _c(self) -> _Options:
         return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
                         self.max_refine, self.inner_tol, self.tile_targets, self.residual, self.method,
                         self.farfield, self.tree_degree, self.tree_theta, self.tree_leaf, self.tree_degree_fp32,
-                        self.tree_theta_fp32)
+                        self.tree_theta_fp32, self.residual_mode)
 
 
 @dataclasses.dataclass
@@ -142,6 +147,7 @@ def _load():
                                                 ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(_Info)]),
         "ctr_ibim_energy": (ctypes.c_int, [P, P, P, ctypes.c_int, _D, P]),
         "ctr_ibim_reaction_potential": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int64, P, P]),
+        "ctr_ibim_potential_map": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]),
         "ctr_weight_tables": (ctypes.c_int, [P]),
         "ctr_default_server_options": (None, [ctypes.POINTER(_ServerOptions)]),
         "ctr_server_create": (ctypes.c_int, [ctypes.POINTER(_ServerOptions), ctypes.POINTER(P)]),
@@ -155,6 +161,8 @@ def _load():
         "ctr_server_release": (ctypes.c_int, [P, ctypes.c_uint64]),
         "ctr_server_stats": (ctypes.c_int, [P, ctypes.POINTER(_ServerStats)]),
         "ctr_server_destroy": (None, [P]),
+        "ctr_server_cancel": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "ctr_set_wait_limit": (ctypes.c_int, [ctypes.c_int64]),
         "ctr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "ctr_last_error": (ctypes.c_char_p, []),
         "ctr_kernel_launches": (ctypes.c_int64, []),
@@ -383,6 +391,29 @@ class CtrIbim:
                                                out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def potential_map(self, psi, dpsi, points, precision: int = FP32_REFINE):
+        """psi_rxn (Eq. 2.31) at many points (see ctr_ibim_potential_map).  Host arrays in, host array out;
+        with psi, dpsi and points all CUDA tensors the work stays on the device and a tensor is returned."""
+        if _is_torch(points):
+            import torch
+            n = points.numel() // 3
+            pts, _ = _dptr(points, 3 * n)
+            p, d1 = _dptr(psi, self.M)
+            d, d2 = _dptr(dpsi, self.M)
+            if not (d1 and d2):
+                raise ValueError("with device points, psi and dpsi must be device tensors too")
+            out = torch.empty(n, dtype=torch.float64, device=points.device)
+            _check(lib.ctr_ibim_potential_map(self._h, p, d, n, pts, ctypes.c_void_p(out.data_ptr()),
+                                              int(precision), 1))
+            return out
+        p = np.ascontiguousarray(psi, dtype=np.float64)
+        d = np.ascontiguousarray(dpsi, dtype=np.float64)
+        z = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        out = np.empty(z.shape[0])
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _check(lib.ctr_ibim_potential_map(self._h, vp(p), vp(d), z.shape[0], vp(z), vp(out), int(precision), 0))
+        return out
+
 
 @dataclasses.dataclass
 class RequestResult:
@@ -454,6 +485,10 @@ class Server:
 
     def release(self, ticket: int):
         _check(lib.ctr_server_release(self._h, ticket))
+
+    def cancel(self, ticket: int):
+        """Cancel a request that has not finished (see ctr_server_cancel)."""
+        _check(lib.ctr_server_cancel(self._h, ticket))
 
     def stats(self) -> dict:
         st = _ServerStats()
@@ -550,6 +585,11 @@ def farfield_plan(ijk, excl_ptr, excl, margin: int, degree: int = 10, theta: flo
     return {"perm": perm, "near_ptr": near_ptr, "near_rng": rng, "far_ptr": far_ptr, "far_begin": fb[:n_far.value],
             "far_end": fe[:n_far.value], "near_pairs": int(np.sum(nt * near_per_block)),
             "far_evaluations": int(np.sum(nt * far_per_block)) * (degree + 1) ** 3}
+
+
+def set_wait_limit(polls: int):
+    """Polls of the pair kernels' bounded waits (< 0: the default); see ctr_set_wait_limit."""
+    _check(lib.ctr_set_wait_limit(int(polls)))
 
 
 def kernel_launches() -> int:

@@ -1,4 +1,5 @@
-"""In-tree build of libctr_ibim.so for sm_103a (nvcc, one -gencode, parallel objects).
+"""In-tree build of libctr_ibim.so for sm_103a (nvcc, one -gencode, parallel objects), and of the
+benchmark's arithmetic-throughput probes as a library of their own (libctr_probe.so).
 
     python -m paper_2210_03699_gb300.build [--force]
 """
@@ -14,6 +15,8 @@ ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libctr_ibim.so")
+PROBE_DIR = os.path.join(HERE, "probe")
+PROBE_LIB = os.path.join(OUT_DIR, "libctr_probe.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -36,11 +39,18 @@ def _deps():
     return files
 
 
+def _probe_deps():
+    return [os.path.join(PROBE_DIR, f) for f in os.listdir(PROBE_DIR) if f.endswith((".cu", ".h"))]
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    for lib, deps in ((LIB, _deps()), (PROBE_LIB, _probe_deps())):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not all(os.path.getmtime(f) <= t for f in deps):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
@@ -62,8 +72,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout + r.stderr, flush=True)
         return obj
 
+    def probe_lib():
+        tmp = PROBE_LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+               os.path.join(PROBE_DIR, "probe.cu"), "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on the probes:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PROBE_LIB)
+
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        probe = ex.submit(probe_lib)
         objs = list(ex.map(compile_one, sources()))
+        probe.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -81,6 +81,7 @@ void ctr_default_options(ctr_options* o) {
     o->tree_leaf = 128;
     o->tree_degree_fp32 = 6;
     o->tree_theta_fp32 = 0.9;
+    o->residual_mode = CTR_RESIDUAL_UPDATE;
 }
 
 const char* ctr_status_string(int st) {
@@ -95,6 +96,7 @@ const char* ctr_status_string(int st) {
         case CTR_ERR_NUMERIC: return "non-finite value";
         case CTR_ERR_DEVICE_WAIT: return "bounded device wait expired";
         case CTR_ERR_CAPACITY: return "capacity exceeded";
+        case CTR_ERR_CANCELLED: return "cancelled";
         default: return "unknown status";
     }
 }
@@ -134,6 +136,10 @@ int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_devic
             return fail(CTR_ERR_INVALID, "eps_in, eps_out must be > 0 and kappa >= 0");
         if (n_charges < 0 || (n_charges > 0 && (!charge_xyz || !charge_q)))
             return fail(CTR_ERR_INVALID, "bad charges");
+        for (int64_t c = 0; c < n_charges; ++c)
+            if (!std::isfinite(charge_xyz[3 * c]) || !std::isfinite(charge_xyz[3 * c + 1]) ||
+                !std::isfinite(charge_xyz[3 * c + 2]) || !std::isfinite(charge_q[c]))
+                return fail(CTR_ERR_NUMERIC, "non-finite charge position or value");
         ctr_options o;
         ctr_default_options(&o);
         if (opt) {
@@ -147,6 +153,8 @@ int ctr_ibim_setup(const ctr_grid* grid, const double* sdist, int sdist_on_devic
                 return fail(CTR_ERR_INVALID, "unknown precision");
             if (o.residual != CTR_FP64 && o.residual != CTR_DF64)
                 return fail(CTR_ERR_INVALID, "residual must be CTR_FP64 or CTR_DF64");
+            if (o.residual_mode != CTR_RESIDUAL_UPDATE && o.residual_mode != CTR_RESIDUAL_FULL)
+                return fail(CTR_ERR_INVALID, "residual_mode must be CTR_RESIDUAL_UPDATE or CTR_RESIDUAL_FULL");
             if (o.method != CTR_METHOD_HYB && o.method != CTR_METHOD_KREG)
                 return fail(CTR_ERR_INVALID, "method must be CTR_METHOD_HYB or CTR_METHOD_KREG");
             if (o.farfield != CTR_FARFIELD_DIRECT && o.farfield != CTR_FARFIELD_TREECODE)
@@ -313,7 +321,7 @@ int ctr_ibim_pair_schedule(const ctr_ibim* s, int precision, int64_t* one_sided,
     if (one_sided) *one_sided = p.pairs_one;
     if (symmetric) *symmetric = p.pairs_sym;
     if (items) *items = (int64_t)p.items.size();
-    if (partial_bytes) *partial_bytes = p.part_doubles * (int64_t)sizeof(double);
+    if (partial_bytes) *partial_bytes = (int64_t)s->acc.bytes;
     return CTR_OK;
 }
 
@@ -453,16 +461,55 @@ int ctr_ibim_reaction_potential(ctr_ibim* s, const double* psi, const double* dp
     return guarded([&]() -> int {
         CTR_TRY(use_device(s));
         if (n_points == 0) return CTR_OK;
-        DevBuf p1, p2, z, o;
-        const double *dp = nullptr, *dd = nullptr, *dz = nullptr;
-        CTR_TRY(copy_in(psi, on_device, s->M, p1, &dp, s->stream));
-        CTR_TRY(copy_in(dpsi_n, on_device, s->M, p2, &dd, s->stream));
-        CTR_TRY(copy_in(xyz, 0, 3 * n_points, z, &dz, s->stream));
-        CTR_TRY(o.alloc(sizeof(double) * n_points));
-        CTR_TRY(reaction_potential(s, dp, dd, n_points, dz, o.as<double>()));
-        CTR_CUDA_TRY(cudaMemcpyAsync(out, o.p, sizeof(double) * n_points, cudaMemcpyDeviceToHost, s->stream));
+        // psi and dpsi where the caller has them; points and results staged in the handle's buffers
+        const int64_t M = s->M;
+        const int64_t need = (on_device ? 0 : 2 * M) + 4 * n_points;
+        CTR_TRY(s->map_io.alloc(sizeof(double) * (size_t)need));
+        double* io = s->map_io.as<double>();
+        const double* dp = psi;
+        const double* dd = dpsi_n;
+        if (!on_device) {
+            CTR_CUDA_TRY(cudaMemcpyAsync(io, psi, sizeof(double) * M, cudaMemcpyHostToDevice, s->stream));
+            CTR_CUDA_TRY(cudaMemcpyAsync(io + M, dpsi_n, sizeof(double) * M, cudaMemcpyHostToDevice, s->stream));
+            dp = io;
+            dd = io + M;
+            io += 2 * M;
+        }
+        CTR_CUDA_TRY(cudaMemcpyAsync(io, xyz, sizeof(double) * 3 * n_points, cudaMemcpyHostToDevice, s->stream));
+        CTR_TRY(potential_map(s, dp, dd, n_points, io, io + 3 * n_points, CTR_FP64));
+        CTR_CUDA_TRY(cudaMemcpyAsync(out, io + 3 * n_points, sizeof(double) * n_points, cudaMemcpyDeviceToHost,
+                                     s->stream));
         CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
-        return CTR_OK;
+        return check_device_error(s, "reaction potential");
+    });
+}
+
+int ctr_ibim_potential_map(ctr_ibim* s, const double* psi, const double* dpsi_n, int64_t n_points, const double* xyz,
+                           double* out, int precision, int on_device) {
+    if (!s || !psi || !dpsi_n || n_points < 0 || (n_points > 0 && (!xyz || !out)))
+        return fail(CTR_ERR_INVALID, "NULL argument");
+    if (precision != CTR_FP64 && precision != CTR_FP32_REFINE && precision != CTR_DF64)
+        return fail(CTR_ERR_INVALID, "unknown precision");
+    return guarded([&]() -> int {
+        CTR_TRY(use_device(s));
+        if (n_points == 0) return CTR_OK;
+        if (on_device) {
+            CTR_TRY(potential_map(s, psi, dpsi_n, n_points, xyz, out, precision));
+            CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+            return check_device_error(s, "potential map");
+        }
+        const int64_t M = s->M;
+        CTR_TRY(s->map_io.alloc(sizeof(double) * (size_t)(2 * M + 4 * n_points)));
+        double* io = s->map_io.as<double>();
+        CTR_CUDA_TRY(cudaMemcpyAsync(io, psi, sizeof(double) * M, cudaMemcpyHostToDevice, s->stream));
+        CTR_CUDA_TRY(cudaMemcpyAsync(io + M, dpsi_n, sizeof(double) * M, cudaMemcpyHostToDevice, s->stream));
+        CTR_CUDA_TRY(cudaMemcpyAsync(io + 2 * M, xyz, sizeof(double) * 3 * n_points, cudaMemcpyHostToDevice,
+                                     s->stream));
+        double* d_out = io + 2 * M + 3 * n_points;
+        CTR_TRY(potential_map(s, io, io + M, n_points, io + 2 * M, d_out, precision));
+        CTR_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(double) * n_points, cudaMemcpyDeviceToHost, s->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return check_device_error(s, "potential map");
     });
 }
 

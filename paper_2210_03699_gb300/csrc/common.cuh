@@ -111,43 +111,33 @@ struct PairPlan {
 // A work item of a pair schedule: target block I (BS consecutive nodes) against
 // sources [j_begin, j_end); one-sided (sym = 0: correction pairs masked) or
 // symmetric (sym = 1: both orientations of every pair, no correction pair in
-// the item).  Target sums: 2 * BS doubles at ibase of the partial buffer;
-// source sums of a symmetric item: 2 * (j_end - j_begin) doubles at jbase.
+// the item).  Its target sums (and a symmetric item's source sums) are added
+// into the handle's exact per-node accumulators.
 struct PairItem {
     int32_t I, j_begin, j_end, sym;
-    int64_t ibase, jbase;
-};
-// One partial region as seen by the nodes of a block: node i reads
-// buf[base + c * len + (i - origin)] when 0 <= i - origin < len.
-struct PairRec {
-    int64_t base;
-    int32_t len, origin;
 };
 
 // The pair schedule of one system for one pair arithmetic: items (device list
-// sorted by decreasing cost; host copy and costs kept for the engine) and, per
-// target block, the regions its nodes sum in a fixed order.
+// sorted by decreasing cost; host copy and costs kept for the engine).
 struct PairSchedule {
     int R = 1;            // targets per thread
     int BS = 256;         // nodes per target block
     int tile = 128;       // sources per shared-memory tile
     int nb = 0;           // target blocks
-    int64_t part_doubles = 0;
     int64_t pairs_sym = 0, pairs_one = 0;   // evaluated pair orientations of each kind
     std::vector<PairItem> items;   // in the order of d_items (decreasing cost)
     std::vector<double> cost;
-    DevBuf d_items, d_rptr, d_recs;
+    DevBuf d_items;
 };
 
 // ---------------------------------------------------------------- far field (treecode)
 constexpr int kTreeMaxN1 = 13;                                        // degree <= 12
 constexpr int kTreeMaxNp = kTreeMaxN1 * kTreeMaxN1 * kTreeMaxN1;
 
-// Far item: target block I against the far clusters flist[l0 .. l1); sums to the
-// partial region at ibase (2 x BS doubles, like a one-sided pair item).
+// Far item: target block I against the far clusters flist[l0 .. l1); its sums are
+// added into the nodes' exact accumulators (like a one-sided pair item's).
 struct FarItem {
     int32_t I, l0, l1, pad;
-    int64_t ibase;
 };
 // Moment chunk: the tree positions [j0, j1) of far cluster q (compact index).
 struct MomChunk {
@@ -175,7 +165,7 @@ struct TreeView {
     const float4* src32 = nullptr;        // the handle's packed sources, tree order
     const float4* srcdf = nullptr;
     const double4* src64 = nullptr;
-    double* part = nullptr;               // partial regions (shared with the pair items)
+    unsigned long long* acc = nullptr;    // exact node accumulators (shared with the pair items)
     int BS[3] = {};
     double c1 = 1.0, c2 = 1.0, kappa = 0.0;
 };
@@ -242,7 +232,9 @@ struct ctr_ibim {
     ctr::DevBuf excl;        // int32 [E] sorted correction nodes per target
     ctr::DevBuf rhs;         // double [2M]
     ctr::DevBuf charges;     // double [4][nc]: x, y, z, q
-    ctr::DevBuf partial;     // double scratch of the pair kernels
+    ctr::DevBuf acc;         // exact accumulators of the dense sum: pk::kFxWords x M 64-bit words
+    ctr::DevBuf map_ws;      // double split partials of the potential-map kernels (grown on demand)
+    ctr::DevBuf map_io;      // device staging of host arguments of the potential maps (grown on demand)
     ctr::DevBuf err;         // int device error word
     ctr::DevBuf vecs;        // double [6][2M] solver vectors
     ctr::DevBuf red;         // reduction scratch
@@ -270,12 +262,15 @@ int launch_tree(ctr_ibim* s, int pol);
 int64_t tree_bytes(const ctr_ibim* s);
 // schedule.cu: symmetric / one-sided pair schedules of a handle
 int build_schedules(ctr_ibim* s, const int slots[3]);
+// the handle's exact node accumulators, allocated and cleared (pairsum.cu)
+int alloc_accumulators(ctr_ibim* s);
 int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision);
 int apply_operator_timed(ctr_ibim* s, const double* d_x, double* d_y, int precision, cudaEvent_t* ev);
 // krylov.cu: solver workspace
-// energy.cu
-int reaction_potential(ctr_ibim* s, const double* d_psi, const double* d_dpsi, int64_t npts,
-                       const double* d_xyz, double* d_out);
+// potential.cu: psi_rxn of Eq. (2.31) at n points in pair arithmetic `precision` (CTR_FP32_REFINE,
+// CTR_DF64 or CTR_FP64), all pointers device memory; enqueued on the handle's stream
+int potential_map(ctr_ibim* s, const double* d_psi, const double* d_dpsi, int64_t n, const double* d_xyz,
+                  double* d_out, int precision);
 // reductions (krylov.cu)
 int device_dot(ctr_ibim* s, const double* a, const double* b, int64_t n, double* h_out);
 int check_device_error(ctr_ibim* s, const char* where);

@@ -39,6 +39,7 @@ using namespace pk;
 namespace {
 
 constexpr int kVecThreads = 256;
+constexpr double kUpdateGate = 1e-4;   // |r| / |g| below which refinement residuals are updated
 
 __device__ __forceinline__ double block_sum_d(double v) {
     __shared__ double sh[kVecThreads / 32];
@@ -54,6 +55,9 @@ __device__ __forceinline__ double block_sum_d(double v) {
 
 __device__ __forceinline__ bool inner_active(const SlotDev& s) { return s.stat.state == kSlotInner; }
 __device__ __forceinline__ bool update_active(const SlotDev& s) { return s.stat.state == kSlotUpdate; }
+// Pair arithmetic of a slot's residual in this cycle: the residual arithmetic for g - A x, the inner
+// one for an update r - A d of a small correction d.
+__device__ __forceinline__ int res_arith(const SlotDev& s) { return s.upd ? s.inner_prec : s.res_prec; }
 
 // ---------------------------------------------------------------- packing
 __device__ __forceinline__ void pack_weights(const SlotDev& s, int prec, int64_t t, double a, double b) {
@@ -86,7 +90,8 @@ __global__ void k_prep_inner(SlotDev* S) {
     }
 }
 
-// update: x += Lambda^-1 V y (k columns) and the weights of x
+// update: d = Lambda^-1 V y (k columns), x += d, and the weights of x (residual g - A x) or, for a
+// residual update, d kept in z and its weights in the inner arithmetic (residual r - A d)
 __global__ void k_update_x(SlotDev* S) {
     const SlotDev& s = S[blockIdx.y];
     if (!update_active(s)) return;
@@ -98,10 +103,18 @@ __global__ void k_update_x(SlotDev* S) {
             v1 += s.V[(size_t)i * n + t] * s.y[i];
             v2 += s.V[(size_t)i * n + M + t] * s.y[i];
         }
-        const double x1 = s.x[t] + v1 * s.il1, x2 = s.x[M + t] + v2 * s.il2;
+        const double d1 = v1 * s.il1, d2 = v2 * s.il2;
+        const double x1 = s.x[t] + d1, x2 = s.x[M + t] + d2;
         s.x[t] = x1;
         s.x[M + t] = x2;
-        pack_weights(s, s.res_prec, s.tinv ? (int64_t)s.tinv[t] : t, s.scale * s.W[t] * x1, s.scale * s.W[t] * x2);
+        const int64_t pos = s.tinv ? (int64_t)s.tinv[t] : t;
+        if (s.upd) {
+            s.z[t] = d1;
+            s.z[M + t] = d2;
+            pack_weights(s, s.inner_prec, pos, s.scale * s.W[t] * d1, s.scale * s.W[t] * d2);
+        } else {
+            pack_weights(s, s.res_prec, pos, s.scale * s.W[t] * x1, s.scale * s.W[t] * x2);
+        }
     }
 }
 
@@ -134,13 +147,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
         const int2 w = items[it];   // slot, item
         const SlotDev& s = S[w.x];
         const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec)
-                                    : (update_active(s) && s.res_prec == prec);
+                                    : (update_active(s) && res_arith(s) == prec);
         if (!want) continue;
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
         if constexpr (kShared) {
-            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.part, pkc, err, sm.ring,
+            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.acc, pkc, err, sm.ring,
                                            sm.jred, sm.tab, bar, gt))
                 return;
         } else {
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
             }
             __syncthreads();
             const PairConsts k = kc;   // block-uniform register copy: no shared loads in the pair loops
-            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.part, k, err, sm.ring,
+            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.acc, k, err, sm.ring,
                                            sm.jred, sm.tab, bar, gt))
                 return;
         }
@@ -159,19 +172,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
     }
 }
 
-// finish: diag + fixed-order sum of the schedule's partial regions + correction of the applied vector;
-// inner: w = V_{j+1} = A z;   update: r = g - A x
+// finish: diag + the node's accumulated dense sum (read and cleared) + correction of the applied vector;
+// inner: w = V_{j+1} = A z;   update: r = g - A x, or r = r - A d (residual update, d in z)
 __global__ void k_finish(SlotDev* S, int half) {
     const SlotDev& s = S[blockIdx.y];
     if (half == 0 ? !inner_active(s) : !update_active(s)) return;
     const int64_t M = s.M, E = s.E;
-    const double* x = (half == 0) ? s.z : s.x;
-    const int prec = (half == 0) ? s.inner_prec : s.res_prec;
-    const int pol = (prec == CTR_FP32_REFINE) ? 0 : (prec == CTR_DF64 ? 1 : 2);
+    const bool upd = (half == 1) && s.upd;
+    const double* x = (half == 0 || upd) ? s.z : s.x;
     double* out = (half == 0) ? s.V + (size_t)(s.j + 1) * s.n : s.r;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        double s1 = 0.0, s2 = 0.0;
-        gather_partials(s.recs[pol], s.rptr[pol], s.BS[pol], s.part, s.tinv ? (int64_t)s.tinv[i] : i, s1, s2);
+        double s1, s2;
+        fx_read(s.acc + (s.tinv ? (int64_t)s.tinv[i] : i), M, true, s1, s2);
         double c1 = 0.0, c2 = 0.0;
         for (int e = s.cptr[i]; e < s.cptr[i + 1]; ++e) {
             const int m = s.cnode[e];
@@ -184,6 +196,9 @@ __global__ void k_finish(SlotDev* S, int half) {
         if (half == 0) {
             out[i] = y1;
             out[M + i] = y2;
+        } else if (upd) {   // out is r: each thread updates its own two entries
+            out[i] -= y1;
+            out[M + i] -= y2;
         } else {
             out[i] = s.g[i] - y1;
             out[M + i] = s.g[M + i] - y2;
@@ -316,7 +331,7 @@ __global__ void k_decide(SlotDev* S, int cap) {
     if (q >= cap) return;
     SlotDev& s = S[q];
     if (!update_active(s)) return;
-    s.stat.matvecs_fp64++;
+    if (s.upd) s.stat.matvecs_fp32++; else s.stat.matvecs_fp64++;
     s.stat.refinements++;
     const double rn = sqrt(s.scal[1]);
     s.stat.residual = (s.gnorm > 0.0) ? rn / s.gnorm : 0.0;
@@ -334,6 +349,10 @@ __global__ void k_decide(SlotDev* S, int cap) {
     }
     s.beta = rn;
     s.tol_cycle = s.refine ? s.inner_tol * rn : s.tol_out * s.gnorm;
+    // The next residual may be updated as r - A d in the inner arithmetic once r is small: the inner
+    // operator's error on d (about 1e-7 |A| |d|, |d| ~ |A^-1| |r|) then stays orders of magnitude
+    // below the tolerance, while g - A x would need the residual arithmetic at full magnitude.
+    s.upd = (s.refine && s.res_update && rn <= kUpdateGate * s.gnorm) ? 1 : 0;
     s.stat.state = kSlotStart;
 }
 
@@ -398,7 +417,7 @@ struct EngineTreeAcc {
     int half, prec;
     __device__ const TreeView* view(int q) const {
         const SlotDev& s = S[q];
-        const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec) : (update_active(s) && s.res_prec == prec);
+        const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec) : (update_active(s) && res_arith(s) == prec);
         return (want && s.tv.on) ? &s.tv : nullptr;
     }
 };
@@ -748,7 +767,7 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     d.src32 = s->src32.as<float4>();
     d.src64 = s->src64.as<double4>();
     d.srcdf = s->srcdf.as<float4>();
-    d.part = s->partial.as<double>();
+    d.acc = s->acc.as<unsigned long long>();
     d.g = s->rhs.as<double>();
     d.lam1 = 0.5 * (1.0 + s->eps_out / s->eps_in);
     d.lam2 = 0.5 * (1.0 + s->eps_in / s->eps_out);
@@ -760,11 +779,11 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     d.refine = (s->opt.precision == CTR_FP32_REFINE) ? 1 : 0;
     d.inner_prec = s->opt.precision;
     d.res_prec = d.refine ? s->opt.residual : s->opt.precision;
+    d.res_update = (d.refine && s->opt.residual_mode == CTR_RESIDUAL_UPDATE) ? 1 : 0;
+    d.upd = 0;
     CTR_TRY(pair_consts(s, true, &d.kc));
     for (int p = 0; p < 3; ++p) {
         d.items[p] = s->sched[p].d_items.as<PairItem>();
-        d.recs[p] = s->sched[p].d_recs.as<PairRec>();
-        d.rptr[p] = s->sched[p].d_rptr.as<int32_t>();
         d.BS[p] = s->sched[p].BS;
     }
     double* b = s->vecs.as<double>();
@@ -906,6 +925,9 @@ static int engine_autotune(Engine* e) {
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    // the timed launches added into the slots' accumulators with no finish after them: clear them
+    for (int q = 0; q < e->cap; ++q)
+        if (e->owner[q]) CTR_CUDA_TRY(cudaMemsetAsync(e->owner[q]->acc.p, 0, e->owner[q]->acc.bytes, e->stream));
     e->var32 = best;
     e->graph_dirty = true;
     g_last_var = best;

@@ -28,6 +28,8 @@ struct SlotDev {
     int M, E, nblk;
     int64_t n;
     int refine, inner_prec, res_prec, max_refine;
+    int res_update;          // refinement residuals after the first: r -= A d in the inner arithmetic
+    int upd;                 // this cycle's residual is such an update (d = the cycle's correction, in z)
     int64_t budget;
     // system (owned by the handle)
     const double* W;
@@ -40,14 +42,12 @@ struct SlotDev {
     float4* src32;
     double4* src64;
     float4* srcdf;
-    double* part;
+    unsigned long long* acc;   // exact node accumulators of the dense sum
     const double* g;
     double lam1, lam2, il1, il2, h2, h3, scale;
     pk::PairConsts kc;
     // pair schedules of the three arithmetics ([0] FP32, [1] float-float, [2] FP64; owned by the handle)
     const PairItem* items[3];
-    const PairRec* recs[3];
-    const int32_t* rptr[3];
     int BS[3];
     TreeView tv;             // far-field data of a treecode handle (tv.on = 0 otherwise)
     // solver workspace (owned by the handle)

@@ -10,7 +10,7 @@ namespace ctr {
 namespace pk {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = 1u << 22;   // default polls of a bounded mbarrier wait
 constexpr int kExpHi = 64;      // e^{-k}, k = 0..63
 constexpr int kExpLo = 1024;    // e^{-k/1024}, k = 0..1023
 
@@ -21,6 +21,8 @@ struct PairConsts {
     const float2* exp_tab;           // [kExpHi + kExpLo] float-float, global
     // the FP32 values duplicated into both halves of a 64-bit word (f32x2 operands)
     unsigned long long one2, mone2, three2, mthree2, c1x2, nc1x2, c2x2, nc2x2, kap2, kl2x2;
+    uint32_t wait_limit;             // polls of a source-tile wait before the block gives up
+    uint32_t pad_;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -57,9 +59,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false after kWaitLimit polls (each poll may suspend briefly).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+// Bounded wait: false after `limit` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -223,6 +225,107 @@ __device__ __forceinline__ F2 exp_neg_ffl(F2 x, const float2* tab) {
     const F2 omf = fast_two_sum(1.0f, -fh);
     const F2 ef = fast_two_sum(omf.hi, __fadd_rn(__fsub_rn(omf.lo, f.lo), q));
     return mull(mull(f2(tab[k >> 10]), f2(tab[kExpHi + (k & 1023)])), ef);
+}
+
+// ------------------------------------------------------------------ exact node accumulators
+// The dense sum's partial results (an item's target sums, a symmetric tile's source sums, a far item's
+// sums) are added into per-node accumulators in whatever order the blocks run.  To keep the result
+// independent of that order, each contribution v (FP64) is turned into the integer round(|v| 2^kFxFrac)
+// and added exactly: the integer's 32-bit chunks go to 64-bit words by atomic addition (fewer than 2^31
+// contributions per word cannot carry out of it), positive and negative contributions to separate sets
+// of kFxChunks words, so a contribution touches at most the three words its 53 significant bits span.
+// Reading a node's sum propagates the carries, subtracts the two sets and rounds once to FP64.
+// Range: |v| < 2^(32 kFxChunks - kFxFrac) = 2^72; below 2^-kFxFrac a contribution is rounded to a
+// multiple of 2^-kFxFrac = 7.5e-37.  A non-finite or out-of-range contribution marks the node
+// (its last word), and the node then reads as NaN, as an FP64 sum of such a term would.
+// Layout: word k of sign set g (0 positive, 1 negative) of sum c (0, 1) of node position p at
+// acc[((2 c + g) kFxChunks + k) * stride + p], the mark at acc[4 kFxChunks * stride + p]:
+// kFxWords 64-bit words per node.
+constexpr int kFxChunks = 6;
+constexpr int kFxFrac = 120;
+constexpr int kFxWords = 4 * kFxChunks + 1;
+
+__device__ __forceinline__ void fx_add(unsigned long long* __restrict__ acc, int64_t stride, int c, double v) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex == 0x7ff) {   // not finite
+        atomicOr(acc + (int64_t)(4 * kFxChunks) * stride, 1ull);
+        return;
+    }
+    unsigned long long m = bits & ((1ull << 52) - 1);
+    if (ex != 0) m |= 1ull << 52;
+    if (m == 0) return;
+    int sh = (ex != 0 ? ex - 1075 : -1074) + kFxFrac;   // |v| 2^kFxFrac = m 2^sh
+    if (sh < 0) {                                       // below the resolution: round to nearest
+        if (sh < -60) return;
+        m = (m + (1ull << (-sh - 1))) >> (-sh);
+        sh = 0;
+        if (m == 0) return;
+    }
+    if (sh + 53 > 32 * kFxChunks) {   // out of range
+        atomicOr(acc + (int64_t)(4 * kFxChunks) * stride, 1ull);
+        return;
+    }
+    unsigned long long* base = acc + (int64_t)((2 * c + (int)(bits >> 63)) * kFxChunks) * stride;
+    // m 2^sh spans the 32-bit chunks k0 .. k0 + 2 (m < 2^53)
+    const int k0 = sh >> 5, r = sh & 31;
+    const unsigned long long lo = m << r;                       // bits 0..63 of m 2^r
+    const unsigned long long hi = r ? (m >> (64 - r)) : 0ull;   // bits 64.. (m 2^r < 2^85)
+    const unsigned long long ch[3] = {lo & 0xffffffffull, lo >> 32, hi};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (ch[q] != 0 && k0 + q < kFxChunks) atomicAdd(base + (int64_t)(k0 + q) * stride, ch[q]);
+}
+
+// One sum (c) of the node at acc (stride as in fx_add), rounded to FP64: carries of both sign sets,
+// positive minus negative, one rounding.  The node's words of that sum are cleared when `clear`.
+__device__ __forceinline__ double fx_read_one(unsigned long long* __restrict__ acc, int64_t stride, int c,
+                                              bool clear) {
+    uint32_t D[kFxChunks + 1];
+    unsigned long long cp = 0, cn = 0;
+    long long borrow = 0;
+#pragma unroll
+    for (int k = 0; k <= kFxChunks; ++k) {
+        unsigned long long tp = cp, tn = cn;
+        if (k < kFxChunks) {
+            unsigned long long* ap = acc + (int64_t)((2 * c) * kFxChunks + k) * stride;
+            unsigned long long* an = acc + (int64_t)((2 * c + 1) * kFxChunks + k) * stride;
+            tp += *ap;
+            tn += *an;
+            if (clear) *ap = *an = 0ull;
+        }
+        cp = tp >> 32;
+        cn = tn >> 32;
+        const long long t = (long long)(tp & 0xffffffffull) - (long long)(tn & 0xffffffffull) - borrow;
+        D[k] = (uint32_t)t;
+        borrow = t < 0 ? 1 : 0;
+    }
+    const bool neg = borrow != 0;
+    if (neg) {   // two's complement of the chunk string
+        unsigned long long carry = 1;
+#pragma unroll
+        for (int k = 0; k <= kFxChunks; ++k) {
+            const unsigned long long t = (unsigned long long)(uint32_t)~D[k] + carry;
+            D[k] = (uint32_t)t;
+            carry = t >> 32;
+        }
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int k = kFxChunks; k >= 0; --k) v = fma(v, 4294967296.0, (double)D[k]);
+    v = ldexp(v, -kFxFrac);
+    return neg ? -v : v;
+}
+
+// Both sums of the node at acc (NaN when a contribution was marked); clears the node's words when `clear`.
+__device__ __forceinline__ void fx_read(unsigned long long* __restrict__ acc, int64_t stride, bool clear, double& s1,
+                                        double& s2) {
+    unsigned long long* mark = acc + (int64_t)(4 * kFxChunks) * stride;
+    const bool bad = *mark != 0ull;
+    s1 = fx_read_one(acc, stride, 0, clear);
+    s2 = fx_read_one(acc, stride, 1, clear);
+    if (clear) *mark = 0ull;
+    if (bad) s1 = s2 = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // ------------------------------------------------------------------ pair policies
@@ -705,18 +808,37 @@ __device__ __forceinline__ void fold_targets(const typename Policy::Acc& a, doub
     else Policy::fold_pack(a, s1, s2);
 }
 
+// Where a work item's sums go.  RegionOut: the sums of node i to out[c * cstride + (i - t0)], c = 0, 1
+// (one region per item, added later in a fixed order); FxOut: added into the node's exact accumulators.
+struct RegionOut {
+    double* out;
+    int64_t cstride, t0;
+    __device__ __forceinline__ void put(int64_t i, double s1, double s2) const {
+        out[i - t0] = s1;
+        out[cstride + i - t0] = s2;
+    }
+};
+struct FxOut {
+    unsigned long long* acc;
+    int64_t stride;
+    __device__ __forceinline__ void put(int64_t i, double s1, double s2) const {
+        fx_add(acc + i, stride, 0, s1);
+        fx_add(acc + i, stride, 1, s2);
+    }
+};
+
 // One one-sided work item of the dense pair sum: target block `tblock`
 // (kThreads * R targets) against sources [j_begin, j_end), with the correction
-// pairs masked; the sums of target i go to out[c * cstride + (i - t0)], c = 0, 1.
+// pairs masked; the sums of target i go to `out` (RegionOut or FxOut).
 // Shared memory (ring, tables, barriers) is set up by the caller; `gt` counts
 // the tiles this block has consumed so far (it fixes the mbarrier phase parity
 // across items).  Returns false when a bounded wait expired (the error word is
 // set; the caller must return).
-template <typename Policy, int R, int U = 2>
+template <typename Policy, int R, int U = 2, typename Out = FxOut>
 __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict__ src, int M,
                                           const int32_t* __restrict__ eptr, const int32_t* __restrict__ excl,
-                                          int tblock, int j_begin, int j_end, double* __restrict__ out,
-                                          int64_t cstride, int64_t t0, const PairConsts& kc,
+                                          int tblock, int j_begin, int j_end, const Out& out,
+                                          const PairConsts& kc,
                                           int* __restrict__ err, typename Policy::Src* ring, const float2* tab,
                                           uint64_t* bar, uint32_t& gt) {
     using Src = typename Policy::Src;
@@ -759,11 +881,13 @@ __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict
     for (int k = 0; k < ntiles; ++k) {
         const uint32_t g = gt + (uint32_t)k;
         if (tid == 0 && k + 1 < ntiles) issue(k + 1);
-        const bool ok = mbar_wait(&bar[g & 1], (g >> 1) & 1);
+        const bool ok = mbar_wait(&bar[g & 1], (g >> 1) & 1, kc.wait_limit);
         if (__syncthreads_or(!ok)) {
-            // give up: flag it, let the copy that may still be in flight land, return
+            // give up: flag it, let the copies that may still be in flight (this tile's and the
+            // next one's) land in this block's shared memory, return
             if (tid == 0) {
                 atomicOr(err, kErrWait);
+                (void)mbar_wait(&bar[g & 1], (g >> 1) & 1);
                 if (k + 1 < ntiles) (void)mbar_wait(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
             }
             return false;
@@ -810,12 +934,8 @@ __device__ __forceinline__ bool pair_item(const typename Policy::Src* __restrict
     }
     gt += (uint32_t)ntiles;
 #pragma unroll
-    for (int a = 0; a < RP; ++a) {
-        if (ti[a] < M) {
-            out[ti[a] - t0] = s1[a];
-            out[cstride + ti[a] - t0] = s2[a];
-        }
-    }
+    for (int a = 0; a < RP; ++a)
+        if (ti[a] < M) out.put(ti[a], s1[a], s2[a]);
     return true;
 }
 
@@ -851,8 +971,8 @@ __device__ __forceinline__ void transpose_sum(typename Policy::JAcc (&v)[V], int
 // One symmetric work item: target block `tblock` against sources
 // [j_begin, j_end), no correction pair among them (the schedule guarantees it).
 // Every pair is evaluated once for both orientations (Policy::pair_sym).  The
-// target sums go to out_i[c * BS + (i - tblock * BS)], the source sums to
-// out_j[c * len + (j - j_begin)], len = j_end - j_begin.  Sources are read by
+// target sums (at the item's end) and the source sums (per tile) are added
+// into the nodes' exact accumulators (`out`).  Sources are read by
 // broadcast as in the one-sided item; a thread accumulates the source-side
 // terms of a chunk of V sources over its R targets, the warp transposes and
 // sums them (transpose_sum), and the kWarps warp sums of a tile are added in
@@ -862,8 +982,7 @@ __device__ __forceinline__ void transpose_sum(typename Policy::JAcc (&v)[V], int
 // pair arithmetics within the instruction cache.
 template <typename Policy, int R, int V, int U, int S = V>
 __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __restrict__ src, int M, int tblock,
-                                              int j_begin, int j_end, double* __restrict__ out_i,
-                                              double* __restrict__ out_j, const PairConsts& kc,
+                                              int j_begin, int j_end, const FxOut& out, const PairConsts& kc,
                                               int* __restrict__ err, typename Policy::Src* ring,
                                               typename Policy::JAcc* jred, const float2* tab, uint64_t* bar,
                                               uint32_t& gt) {
@@ -907,10 +1026,11 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
     for (int k = 0; k < ntiles; ++k) {
         const uint32_t g = gt + (uint32_t)k;
         if (tid == 0 && k + 1 < ntiles) issue(k + 1);
-        const bool ok = mbar_wait(&bar[g & 1], (g >> 1) & 1);
+        const bool ok = mbar_wait(&bar[g & 1], (g >> 1) & 1, kc.wait_limit);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
+            if (tid == 0) {   // as in pair_item: flag, drain both copies in flight, return
                 atomicOr(err, kErrWait);
+                (void)mbar_wait(&bar[g & 1], (g >> 1) & 1);
                 if (k + 1 < ntiles) (void)mbar_wait(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
             }
             return false;
@@ -988,50 +1108,32 @@ __device__ __forceinline__ bool pair_item_sym(const typename Policy::Src* __rest
             for (int w = 1; w < kWarps; ++w) t = Policy::jadd(t, jred[w * TILE + tid]);
             double d1 = 0.0, d2 = 0.0;
             Policy::fold(t, d1, d2);
-            out_j[j0 - j_begin + tid] = d1;
-            out_j[(int64_t)len + j0 - j_begin + tid] = d2;
+            out.put(j0 + tid, d1, d2);
         }
         __syncthreads();   // jred and the buffer of this tile are free again
     }
     gt += (uint32_t)ntiles;
 #pragma unroll
-    for (int a = 0; a < RP; ++a) {
-        if (ti[a] < M) {
-            out_i[ti[a] - tblock * BS] = s1[a];
-            out_i[BS + ti[a] - tblock * BS] = s2[a];
-        }
-    }
+    for (int a = 0; a < RP; ++a)
+        if (ti[a] < M) out.put(ti[a], s1[a], s2[a]);
     return true;
 }
 
-// Runs one item of a schedule (dispatch on its kind).
+// Runs one item of a schedule (dispatch on its kind); its sums go into the nodes' exact accumulators
+// (acc, M words per accumulator word, fx_add).
 template <typename Policy, int R, int V, int U>
 __device__ __forceinline__ bool run_item(const PairItem& it, const typename Policy::Src* __restrict__ src, int M,
                                          const int32_t* __restrict__ eptr, const int32_t* __restrict__ excl,
-                                         double* __restrict__ buf, const PairConsts& kc, int* __restrict__ err,
-                                         typename Policy::Src* ring, typename Policy::JAcc* jred,
-                                         const float2* tab, uint64_t* bar, uint32_t& gt) {
-    constexpr int BS = kThreads * R * Policy::kPack;
+                                         unsigned long long* __restrict__ acc, const PairConsts& kc,
+                                         int* __restrict__ err, typename Policy::Src* ring,
+                                         typename Policy::JAcc* jred, const float2* tab, uint64_t* bar,
+                                         uint32_t& gt) {
     constexpr int S = Policy::kSymStep < V ? Policy::kSymStep : V;
+    const FxOut out{acc, (int64_t)M};
     if (it.sym)
-        return pair_item_sym<Policy, R, V, U, S>(src, M, it.I, it.j_begin, it.j_end, buf + it.ibase,
-                                                 buf + it.jbase, kc, err, ring, jred, tab, bar, gt);
-    return pair_item<Policy, R, U>(src, M, eptr, excl, it.I, it.j_begin, it.j_end, buf + it.ibase, BS,
-                                   (int64_t)it.I * BS, kc, err, ring, tab, bar, gt);
-}
-
-// Fixed-order sum of every partial region that covers node i (block i / BS).
-__device__ __forceinline__ void gather_partials(const PairRec* __restrict__ recs, const int32_t* __restrict__ rptr,
-                                                int BS, const double* __restrict__ buf, int64_t i, double& s1,
-                                                double& s2) {
-    const int b = (int)(i / BS);
-    for (int q = rptr[b]; q < rptr[b + 1]; ++q) {
-        const PairRec r = recs[q];
-        const int64_t off = i - r.origin;
-        if (off < 0 || off >= r.len) continue;
-        s1 += buf[r.base + off];
-        s2 += buf[r.base + r.len + off];
-    }
+        return pair_item_sym<Policy, R, V, U, S>(src, M, it.I, it.j_begin, it.j_end, out, kc, err, ring, jred, tab,
+                                                 bar, gt);
+    return pair_item<Policy, R, U>(src, M, eptr, excl, it.I, it.j_begin, it.j_end, out, kc, err, ring, tab, bar, gt);
 }
 
 // Shared-memory bytes of a pair block: the two-stage source ring, the warp
@@ -1108,5 +1210,7 @@ int launch_schedule(ctr_ibim* s, int pol, const void* src, const pk::PairConsts&
 void set_packed_consts(pk::PairConsts& kc);
 // Pair constants of a handle (kernel-ratio terms, kappa, tables when needed)
 int pair_consts(ctr_ibim* s, bool tables, pk::PairConsts* out);
+// Polls of the pair kernels' bounded waits for launches prepared from now on (ctr_set_wait_limit)
+uint32_t wait_limit();
 
 }  // namespace ctr

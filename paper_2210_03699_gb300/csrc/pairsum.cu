@@ -16,9 +16,10 @@
 // per target) are skipped exactly: a warp takes a masked path only for tiles
 // that contain one of its lanes' excluded nodes.  The work is a schedule of
 // one-sided and symmetric items (schedule.cu): block pairs without correction
-// pairs are evaluated once for both orientations, each item writes FP64
-// partial regions, and the finishing kernel adds them in a fixed order
-// (deterministic).
+// pairs are evaluated once for both orientations, and each item adds its FP64
+// sums into the nodes' exact accumulators (integer addition: the result does
+// not depend on the order in which blocks add), read and cleared by the
+// finishing kernel.
 //
 // Three pair arithmetics share this pipeline (policies below):
 //   Fp32  FP32 terms, rsqrt and exp2 on the SFU (44 FP32-pipe ops per pair);
@@ -26,6 +27,7 @@
 //   Df64  double-FP32 "float-float" terms (error-free sums and products with
 //         FMA, rsqrt by one Newton step in df64, exp by two exact tables and
 //         a degree-4 polynomial), ~2^-44 relative, on the FP32 pipe.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -50,8 +52,9 @@ __global__ void __launch_bounds__(kThreads) pair_kernel(const typename Policy::S
     const int j_begin = blockIdx.y * src_per_split;
     const int j_end = min(M, j_begin + src_per_split);
     uint32_t gt = 0;
-    (void)pair_item<Policy, R>(src, M, eptr, excl, blockIdx.x, j_begin, j_end,
-                               partial + (size_t)blockIdx.y * 2 * M, M, 0, kc, err, sm.ring, sm.tab, bar, gt);
+    const RegionOut out{partial + (size_t)blockIdx.y * 2 * M, M, 0};
+    (void)pair_item<Policy, R, 2, RegionOut>(src, M, eptr, excl, blockIdx.x, j_begin, j_end, out, kc, err, sm.ring,
+                                             sm.tab, bar, gt);
 }
 
 // a = h^3 W rho1/(4 pi), b = h^3 W rho2/(4 pi) into the weight slots of the packed sources
@@ -81,16 +84,15 @@ __global__ void pack_kernel(const double* __restrict__ x, const double* __restri
     }
 }
 
-// y = diag + fixed-order sum of the schedule's partial regions + correction (FP64)
-__global__ void finish_kernel(int64_t M, const PairRec* __restrict__ recs, const int32_t* __restrict__ rptr, int BS,
-                              const double* __restrict__ partial, const double* __restrict__ x,
+// y = diag + the node's accumulated dense sum (read and cleared) + correction (FP64)
+__global__ void finish_kernel(int64_t M, unsigned long long* __restrict__ acc, const double* __restrict__ x,
                               double* __restrict__ y, const double* __restrict__ W, const int32_t* __restrict__ ptr,
                               const int32_t* __restrict__ node, const double* __restrict__ w, int64_t E,
                               double lam1, double lam2, double h2, double h3, const int32_t* __restrict__ tinv) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    double s1 = 0.0, s2 = 0.0;
-    gather_partials(recs, rptr, BS, partial, tinv ? (int64_t)tinv[i] : i, s1, s2);
+    double s1, s2;
+    fx_read(acc + (tinv ? (int64_t)tinv[i] : i), M, true, s1, s2);
     double c1 = 0.0, c2 = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
         const int m = node[e];
@@ -148,10 +150,18 @@ PairPlan make_plan(int64_t M, int R, int tile, int slots) {
     return p;
 }
 
+// Dynamic shared memory of the one-sided grid launch: the source ring only (no symmetric items, no
+// tables); the occupancy query and the launch use the same figure.
+template <typename Policy>
+constexpr size_t grid_launch_smem() {
+    static_assert(!Policy::kTables, "the one-sided grid launch carries no exponential tables");
+    return pair_ring_bytes<Policy>();
+}
+
 template <typename Policy, int R>
 int resident_slots(int sms, int* slots) {
     int per_sm = 0;
-    const size_t smem = pair_smem_bytes<Policy>();
+    const size_t smem = grid_launch_smem<Policy>();
     CTR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel<Policy, R>, kThreads, smem));
     *slots = std::max(1, per_sm) * sms;
     return CTR_OK;
@@ -195,8 +205,15 @@ void set_packed_consts(PairConsts& kc) {
     kc.kl2x2 = dup(kc.kl2f);
 }
 
+namespace {
+std::atomic<uint32_t> g_wait_limit{kWaitLimit};
+}  // namespace
+
+uint32_t wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 int pair_consts(ctr_ibim* s, bool tables, PairConsts* out) {
     PairConsts kc{};
+    kc.wait_limit = wait_limit();
     kc.c1 = s->eps_out / s->eps_in;
     kc.c2 = s->eps_in / s->eps_out;
     kc.kappa = s->kappa;
@@ -211,6 +228,13 @@ int pair_consts(ctr_ibim* s, bool tables, PairConsts* out) {
     kc.exp_tab = nullptr;
     if (tables) CTR_TRY(exp_table(s->device, &kc.exp_tab));
     *out = kc;
+    return CTR_OK;
+}
+
+int alloc_accumulators(ctr_ibim* s) {
+    const size_t bytes = sizeof(unsigned long long) * (size_t)kFxWords * (size_t)s->M;
+    CTR_TRY(s->acc.alloc(bytes));
+    CTR_CUDA_TRY(cudaMemsetAsync(s->acc.p, 0, bytes, s->stream));
     return CTR_OK;
 }
 
@@ -256,11 +280,9 @@ int apply_operator_timed(ctr_ibim* s, const double* d_x, double* d_y, int precis
     CTR_TRY(mark(2));
     CTR_TRY(launch_tree(s, pol));
     CTR_TRY(mark(3));
-    const PairSchedule& p = s->sched[pol];
     const double h2 = s->h * s->h;
     const double h3 = s->h * s->h * s->h;
-    finish_kernel<<<grid_for(M, 256), 256, 0, st>>>(M, p.d_recs.as<PairRec>(), p.d_rptr.as<int32_t>(), p.BS,
-                                                   s->partial.as<double>(), d_x, d_y, s->na.W,
+    finish_kernel<<<grid_for(M, 256), 256, 0, st>>>(M, s->acc.as<unsigned long long>(), d_x, d_y, s->na.W,
                                                    s->corr_ptr.as<int32_t>(), s->corr_node.as<int32_t>(),
                                                    s->corr_w.as<double>(), s->E,
                                                    0.5 * (1.0 + s->eps_out / s->eps_in),
@@ -271,6 +293,12 @@ int apply_operator_timed(ctr_ibim* s, const double* d_x, double* d_y, int precis
 }
 
 }  // namespace ctr
+
+extern "C" int ctr_set_wait_limit(int64_t polls) {
+    if (polls > (int64_t)UINT32_MAX) return ctr::fail(CTR_ERR_INVALID, "polls must be < 2^32");
+    ctr::g_wait_limit.store(polls < 0 ? ctr::pk::kWaitLimit : (uint32_t)polls, std::memory_order_relaxed);
+    return CTR_OK;
+}
 
 namespace ctr {
 
@@ -303,7 +331,8 @@ int launch_fp32_pairs_external(const float4* src, int64_t M, const int32_t* eptr
     kc.kappaf = (float)kappa;
     kc.kl2f = (float)(-kappa * 1.4426950408889634);
     set_packed_consts(kc);
-    const size_t smem = 2 * Fp32Policy::kTile * Fp32Policy::kVec * sizeof(float4);
+    kc.wait_limit = wait_limit();
+    const size_t smem = grid_launch_smem<Fp32Policy>();
     dim3 grid(p.target_blocks, p.splits);
     pair_kernel<Fp32Policy, 2><<<grid, kThreads, smem, st>>>(src, (int)M, eptr, excl, p.src_per_split, partial, kc,
                                                              err);

@@ -14,9 +14,9 @@
 // lie within a few h of P_i, near pairs form a band around the diagonal.
 //
 // Items are split to at most a quarter-wave of work each and sorted by cost
-// for the atomic-counter scheduler.  Every item writes its own partial region;
-// the nodes of a block add the regions that cover them in a fixed order
-// (PairRec lists), so the result does not depend on which block ran what.
+// for the atomic-counter scheduler.  Every item adds its sums into the nodes'
+// exact accumulators (pairkern.cuh, fx_add: integer addition, so the order in
+// which blocks add does not change a bit of the result).
 #include <algorithm>
 #include <atomic>
 #include <numeric>
@@ -55,8 +55,9 @@ __global__ void __launch_bounds__(kThreads, 2) sched_kernel(const typename Polic
                                                          const int32_t* __restrict__ eptr,
                                                          const int32_t* __restrict__ excl,
                                                          const PairItem* __restrict__ items, int n_items,
-                                                         int* __restrict__ counter, double* __restrict__ buf,
-                                                         PairConsts kc, int* __restrict__ err) {
+                                                         int* __restrict__ counter,
+                                                         unsigned long long* __restrict__ acc, PairConsts kc,
+                                                         int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PairSmem<Policy> sm(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kThreads, 2) sched_kernel(const typename Polic
         const int it = cur;
         __syncthreads();
         if (it >= n_items) break;
-        if (!run_item<Policy, R, V, U>(items[it], src, M, eptr, excl, buf, kc, err, sm.ring, sm.jred, sm.tab, bar,
+        if (!run_item<Policy, R, V, U>(items[it], src, M, eptr, excl, acc, kc, err, sm.ring, sm.jred, sm.tab, bar,
                                        gt))
             return;
     }
@@ -107,7 +108,7 @@ int sched_launch(ctr_ibim* s, int pol, const void* src, const PairConsts& kc, in
         reinterpret_cast<const typename Policy::Src*>(src), (int)s->M,
         s->tree ? s->tree->d_eptr.as<int32_t>() : s->corr_ptr.as<int32_t>(),
         s->tree ? s->tree->d_excl.as<int32_t>() : s->excl.as<int32_t>(), p.d_items.as<PairItem>(),
-        (int)p.items.size(), counter, s->partial.as<double>(), kc, s->err.as<int>());
+        (int)p.items.size(), counter, s->acc.as<unsigned long long>(), kc, s->err.as<int>());
     CTR_LAUNCHED();
     return CTR_OK;
 }
@@ -163,7 +164,6 @@ void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost,
     p.items.clear();
     p.cost.clear();
     p.pairs_sym = p.pairs_one = 0;
-    int64_t off = 0;
     for (const Run& r : runs) {
         const int64_t len = r.j1 - r.j0;
         const double unit = (double)BS * (r.sym ? sym_cost : 1.0);
@@ -177,13 +177,6 @@ void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost,
             it.j_begin = (int32_t)a;
             it.j_end = (int32_t)std::min<int64_t>(r.j1, a + plen);
             it.sym = r.sym;
-            it.ibase = off;
-            off += 2 * (int64_t)BS;
-            it.jbase = 0;
-            if (r.sym) {
-                it.jbase = off;
-                off += 2 * (int64_t)(it.j_end - it.j_begin);
-            }
             const int64_t tgt = std::min<int64_t>(BS, M - (int64_t)r.I * BS);
             if (r.sym) p.pairs_sym += tgt * (it.j_end - it.j_begin);
             else p.pairs_one += tgt * (it.j_end - it.j_begin);
@@ -191,27 +184,10 @@ void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost,
             p.cost.push_back(unit * (double)(it.j_end - it.j_begin));
         }
     }
-    p.part_doubles = off;
 }
 
-// Device copies: region lists per block in item creation order, items sorted by decreasing cost
-// (afterwards the host copy is in that sorted order too).
+// Device copy of the items sorted by decreasing cost (afterwards the host copy is in that order too).
 int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
-    const int nb = p.nb;
-    std::vector<std::vector<PairRec>> per(nb);
-    for (const PairItem& it : p.items) {
-        per[it.I].push_back(PairRec{it.ibase, p.BS, (int32_t)((int64_t)it.I * p.BS)});
-        if (it.sym) {
-            const int b0 = it.j_begin / p.BS, b1 = (it.j_end - 1) / p.BS;
-            for (int b = b0; b <= b1; ++b)
-                per[b].push_back(PairRec{it.jbase, it.j_end - it.j_begin, it.j_begin});
-        }
-    }
-    std::vector<int32_t> rptr(nb + 1, 0);
-    for (int b = 0; b < nb; ++b) rptr[b + 1] = rptr[b] + (int32_t)per[b].size();
-    std::vector<PairRec> recs;
-    recs.reserve(rptr[nb]);
-    for (int b = 0; b < nb; ++b) recs.insert(recs.end(), per[b].begin(), per[b].end());
     std::vector<int> order(p.items.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p.cost[a] > p.cost[b]; });
@@ -222,15 +198,9 @@ int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
         sorted_cost[k] = p.cost[order[k]];
     }
     CTR_TRY(p.d_items.alloc(sizeof(PairItem) * std::max<size_t>(1, sorted.size())));
-    CTR_TRY(p.d_rptr.alloc(sizeof(int32_t) * rptr.size()));
-    CTR_TRY(p.d_recs.alloc(sizeof(PairRec) * std::max<size_t>(1, recs.size())));
     if (!sorted.empty())
         CTR_CUDA_TRY(cudaMemcpyAsync(p.d_items.p, sorted.data(), sizeof(PairItem) * sorted.size(),
                                      cudaMemcpyHostToDevice, st));
-    CTR_CUDA_TRY(cudaMemcpyAsync(p.d_rptr.p, rptr.data(), sizeof(int32_t) * rptr.size(), cudaMemcpyHostToDevice, st));
-    if (!recs.empty())
-        CTR_CUDA_TRY(
-            cudaMemcpyAsync(p.d_recs.p, recs.data(), sizeof(PairRec) * recs.size(), cudaMemcpyHostToDevice, st));
     CTR_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
     // the host copy follows the device order: the engine's work entries index the device list
     p.items.swap(sorted);
@@ -301,13 +271,11 @@ int build_schedules(ctr_ibim* s, const int slots[3]) {
     CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
     const int Rs[3] = {kR32 * Fp32x2Policy::kPack, kRdf, kR64};   // targets per thread
     const int tiles[3] = {Fp32x2Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
-    int64_t need = 1;
     for (int p = 0; p < 3; ++p) {
         plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], flags, g0, nb0, slots[p]);
         CTR_TRY(upload_schedule(s->sched[p], M, s->stream));
-        need = std::max(need, s->sched[p].part_doubles);
     }
-    CTR_TRY(s->partial.alloc(sizeof(double) * (size_t)need));
+    CTR_TRY(alloc_accumulators(s));
     CTR_TRY(s->counter.alloc(sizeof(int) * 4));
     return CTR_OK;
 }

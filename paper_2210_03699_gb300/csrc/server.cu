@@ -17,7 +17,7 @@
 // for memory to free up (requests behind it wait too, so none starves).  The
 // footprint estimate counts the tube nodes on the host (|d| < eps) and charges
 // the per-node cost of geometry, packed sources, solver vectors and the
-// Krylov basis plus the pair schedules' partial regions (M^2 / 32 bytes);
+// Krylov basis plus the dense sum's exact node accumulators (200 bytes);
 // after setup the handle's real allocation is charged instead.
 #include <chrono>
 #include <condition_variable>
@@ -54,16 +54,17 @@ struct Request {
     cudaStream_t stream = nullptr;   // the handle's own non-blocking stream (created and destroyed here)
     int64_t charged = 0;
     bool done = false;
+    bool cancel = false;   // ctr_server_cancel: drop at the next point the owning thread reaches
 };
 
 size_t handle_bytes(const ctr_ibim* s) {
     const DevBuf* bufs[] = {&s->lin, &s->nodes, &s->src32, &s->src64, &s->srcdf, &s->corr_ptr, &s->corr_node,
-                            &s->corr_w, &s->bad, &s->excl, &s->rhs, &s->charges, &s->partial, &s->err, &s->vecs,
-                            &s->red, &s->kr.V, &s->kr.H, &s->kr.cs, &s->kr.sn, &s->kr.s, &s->kr.y,
+                            &s->corr_w, &s->bad, &s->excl, &s->rhs, &s->charges, &s->acc, &s->err, &s->vecs,
+                            &s->red, &s->map_ws, &s->map_io, &s->kr.V, &s->kr.H, &s->kr.cs, &s->kr.sn, &s->kr.s, &s->kr.y,
                             &s->kr.part, &s->kr.scal};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
-    for (const PairSchedule& p : s->sched) b += p.d_items.bytes + p.d_rptr.bytes + p.d_recs.bytes;
+    for (const PairSchedule& p : s->sched) b += p.d_items.bytes;
     b += s->counter.bytes;
     b += (size_t)tree_bytes(s);
     return b;
@@ -104,17 +105,15 @@ int64_t estimate_bytes(const Request& r) {
     int64_t M = 0;
     for (double d : r.sdist) M += (std::fabs(d) < eps) ? 1 : 0;
     const int m = r.opt.restart > 0 ? r.opt.restart : 64;
-    // per node: geometry 16 doubles, packed sources 32 + 64 + 64 bytes, corrections (~50 entries
-    // worst case, K-reg) 36 bytes each, solver vectors 12 doubles, Krylov (m + 1) x 2 doubles;
-    // pair partial regions: the source sums of the symmetric items, M^2 / 256 doubles for the
-    // 256-node blocks of the float-float and FP64 schedules, plus the target sums (a few MB)
-    const int64_t per_node = 16 * 8 + 160 + 50 * 36 + 12 * 8 + (int64_t)(m + 1) * 16;
-    // with the treecode: the near and far items of the three arithmetics (a few dozen regions per
-    // target block), the tree-order exclusion lists and the cluster charges
-    const int64_t regions = (r.opt.farfield == CTR_FARFIELD_TREECODE) ? M * 4096 + ((int64_t)64 << 20)
-                                                                      : M * M / 32 + ((int64_t)16 << 20);
+    // per node: geometry 16 doubles, packed sources 64 + 64 + 64 bytes, corrections (~50 entries
+    // worst case, K-reg) 36 bytes each, solver vectors 12 doubles, Krylov (m + 1) x 2 doubles, the
+    // dense sum's exact accumulators 25 words; plus the pair schedules' items (a few MB)
+    const int64_t per_node = 16 * 8 + 192 + 50 * 36 + 12 * 8 + (int64_t)(m + 1) * 16 + 25 * 8;
+    // with the treecode: the tree-order exclusion lists, moment chunks and cluster charges
+    const int64_t extra = (r.opt.farfield == CTR_FARFIELD_TREECODE) ? M * 512 + ((int64_t)64 << 20)
+                                                                    : ((int64_t)16 << 20);
     const int64_t grid_bytes = (int64_t)r.sdist.size() * (8 + 4);   // staging copy + node map during setup
-    return M * per_node + regions + grid_bytes;
+    return M * per_node + extra + grid_bytes;
 }
 
 void release_stream(Request* r) {
@@ -208,15 +207,25 @@ void setup_loop(ctr_server* sv) {
         r->sdist.clear();
         r->sdist.shrink_to_fit();
         if (s1 >= 0 && (sv->fatal || sv->stop)) {   // the engine is gone: nothing will run this system
-            sv->used -= r->charged;
-            r->charged = 0;
-            finish_request(sv, r, sv->fatal ? sv->fatal : CTR_ERR_INVALID);
+            // free the system before the request is marked done (a waiter may release it at once)
             lk.unlock();
             ctr_ibim_destroy(sys);
             release_stream(r);
+            lk.lock();
+            sv->used -= r->charged;
+            r->charged = 0;
+            finish_request(sv, r, sv->fatal ? sv->fatal : CTR_ERR_INVALID);
             break;
         }
-        if (s1 < 0) {
+        if (s1 >= 0 && r->cancel) {   // cancelled during its setup
+            lk.unlock();
+            ctr_ibim_destroy(sys);
+            release_stream(r);
+            lk.lock();
+            sv->used -= r->charged;
+            r->charged = 0;
+            finish_request(sv, r, CTR_ERR_CANCELLED);
+        } else if (s1 < 0) {
             sv->used -= r->charged;
             r->charged = 0;
             finish_request(sv, r, s1);
@@ -247,6 +256,22 @@ void worker_loop(ctr_server* sv) {
             take.swap(sv->ready);
         }
         for (Request* r : take) {
+            bool cancelled;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                cancelled = r->cancel;
+            }
+            if (cancelled) {   // cancelled while set up and waiting for a slot
+                ctr_ibim_destroy(r->sys);
+                release_stream(r);
+                std::lock_guard<std::mutex> lk(sv->mu);
+                r->sys = nullptr;
+                sv->used -= r->charged;
+                r->charged = 0;
+                finish_request(sv, r, CTR_ERR_CANCELLED);
+                sv->cv_work.notify_all();
+                continue;
+            }
             int slot = -1;
             const int s1 = engine_admit(sv->engine, r->sys, &slot);
             if (s1 < 0) {
@@ -265,6 +290,28 @@ void worker_loop(ctr_server* sv) {
                 sv->running.push_back(r);
                 sv->peak_slots = std::max(sv->peak_slots, (int)sv->running.size());
             }
+        }
+        // cancelled running systems leave their slots between two steps
+        std::vector<Request*> cancelled;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (Request* r : sv->running)
+                if (r->cancel) cancelled.push_back(r);
+        }
+        for (Request* r : cancelled) {
+            ctr_solve_info info{};
+            (void)engine_retire(sv->engine, r->slot, &info);
+            ctr_ibim_destroy(r->sys);
+            release_stream(r);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->sys = nullptr;
+            r->slot = -1;
+            r->res.info = info;
+            sv->running.erase(std::find(sv->running.begin(), sv->running.end(), r));
+            sv->used -= r->charged;
+            r->charged = 0;
+            finish_request(sv, r, CTR_ERR_CANCELLED);
+            sv->cv_work.notify_all();
         }
         bool any;
         {
@@ -389,7 +436,7 @@ int ctr_server_submit(ctr_server* sv, const ctr_grid* grid, const double* sdist,
     sv->all[r->ticket] = r;
     sv->waiting.push_back(r);
     *ticket = r->ticket;
-    sv->cv_work.notify_one();
+    sv->cv_work.notify_all();   // both the setup thread and the worker wait on cv_work
     return CTR_OK;
 }
 
@@ -442,6 +489,24 @@ int ctr_server_release(ctr_server* sv, uint64_t ticket) {
     if (!it->second->done) return fail(CTR_ERR_INVALID, "request not finished");
     delete it->second;
     sv->all.erase(it);
+    return CTR_OK;
+}
+
+int ctr_server_cancel(ctr_server* sv, uint64_t ticket) {
+    if (!sv) return fail(CTR_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(CTR_ERR_INVALID, "unknown ticket");
+    Request* r = it->second;
+    if (r->done) return fail(CTR_ERR_INVALID, "request already finished");
+    auto q = std::find(sv->waiting.begin(), sv->waiting.end(), r);
+    if (q != sv->waiting.end()) {   // still queued: nothing was charged or set up
+        sv->waiting.erase(q);
+        finish_request(sv, r, CTR_ERR_CANCELLED);
+        return CTR_OK;
+    }
+    r->cancel = true;   // in setup, set up, or running: the owning thread drops it
+    sv->cv_work.notify_all();
     return CTR_OK;
 }
 

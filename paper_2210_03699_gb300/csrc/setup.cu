@@ -18,14 +18,21 @@ constexpr int kScanThreads = 256;
 
 __device__ __forceinline__ bool in_tube(double d, double eps) { return fabs(d) < eps; }
 
+// Tube nodes per chunk of the grid; a non-finite signed distance anywhere sets kErrNumeric.
 __global__ void tube_count_kernel(const double* __restrict__ sd, int64_t total, double eps,
-                                  int32_t* __restrict__ counts) {
+                                  int32_t* __restrict__ counts, int* __restrict__ err) {
     int64_t base = (int64_t)blockIdx.x * kChunk;
     int c = 0;
+    bool bad = false;
     for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
         int64_t g = base + t;
-        if (g < total && in_tube(sd[g], eps)) ++c;
+        if (g < total) {
+            const double v = sd[g];
+            bad |= !isfinite(v);
+            if (in_tube(v, eps)) ++c;
+        }
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNumeric);
     __shared__ int warp_sum[kScanThreads / 32];
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
@@ -242,12 +249,14 @@ int setup_tube_and_geometry(ctr_ibim* s, const double* d_sdist) {
     DevBuf counts, offsets, node_of, scratch;
     CTR_TRY(counts.alloc(sizeof(int32_t) * nchunks));
     CTR_TRY(offsets.alloc(sizeof(int32_t) * (nchunks + 1)));
-    tube_count_kernel<<<(unsigned)nchunks, kScanThreads, 0, st>>>(d_sdist, total, s->eps, counts.as<int32_t>());
+    tube_count_kernel<<<(unsigned)nchunks, kScanThreads, 0, st>>>(d_sdist, total, s->eps, counts.as<int32_t>(),
+                                                                  s->err.as<int>());
     CTR_LAUNCHED();
     CTR_TRY(exclusive_scan_i32(counts.as<int32_t>(), offsets.as<int32_t>(), nchunks, st, scratch));
     int32_t Mh = 0;
     CTR_CUDA_TRY(cudaMemcpyAsync(&Mh, offsets.as<int32_t>() + nchunks, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CTR_CUDA_TRY(cudaStreamSynchronize(st));
+    CTR_TRY(check_device_error(s, "signed distance"));
     if (Mh <= 0) return fail(CTR_ERR_EMPTY_TUBE, "no grid node with |d| < eps");
     const int64_t M = Mh;
     s->M = M;

@@ -3,10 +3,10 @@
 // the nodes' tree order (the packed source arrays are permuted to it, so that
 // every cluster and target block is a contiguous range), the exclusion lists
 // in tree positions, and per pair arithmetic the schedule: one-sided pair
-// items for the direct ("near") ranges, far items for the far clusters, the
-// moment chunks of the clusters that carry charges, and the partial regions
-// every target block adds in a fixed order (near items, then far items, each
-// in creation order).  Per operator application: the near items run in the
+// items for the direct ("near") ranges, far items for the far clusters and the
+// moment chunks of the clusters that carry charges; near and far items add
+// their sums into the nodes' exact accumulators (order-independent).  Per
+// operator application: the near items run in the
 // pair kernels like any schedule; launch_tree runs the moments, the charge
 // reduction and the far items (tree.cuh).
 #include <cmath>
@@ -205,11 +205,10 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         CTR_TRY(upload(P.d_dref, dr, st));
         CTR_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    // ---- per pair arithmetic: lists, items, chunks, regions
+    // ---- per pair arithmetic: lists, items, chunks
     const int Rs[3] = {kR32 * Fp32x2Policy::kPack, kRdf, kR64};
     const int tiles[3] = {Fp32x2Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
     const size_t real_bytes[3] = {sizeof(float), sizeof(float), sizeof(double)};
-    int64_t need = 1;
     std::vector<int> counts(15, 0);
     for (int p = 0; p < 3; ++p) {
         PairSchedule& sc = s->sched[p];
@@ -268,14 +267,12 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         }
         const double near_cmax = std::max(1.0, near_total / ((double)kTreeItemsPerSlot * std::max(1, slots[p])));
         const double far_cmax = std::max(1.0, far_total / ((double)kTreeItemsPerSlot * std::max(1, slots[p])));
-        std::vector<std::vector<PairRec>> per((size_t)nb);
         std::vector<PairItem> items;
         std::vector<double> icost;
         std::vector<int32_t> flist;
         P.far.clear();
         P.far_cost.clear();
         P.near_pairs = P.far_evals = P.far_pairs = 0;
-        int64_t off = 0;
         for (int I = 0; I < nb; ++I) {
             const int64_t nt = std::min<int64_t>(BS, M - (int64_t)I * BS);
             for (int64_t r = L.near_ptr[(size_t)I]; r < L.near_ptr[(size_t)I + 1]; ++r) {
@@ -292,12 +289,8 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
                     it.j_begin = (int32_t)a;
                     it.j_end = (int32_t)std::min<int64_t>(e, a + plen);
                     it.sym = 0;
-                    it.ibase = off;
-                    it.jbase = 0;
-                    off += 2 * (int64_t)BS;
                     items.push_back(it);
                     icost.push_back((double)BS * (it.j_end - it.j_begin));
-                    per[(size_t)I].push_back(PairRec{it.ibase, BS, (int32_t)((int64_t)I * BS)});
                 }
             }
         }
@@ -315,23 +308,12 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
                 fi.l0 = (int32_t)flist.size();
                 for (int64_t k = a; k < b; ++k) flist.push_back(compact[(size_t)L.far_cl[(size_t)k]]);
                 fi.l1 = (int32_t)flist.size();
-                fi.ibase = off;
-                off += 2 * (int64_t)BS;
                 P.far.push_back(fi);
                 P.far_cost.push_back(unit * (double)(b - a));
-                per[(size_t)I].push_back(PairRec{fi.ibase, BS, (int32_t)((int64_t)I * BS)});
             }
         }
         sc.pairs_one = P.near_pairs;
         sc.pairs_sym = 0;
-        sc.part_doubles = off;
-        need = std::max(need, off);
-        // regions per block (near items, then far items, each in creation order)
-        std::vector<int32_t> rptr((size_t)nb + 1, 0);
-        for (int b = 0; b < nb; ++b) rptr[(size_t)b + 1] = rptr[(size_t)b] + (int32_t)per[(size_t)b].size();
-        std::vector<PairRec> recs;
-        recs.reserve(rptr[(size_t)nb]);
-        for (int b = 0; b < nb; ++b) recs.insert(recs.end(), per[(size_t)b].begin(), per[(size_t)b].end());
         // near items in decreasing cost (the host copy follows the device order)
         std::vector<int> order(items.size());
         std::iota(order.begin(), order.end(), 0);
@@ -343,8 +325,6 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
             sc.cost[k] = icost[(size_t)order[k]];
         }
         CTR_TRY(upload(sc.d_items, sc.items, st));
-        CTR_TRY(upload(sc.d_rptr, rptr, st));
-        CTR_TRY(upload(sc.d_recs, recs, st));
         // far-field buffers and the single-system work entries (decreasing cost)
         CTR_TRY(upload(P.d_box, box, st));
         CTR_TRY(upload(P.d_chunks, P.chunks, st));
@@ -371,7 +351,7 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         counts[3 * p + 2] = (int)P.far.size();
         CTR_CUDA_TRY(cudaStreamSynchronize(st));   // host vectors of this pass go out of scope
     }
-    CTR_TRY(s->partial.alloc(sizeof(double) * (size_t)need));
+    CTR_TRY(alloc_accumulators(s));
     CTR_TRY(s->counter.alloc(sizeof(int) * 4));
     // counters: [2 per arithmetic] work counters, then [3 per arithmetic] entry counts
     std::vector<int> cnt(15, 0);
@@ -402,7 +382,7 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
     v.src32 = s->src32.as<float4>();
     v.srcdf = s->srcdf.as<float4>();
     v.src64 = s->src64.as<double4>();
-    v.part = s->partial.as<double>();
+    v.acc = s->acc.as<unsigned long long>();
     v.c1 = s->eps_out / s->eps_in;
     v.c2 = s->eps_in / s->eps_out;
     v.kappa = s->kappa;

@@ -318,9 +318,8 @@ __global__ void __launch_bounds__(NT) k_tree_far(Acc acc, const int2* __restrict
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (pp[r] < M) {
-                const int64_t off = pp[r] - (int64_t)f.I * BS;
-                t.part[f.ibase + off] = o1[r];
-                t.part[f.ibase + BS + off] = o2[r];
+                pk::fx_add(t.acc + pp[r], M, 0, o1[r]);
+                pk::fx_add(t.acc + pp[r], M, 1, o2[r]);
             }
         }
     }
@@ -439,9 +438,8 @@ __global__ void __launch_bounds__(NT) k_tree_far2(Acc acc, const int2* __restric
 #pragma unroll
         for (int r = 0; r < 2 * RP; ++r) {
             if (pp[r] < M) {
-                const int64_t off = pp[r] - (int64_t)f.I * BS;
-                t.part[f.ibase + off] = o1[r];
-                t.part[f.ibase + BS + off] = o2[r];
+                pk::fx_add(t.acc + pp[r], M, 0, o1[r]);
+                pk::fx_add(t.acc + pp[r], M, 1, o2[r]);
             }
         }
     }

@@ -185,6 +185,17 @@ extern "C" int ctr_farfield_plan(int64_t M, const int32_t* ijk, const int32_t* e
         if (M > INT32_MAX / 4) return fail(CTR_ERR_CAPACITY, "farfield plan: too many nodes");
         if (degree < 2 || degree > 12 || leaf < 1 || block < 1 || margin < 0 || !(theta >= 0.0 && theta < 1.0))
             return fail(CTR_ERR_INVALID, "farfield plan: bad parameters");
+        if (margin > (1 << 20)) return fail(CTR_ERR_INVALID, "farfield plan: margin must be <= 2^20");
+        // the caller's arrays are read as given: check them before any of them indexes another
+        for (int64_t k = 0; k < 3 * M; ++k)
+            if (ijk[k] <= -(1 << 30) || ijk[k] >= (1 << 30))
+                return fail(CTR_ERR_INVALID, "farfield plan: grid indices must lie in (-2^30, 2^30)");
+        if (excl_ptr[0] != 0) return fail(CTR_ERR_INVALID, "farfield plan: excl_ptr[0] must be 0");
+        for (int64_t i = 0; i < M; ++i)
+            if (excl_ptr[i + 1] < excl_ptr[i]) return fail(CTR_ERR_INVALID, "farfield plan: excl_ptr must not decrease");
+        for (int64_t e = 0; e < (int64_t)excl_ptr[M]; ++e)
+            if (excl[e] < 0 || (int64_t)excl[e] >= M)
+                return fail(CTR_ERR_INVALID, "farfield plan: excluded node out of range");
         tree::Octree t;
         tree::build_octree(ijk, M, leaf, t);
         tree::Lists L;

@@ -1,5 +1,8 @@
-// Arithmetic-throughput probes (include/ctr_probe.h): dependent instruction chains on all SMs.
-#include "common.cuh"
+// Arithmetic-throughput probes (ctr_probe.h): dependent instruction chains on all SMs.  Built as a
+// library of its own (libctr_probe.so) for the benchmark's roofline denominators; not part of the
+// solver library or its C ABI.
+#include <cuda_runtime.h>
+
 #include "ctr_probe.h"
 
 namespace {
@@ -90,43 +93,41 @@ __global__ void dfma_kernel(double* out, int64_t iters, double a, double b) {
 }  // namespace
 
 extern "C" int ctr_probe_rate(int kind, int64_t iters, double* ops_per_s, double* seconds) {
-    using namespace ctr;
-    if (!ops_per_s || iters <= 0) return fail(CTR_ERR_INVALID, "bad probe arguments");
+    if (!ops_per_s || iters <= 0 || kind < CTR_PROBE_FFMA || kind > CTR_PROBE_DFMA) return -1;
     int dev = 0, sms = 0;
-    CTR_CUDA_TRY(cudaGetDevice(&dev));
-    CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (cudaGetDevice(&dev) != cudaSuccess) return -4;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -4;
     const int blocks = sms * 8;
-    DevBuf out;
-    CTR_TRY(out.alloc(sizeof(double) * kThreads));
-    cudaEvent_t e0, e1;
-    CTR_CUDA_TRY(cudaEventCreate(&e0));
-    CTR_CUDA_TRY(cudaEventCreate(&e1));
-    double per_thread_iter = kChains;
+    void* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * kThreads) != cudaSuccess) return -5;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto launch = [&](int64_t it) {
         switch (kind) {
-            case CTR_PROBE_FFMA: ffma_kernel<<<blocks, kThreads>>>(out.as<float>(), it, 0.9999f, 1e-4f); break;
-            case CTR_PROBE_FFMA2: ffma2_kernel<<<blocks, kThreads>>>(out.as<float>(), it, 0.9999f, 1e-4f); break;
-            case CTR_PROBE_EX2: ex2_kernel<<<blocks, kThreads>>>(out.as<float>(), it); break;
-            case CTR_PROBE_RSQRT: rsqrt_kernel<<<blocks, kThreads>>>(out.as<float>(), it); break;
-            case CTR_PROBE_DFMA: dfma_kernel<<<blocks, kThreads>>>(out.as<double>(), it, 0.9999, 1e-4); break;
-            default: break;
+            case CTR_PROBE_FFMA: ffma_kernel<<<blocks, kThreads>>>((float*)out, it, 0.9999f, 1e-4f); break;
+            case CTR_PROBE_FFMA2: ffma2_kernel<<<blocks, kThreads>>>((float*)out, it, 0.9999f, 1e-4f); break;
+            case CTR_PROBE_EX2: ex2_kernel<<<blocks, kThreads>>>((float*)out, it); break;
+            case CTR_PROBE_RSQRT: rsqrt_kernel<<<blocks, kThreads>>>((float*)out, it); break;
+            default: dfma_kernel<<<blocks, kThreads>>>((double*)out, it, 0.9999, 1e-4); break;
         }
     };
-    if (kind < CTR_PROBE_FFMA || kind > CTR_PROBE_DFMA) return fail(CTR_ERR_INVALID, "unknown probe kind");
-    if (kind == CTR_PROBE_FFMA2) per_thread_iter = 2 * kChains;
-    launch(iters / 10 + 1);   // warm-up
-    CTR_LAUNCHED();
-    CTR_CUDA_TRY(cudaEventRecord(e0));
-    launch(iters);
-    CTR_CUDA_TRY(cudaEventRecord(e1));
-    CTR_CUDA_TRY(cudaEventSynchronize(e1));
-    CTR_LAUNCHED();
+    const double per_thread_iter = (kind == CTR_PROBE_FFMA2) ? 2.0 * kChains : (double)kChains;
     float ms = 0.f;
-    CTR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (ok) {
+        launch(iters / 10 + 1);   // warm-up
+        ok = cudaGetLastError() == cudaSuccess && cudaEventRecord(e0) == cudaSuccess;
+    }
+    if (ok) {
+        launch(iters);
+        ok = cudaGetLastError() == cudaSuccess && cudaEventRecord(e1) == cudaSuccess &&
+             cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (!ok || !(ms > 0.f)) return -4;
     const double ops = (double)blocks * kThreads * per_thread_iter * (double)iters;
     *ops_per_s = ops / (ms * 1e-3);
     if (seconds) *seconds = ms * 1e-3;
-    return CTR_OK;
+    return 0;
 }

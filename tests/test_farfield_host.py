@@ -62,6 +62,24 @@ def test_plan_theta_zero_and_bad_arguments(systems):
         ctr.farfield_plan(S.geo.ijk, S.excl_ptr, S.excl_idx, 2, 13, 0.8, 64, 256)
     with pytest.raises(ctr.CtrError):
         ctr.farfield_plan(S.geo.ijk, S.excl_ptr, S.excl_idx, 2, 10, 1.0, 64, 256)
+    # a malformed exclusion CSR is rejected before it indexes anything
+    ptr = np.asarray(S.excl_ptr, dtype=np.int64)
+    idx = np.asarray(S.excl_idx, dtype=np.int64)
+    bad_first = ptr.copy()
+    bad_first[0] = 1
+    bad_order = ptr.copy()
+    bad_order[5] = bad_order[6] + 1
+    bad_node = idx.copy()
+    bad_node[3] = S.M
+    neg_node = idx.copy()
+    neg_node[0] = -1
+    for p_, i_ in ((bad_first, idx), (bad_order, idx), (ptr, bad_node), (ptr, neg_node)):
+        with pytest.raises(ctr.CtrError, match="farfield plan"):
+            ctr.farfield_plan(S.geo.ijk, p_, i_, 2, 6, 0.8, 64, 256)
+    huge = np.asarray(S.geo.ijk, dtype=np.int64).copy()
+    huge[0, 0] = 1 << 30
+    with pytest.raises(ctr.CtrError, match="grid indices"):
+        ctr.farfield_plan(huge, ptr, idx, 2, 6, 0.8, 64, 256)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])

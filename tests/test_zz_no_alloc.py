@@ -6,7 +6,9 @@ allocation) use ctr_pair_sum_fp32_static, whose scratch is a fixed device
 array.  Its output must equal the dense pair part of ctr_ibim_matvec's FP32
 operator (the matvec minus its diagonal and its correction) within the FP32
 operator tolerance of the parity tests, on two calls in a row with different
-densities (the second call must not see the first call's scratch).
+densities (the second call must not see the first call's scratch), and the
+second call must leave the device's free memory unchanged (the first call may
+load the library's device code, which brings the fixed array with it).
 """
 import ctypes
 import math
@@ -55,6 +57,7 @@ def test_static_scratch_pair_sum_matches_matvec():
     d_excl = torch.tensor(excl, device="cuda")
     scale = h * h * h / (4.0 * math.pi)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    calls = []
     for seed in (21, 22):                       # two calls in a row, different densities
         x = syn.random_density(M, seed=seed, smooth_points=P)
         src = np.empty((M, 8), dtype=np.float32)
@@ -64,10 +67,18 @@ def test_static_scratch_pair_sum_matches_matvec():
         src[:, 7] = scale * W * x[M:]
         d_src = torch.tensor(src.ravel(), device="cuda")
         out = torch.full((2 * M,), float("nan"), dtype=torch.float64, device="cuda")
+        calls.append((x, d_src, out))           # every caller buffer exists before the first call
+    torch.cuda.synchronize()
+    free = []
+    for x, d_src, out in calls:
         st = L.ctr_pair_sum_fp32_static(M, ctypes.c_void_p(d_src.data_ptr()), ctypes.c_void_p(d_ptr.data_ptr()),
                                         ctypes.c_void_p(d_excl.data_ptr()), prob.eps_out / prob.eps_in, prob.kappa,
                                         ctypes.c_void_p(out.data_ptr()), stream)
         assert st == 0, L.ctr_last_error()
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    assert free[1] == free[0], f"the second call changed the free device memory by {free[0] - free[1]} bytes"
+    for x, d_src, out in calls:
         got = out.cpu().numpy()
         ref = _pair_part_from_matvec(G, ctr, x, h, prob.kappa, prob.eps_in, prob.eps_out)
         assert np.all(np.isfinite(got))
