@@ -56,10 +56,13 @@ OPS_FP64 = {"one": 69, "sym": 69}
 TRAFFIC = {"profile": "profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt", "h": 0.05,
            "sources": None, "fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
 KERNEL_SOURCES = ("paper_2210_03699_gb300/csrc/pairkern.cuh", "paper_2210_03699_gb300/csrc/schedule.cu")
-# Treecode far field (FP32 charges): FMA-pipe lane operations per proxy evaluation counted from the kernel
-# source (tree.cuh, k_tree_far2: 1 sub, 6 fma, 7 mul; an f32x2 instruction does two), plus 2 SFU operations
-# (rsqrt, ex2).
+# Treecode far field of the FP32 operator (FP32 charges): FMA-pipe lane operations per proxy evaluation
+# counted from the kernel source (tree.cuh, k_tree_far2: 1 sub, 6 fma, 7 mul; an f32x2 instruction does
+# two), plus 2 SFU operations (rsqrt, ex2).  The float-float operator's far field (k_tree_far_ff): 196
+# FP32-pipe operations per evaluation (float-float differences, squares, dot products, rsqrt by one Newton
+# step, the table exponential, the two charge combinations and accumulations), 1 SFU operation.
 OPS_FAR = 14
+OPS_FAR_DF = 196
 SFU_FAR = 2
 
 
@@ -101,8 +104,7 @@ def parse():
                          "float-float and two FP64 operator applications of the ellipsoid at --h (the profiling "
                          "case); tree: the solve step with the far-field treecode on the ellipsoid at --tree-h")
     ap.add_argument("--tree-h", type=float, default=0.025, help="tree mode: grid spacing (0.025: ~714k nodes)")
-    ap.add_argument("--tree-tol", type=float, default=1e-6,
-                    help="tree mode: solve tolerance (the FP32 far field sets a floor near 2e-7)")
+    ap.add_argument("--tree-tol", type=float, default=1e-10, help="tree mode: solve tolerance")
     ap.add_argument("--tree-direct", action="store_true",
                     help="tree mode: also time the direct-sum applications at the same size")
     ap.add_argument("--oracle-solves", action="store_true",
@@ -350,7 +352,11 @@ def run_batch(args, ctr):
         g.solve(device=True)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    R, V, U = ctr.tuning_info()
+    shapes = {}
+    for g in systems:
+        t = g.pair_tuning(ctr.FP32_REFINE)
+        key = f"block {t['block_targets']}, tile {t['tile']}, chunk {t['chunk']}, unroll {t['unroll']}"
+        shapes[key] = shapes.get(key, 0) + 1
     line = {"metric": "CTR-IBIM batched pair-interactions/s", "value": pairs / t_batch, "unit": "pair-interactions/s",
             "n_gpus": 1, "steps": 1, "higher_is_better": True, "dtype": "f32 pairs + f64", "data": "synthetic",
             "config": {"workload": f"{len(probs)} random-walk SES molecules, atoms log-uniform in 20-{args.max_atoms}, "
@@ -360,7 +366,7 @@ def run_batch(args, ctr):
             "batch_s": t_batch, "solves_per_s": len(probs) / t_batch, "sequential_s": t_seq,
             "speedup_vs_sequential": t_seq / t_batch, "all_converged": all(i.converged for _, _, i in out),
             "max_iterations": int(max(i.iterations for _, _, i in out)),
-            "autotuned_fp32_variant": {"targets_per_thread": R, "chunk": V, "unroll": U}, "gpu_launches": int(launches)}
+            "fp32_variants": shapes, "gpu_launches": int(launches)}
     for g in systems:
         g.close()
     print(json.dumps(line), flush=True)
@@ -585,15 +591,20 @@ def run_tree(args, ctr, world):
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {ops} lane ops per "
                                    f"one-sided pair; measured FFMA probe {rate_ffma:.4g}/s",
                      "t_ms": t_near * 1e3, "pairs": near, "step_share": n_app[pr] * t_near / step_s})
-        kern.append({"bound": "alu", "kernel": f"k_tree_mom + k_tree_momred + k_tree_far2<"
-                                               f"{'2, 256' if tag == 'fp32' else '1, 128'}> (treecode far field, "
-                                               f"{tag} blocks)",
-                     "achieved": far / t_far if t_far > 0 else None, "peak": far_peak,
+        if tag == "fp32":
+            fname, fpeak = "k_tree_mom + k_tree_momred + k_tree_far2<2, 256> (treecode far field, FP32 charges)", far_peak
+            fbasis = (f"min({sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {OPS_FAR} lane ops, SFU: "
+                      f"1/(1/ex2 + 1/rsqrt) with the measured probes {rate_ex2:.4g}/s, {rate_rsq:.4g}/s) per proxy "
+                      f"evaluation")
+        else:
+            fname = "k_tree_mom<double> + k_tree_momred<double> + k_tree_far_ff<2, 128> (treecode far field, float-float)"
+            fpeak = rate_units / OPS_FAR_DF
+            fbasis = (f"{sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {OPS_FAR_DF} FP32-pipe ops per "
+                      f"float-float proxy evaluation")
+        kern.append({"bound": "alu", "kernel": fname,
+                     "achieved": far / t_far if t_far > 0 else None, "peak": fpeak,
                      "unit": "proxy evaluations/s",
-                     "frac": far / t_far / far_peak if t_far > 0 else None, "traffic": None,
-                     "peak_basis": f"min({sms} SMs x 128 FP32 lanes x {f_max / 1e6:.0f} MHz / {OPS_FAR} lane ops, "
-                                   f"SFU: 1/(1/ex2 + 1/rsqrt) with the measured probes {rate_ex2:.4g}/s, "
-                                   f"{rate_rsq:.4g}/s) per proxy evaluation",
+                     "frac": far / t_far / fpeak if t_far > 0 else None, "traffic": None, "peak_basis": fbasis,
                      "t_ms": t_far * 1e3, "evaluations": far, "step_share": n_app[pr] * t_far / step_s})
     kern.sort(key=lambda k: -k["step_share"])
     e2e = None
@@ -711,6 +722,7 @@ def main():
             torch.cuda.synchronize()
             t_mv[pr] = e0.elapsed_time(e1) * 1e-3 / reps
             sched[pr] = G.pair_schedule(pr)
+            sched[pr]["shape"] = G.pair_tuning(pr)
         Mk = G.M
         # accuracy of the timed step's result: the residual recomputed with the float-float operator
         g = torch.empty(2 * Mk, dtype=torch.float64, device="cuda")
@@ -750,7 +762,7 @@ def main():
                                   f"per symmetric pair evaluation (both orientations)",
                 "t_matvec_ms": t_mv[pr] * 1e3, "one_sided_pairs": sc["one_sided_pairs"],
                 "symmetric_pairs": sc["symmetric_pairs"], "items": sc["items"],
-                "partial_bytes": sc["partial_bytes"], "applications_per_step": n_app,
+                "partial_bytes": sc["partial_bytes"], "kernel_shape": sc["shape"], "applications_per_step": n_app,
                 "step_share": n_app * t_mv[pr] / step_s}
 
     if prec == ctr.FP32_REFINE:

@@ -85,8 +85,8 @@ enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
  *       separated from it (theta |c_B - c_C| > r_B + r_C on the integer boxes
  *       widened by ceil(eps/h) grid units, decided exactly), that holds none of
  *       the block's correction nodes and that has more than (degree+1)^3 nodes
- *       (a sixteenth of that for the float-float arithmetic, whose direct pairs
- *       cost about 16 FP32 proxy evaluations each)
+ *       (half of that for the float-float arithmetic, whose direct pairs cost
+ *       about two of its float-float proxy evaluations each)
  *       is replaced by (degree+1)^3 tensor Chebyshev points on the tight box of
  *       its points P carrying interpolated charges (barycentric Lagrange
  *       interpolation of the kernels' source variable, d/dn_y on the basis);
@@ -94,12 +94,15 @@ enum { CTR_METHOD_HYB = 0, CTR_METHOD_KREG = 1 };
  *       exactly.  The error against the direct sum falls geometrically with the
  *       degree (about 6e-8 relative at degree 10, theta 0.8; the CTR_FP32_REFINE
  *       operator, which only drives the inner GMRES, uses its own degree and
- *       theta, 6 and 0.9 by default: about 7e-6).  The far field is
- *       FP32 in the CTR_FP32_REFINE and CTR_DF64 arithmetics and FP64 in
- *       CTR_FP64; the direct part keeps the arithmetic's pair kernels.  So a
- *       CTR_FP32_REFINE solve on the treecode reaches a relative residual near
- *       1e-7 at best (its float-float residual has an FP32 far field): use a
- *       tolerance of about 1e-6; CTR_FP64 solves have no such floor.
+ *       theta, 6 and 0.9 by default: about 7e-6).  The far field has the
+ *       arithmetic of its operator: FP32 charges and evaluations for
+ *       CTR_FP32_REFINE, FP64 charges and float-float evaluations for CTR_DF64,
+ *       FP64 for CTR_FP64; the direct part keeps the arithmetic's pair kernels.
+ *       The CTR_DF64 and CTR_FP64 treecode operators are consistent to their
+ *       arithmetic's rounding, so refinement reaches tolerances like 1e-10 (the
+ *       solution is then that of the treecode operator, within the
+ *       interpolation error of the direct sum's).  A CTR_FP32_REFINE treecode
+ *       solve forms every refinement residual in full (no residual update).
  */
 enum { CTR_FARFIELD_DIRECT = 0, CTR_FARFIELD_TREECODE = 1 };
 
@@ -108,7 +111,8 @@ enum { CTR_FARFIELD_DIRECT = 0, CTR_FARFIELD_TREECODE = 1 };
  * (x_{k+1} = x_k + d_k, d_k from an FP32-operator GMRES solve of A d = r_k):
  *   CTR_RESIDUAL_UPDATE  r_1 = g - A x_1 in the residual arithmetic (opt.residual);
  *       every later r_{k+1} = r_k - A d_k with the FP32-pair operator, once
- *       |r_k| <= 1e-4 |g| (before that, g - A x again).  A is linear, so this is
+ *       |r_k| <= 1e-4 |g| (before that, g - A x again; always with the treecode,
+ *       whose FP32 operator is also an approximation).  A is linear, so this is
  *       g - A x_{k+1} with the FP32 operator's error (about 1e-7 relative,
  *       measured) applied to the small correction d_k only: for |r_k| ~ 1e-5 |g|
  *       the residual is off by about 1e-12 |g|.  One application of the
@@ -131,8 +135,7 @@ typedef struct {
     int max_iter;          /* limit on GMRES iterations (all cycles, all refinements); <= 0: 400 */
     int max_refine;        /* limit on refinement steps (CTR_FP32_REFINE); <= 0 selects 10 */
     double inner_tol;      /* relative tolerance of each FP32 GMRES solve; <= 0 selects 1e-5 */
-    int tile_targets;      /* reserved, ignored: the pair schedules use 4 targets per thread
-                              (FP32) and 1 (float-float, FP64) */
+    int tile_targets;      /* reserved, ignored */
     int residual;          /* pair arithmetic of the refinement residual r = g - A x:
                               CTR_DF64 (the default of ctr_default_options) or CTR_FP64 */
     int method;            /* CTR_METHOD_HYB (default) or CTR_METHOD_KREG */
@@ -144,6 +147,16 @@ typedef struct {
                               rounding is ~2e-5); <= 0 selects 6 */
     double tree_theta_fp32;/* theta of the CTR_FP32_REFINE operator; <= 0 selects 0.9 */
     int residual_mode;     /* CTR_RESIDUAL_UPDATE (default) or CTR_RESIDUAL_FULL (see above) */
+    int fp32_block;        /* targets per block of the FP32 pair kernel, 512 or 1024; 0: tuned */
+    int fp32_tile;         /* sources per shared-memory tile of the FP32 pair kernel, 128 or 256; 0: tuned.
+                              With both 0 the setup picks the FP32 kernel variant (block, tile,
+                              transposed chunk, unroll) by timing every variant on the system itself,
+                              once per device and size bucket (floor(log2 M)) per process, and keeps
+                              the choice for later systems of that bucket (see ctr_ibim_pair_tuning).
+                              Block and tile fix the FP32 summation order, so a system's results are
+                              the same alone and in any batch of the process; another process may
+                              time differently and choose another variant (results then differ
+                              within the FP32 operator's rounding).  Treecode handles use 1024, 256. */
 } ctr_options;
 
 typedef struct {
@@ -277,7 +290,7 @@ int ctr_ibim_time_operator(ctr_ibim* sys, int precision, int reps, double* pack_
  * direct), leaf (>= 1), target block size (>= 1) and min_far, the node count a
  * well-separated cluster must exceed to be approximated (<= 0 selects
  * (degree+1)^3; a handle uses (degree+1)^3 for its FP32 and FP64 blocks and
- * (degree+1)^3 / 16 for its float-float blocks).  Outputs (host, any may
+ * (degree+1)^3 / 2 for its float-float blocks).  Outputs (host, any may
  * be NULL): perm (M), n_near_ranges, n_far, near_ptr (nb + 1 with
  * nb = ceil(M / block)), near_rng (2 per range: [begin, end) tree positions),
  * far_ptr (nb + 1), far_begin and far_end (n_far each: the position range of
@@ -500,14 +513,23 @@ const char* ctr_last_error(void);
 int64_t ctr_kernel_launches(void);
 
 /*
- * The FP32 pair-kernel variant the solver's autotuner chose most recently in
- * this process: targets per thread (fixed, 4), sources per transposed chunk of
- * the symmetric items (4 or 8) and unroll of the chunk loop (1 or 2); all
- * 0 before the first tuned solve.  The tuner times each variant once on a
- * solve's real work items at its first step (cached per device and
- * problem-size bucket); variants never change the results.
+ * The FP32 pair-kernel variant the most recent setup in this process took from
+ * its tuning (timed, or from the tuning cache; see ctr_options.fp32_block):
+ * targets per thread (2 or 4), sources
+ * per transposed chunk of the symmetric items (4 or 8) and unroll of the
+ * chunk loop (1 or 2); all 0 before the first tuning.
  */
 int ctr_tuning_info(int* targets_per_thread, int* chunk, int* unroll);
+
+/*
+ * The pair-kernel shape of one arithmetic (precision) of a handle's schedule:
+ * targets per block, sources per shared-memory tile, sources per transposed
+ * chunk and unroll of the chunk loop (outputs may be NULL).  CTR_FP32_REFINE:
+ * the tuned or requested variant; CTR_DF64: 256, 128, 8, 1 and CTR_FP64:
+ * 256, 128, 8, 1 (fixed).
+ */
+int ctr_ibim_pair_tuning(const ctr_ibim* sys, int precision, int* block_targets, int* tile, int* chunk,
+                         int* unroll);
 
 #ifdef __cplusplus
 }

@@ -55,7 +55,8 @@ class _Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("tile_targets", ctypes.c_int), ("residual", ctypes.c_int),
                 ("method", ctypes.c_int), ("farfield", ctypes.c_int), ("tree_degree", ctypes.c_int),
                 ("tree_theta", ctypes.c_double), ("tree_leaf", ctypes.c_int), ("tree_degree_fp32", ctypes.c_int),
-                ("tree_theta_fp32", ctypes.c_double), ("residual_mode", ctypes.c_int)]
+                ("tree_theta_fp32", ctypes.c_double), ("residual_mode", ctypes.c_int), ("fp32_block", ctypes.c_int),
+                ("fp32_tile", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -98,12 +99,14 @@ class Options:
     tree_degree_fp32: int = 6
     tree_theta_fp32: float = 0.9
     residual_mode: int = RESIDUAL_UPDATE
+    fp32_block: int = 0
+    fp32_tile: int = 0
 
     def _c(self) -> _Options:
         return _Options(self.tube_halfwidth, self.precision, self.tol, self.restart, self.max_iter,
                         self.max_refine, self.inner_tol, self.tile_targets, self.residual, self.method,
                         self.farfield, self.tree_degree, self.tree_theta, self.tree_leaf, self.tree_degree_fp32,
-                        self.tree_theta_fp32, self.residual_mode)
+                        self.tree_theta_fp32, self.residual_mode, self.fp32_block, self.fp32_tile)
 
 
 @dataclasses.dataclass
@@ -168,6 +171,7 @@ def _load():
         "ctr_kernel_launches": (ctypes.c_int64, []),
         "ctr_ibim_pair_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 4),
         "ctr_tuning_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)] * 3),
+        "ctr_ibim_pair_tuning": (ctypes.c_int, [P, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4),
         "ctr_ibim_farfield_info": (ctypes.c_int, [P, ctypes.c_int, P] + [_I64] * 4),
         "ctr_ibim_time_operator": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int] + [_D] * 4),
         "ctr_farfield_plan": (ctypes.c_int, [ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -315,6 +319,12 @@ class CtrIbim:
         _check(lib.ctr_ibim_pair_schedule(self._h, int(precision), *[ctypes.byref(x) for x in v]))
         return {"one_sided_pairs": v[0].value, "symmetric_pairs": v[1].value, "items": v[2].value,
                 "partial_bytes": v[3].value}
+
+    def pair_tuning(self, precision: int = FP32_REFINE) -> dict:
+        """Pair-kernel shape of one arithmetic's schedule (see ctr_ibim_pair_tuning)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib.ctr_ibim_pair_tuning(self._h, int(precision), *[ctypes.byref(x) for x in v]))
+        return {"block_targets": v[0].value, "tile": v[1].value, "chunk": v[2].value, "unroll": v[3].value}
 
     def farfield_info(self, precision: int = FP32_REFINE) -> dict:
         """The treecode of this handle for one arithmetic (see ctr_ibim_farfield_info)."""

@@ -82,6 +82,8 @@ void ctr_default_options(ctr_options* o) {
     o->tree_degree_fp32 = 6;
     o->tree_theta_fp32 = 0.9;
     o->residual_mode = CTR_RESIDUAL_UPDATE;
+    o->fp32_block = 0;
+    o->fp32_tile = 0;
 }
 
 const char* ctr_status_string(int st) {
@@ -107,7 +109,23 @@ int64_t ctr_kernel_launches(void) { return g_launches.load(std::memory_order_rel
 
 int ctr_tuning_info(int* targets_per_thread, int* chunk, int* unroll) {
     if (!targets_per_thread || !chunk || !unroll) return fail(CTR_ERR_INVALID, "NULL argument");
-    last_tuning(targets_per_thread, chunk, unroll);
+    const int v = last_fp32_variant();
+    *targets_per_thread = v < 0 ? 0 : pk::kVar32[v].R * pk::Fp32x2Policy::kPack;
+    *chunk = v < 0 ? 0 : pk::kVar32[v].V;
+    *unroll = v < 0 ? 0 : pk::kVar32[v].U;
+    return CTR_OK;
+}
+
+int ctr_ibim_pair_tuning(const ctr_ibim* s, int precision, int* block_targets, int* tile, int* chunk, int* unroll) {
+    if (!s) return fail(CTR_ERR_INVALID, "NULL handle");
+    if (precision != CTR_FP32_REFINE && precision != CTR_DF64 && precision != CTR_FP64)
+        return fail(CTR_ERR_INVALID, "precision");
+    const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
+    const ctr::PairSchedule& p = s->sched[pol];
+    if (block_targets) *block_targets = p.BS;
+    if (tile) *tile = p.tile;
+    if (chunk) *chunk = pol == 0 ? pk::kVar32[p.var].V : (pol == 1 ? pk::kChunkDf : pk::kChunk64);
+    if (unroll) *unroll = pol == 0 ? pk::kVar32[p.var].U : 1;
     return CTR_OK;
 }
 

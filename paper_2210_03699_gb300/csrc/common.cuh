@@ -120,6 +120,7 @@ struct PairItem {
 // The pair schedule of one system for one pair arithmetic: items (device list
 // sorted by decreasing cost; host copy and costs kept for the engine).
 struct PairSchedule {
+    int var = 0;          // kernel variant (FP32: index into pk::kVar32; 0 for the fixed shapes)
     int R = 1;            // targets per thread
     int BS = 256;         // nodes per target block
     int tile = 128;       // sources per shared-memory tile
@@ -145,8 +146,8 @@ struct MomChunk {
 };
 
 // Device view of a handle's far-field data, per pair arithmetic p (0 FP32,
-// 1 float-float, 2 FP64; charges and far sums are FP32 for p < 2, FP64 for p = 2;
-// each arithmetic has its own interpolation degree n = n1 - 1).
+// 1 float-float, 2 FP64; moments and charges are FP32 for p = 0 and FP64 for p = 1, 2, far sums
+// FP32, float-float and FP64; each arithmetic has its own interpolation degree n = n1 - 1).
 struct TreeView {
     int on = 0;
     int M = 0;
@@ -162,6 +163,7 @@ struct TreeView {
     void* mom[3] = {};                    // per far cluster: Q0[np], Qk[np], Qk'[np]
     const FarItem* far[3] = {};
     const int32_t* flist[3] = {};         // far cluster (compact index) lists
+    const float2* exp_tab = nullptr;      // float-float e^{-x} tables of the device (float-float far field)
     const float4* src32 = nullptr;        // the handle's packed sources, tree order
     const float4* srcdf = nullptr;
     const double4* src64 = nullptr;
@@ -264,6 +266,9 @@ int64_t tree_bytes(const ctr_ibim* s);
 int build_schedules(ctr_ibim* s, const int slots[3]);
 // the handle's exact node accumulators, allocated and cleared (pairsum.cu)
 int alloc_accumulators(ctr_ibim* s);
+// the weights a = h^3 W x1 / (4 pi), b = h^3 W x2 / (4 pi) of x (2M doubles, device) into the packed
+// sources of one arithmetic (pairsum.cu)
+int pack_sources(ctr_ibim* s, const double* d_x, int precision);
 int apply_operator(ctr_ibim* s, const double* d_x, double* d_y, int precision);
 int apply_operator_timed(ctr_ibim* s, const double* d_x, double* d_y, int precision, cudaEvent_t* ev);
 // krylov.cu: solver workspace

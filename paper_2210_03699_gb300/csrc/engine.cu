@@ -381,8 +381,10 @@ __global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
     if (q < cap) out[q] = S[q].stat;
 }
 
+constexpr int kNV = kNumVar32;   // work lists per arithmetic
+
 template <typename Policy, int R, int V, int U, bool kShared>
-int launch_persistent_k(Engine* e, int pol, int half, int prec) {
+int launch_persistent_k(Engine* e, int pol, int var, int half, int prec) {
     const size_t smem = pair_smem_bytes<Policy>();
     static int per_dev[64] = {0};   // resident blocks of this instantiation, per device (attribute set there)
     int dev = 0;
@@ -398,18 +400,26 @@ int launch_persistent_k(Engine* e, int pol, int half, int prec) {
                                                                    smem));
         per_sm = std::max(1, b);
     }
+    const int list = pol * kNV + var;
     k_pairs<Policy, R, V, U, kShared><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
-        e->slots.as<SlotDev>(), e->items[pol].as<int2>(), e->n_items.as<int>() + pol,
-        e->counters.as<int>() + 2 * pol + half, half, prec, pol, e->exp_tab, e->err.as<int>(), e->kc_val[pol]);
+        e->slots.as<SlotDev>(), e->items[pol][var].as<int2>(), e->n_items.as<int>() + list,
+        e->counters.as<int>() + 2 * list + half, half, prec, pol, e->exp_tab, e->err.as<int>(), e->kc_val[pol]);
     CTR_LAUNCHED();
     return CTR_OK;
 }
 
 template <typename Policy, int R, int V, int U>
-int launch_persistent(Engine* e, int pol, int half, int prec) {
-    return e->kc_shared[pol] ? launch_persistent_k<Policy, R, V, U, true>(e, pol, half, prec)
-                             : launch_persistent_k<Policy, R, V, U, false>(e, pol, half, prec);
+int launch_persistent(Engine* e, int pol, int var, int half, int prec) {
+    return e->kc_shared[pol] ? launch_persistent_k<Policy, R, V, U, true>(e, pol, var, half, prec)
+                             : launch_persistent_k<Policy, R, V, U, false>(e, pol, var, half, prec);
 }
+
+struct PersistentRun {
+    Engine* e;
+    int var, half;
+    template <typename P, int R, int V, int U>
+    int run() const { return launch_persistent<P, R, V, U>(e, 0, var, half, CTR_FP32_REFINE); }
+};
 
 // Treecode entries of a slot in this half's arithmetic (filtered by the slot's state at run time).
 struct EngineTreeAcc {
@@ -434,7 +444,13 @@ int launch_tree_engine(Engine* e, int pol, int half, int prec) {
     k_tree_momred<Real, EngineTreeAcc><<<4 * e->sms, kThreads, 0, e->stream>>>(acc, e->tree_ent[pol][1].as<int2>(),
                                                                              cnt + 1, pol);
     CTR_LAUNCHED();
-    if constexpr (sizeof(Real) == 4) {
+    if constexpr (sizeof(Real) == 8 && R == kTreeR[1] && NT == kTreeNT[1]) {   // float-float far field
+        auto kern = k_tree_far_ff<R, NT, EngineTreeAcc>;
+        const int smem = (int)tree_farff_smem(std::max(1, e->tree_np[pol]));   // the largest proxy count admitted
+        const int per_sm = far_per_sm(kern, NT, smem, (int)tree_farff_smem(), cache);
+        if (per_sm < 0) return per_sm;
+        kern<<<per_sm * e->sms, NT, smem, e->stream>>>(acc, e->tree_ent[pol][2].as<int2>(), cnt + 2, ctr + 1);
+    } else if constexpr (sizeof(Real) == 4) {
         auto kern = k_tree_far2<R / 2, NT, EngineTreeAcc>;
         const int smem = (int)tree_far2_smem(std::max(1, e->tree_np[pol]));   // the largest proxy count admitted
         const int per_sm = far_per_sm(kern, NT, smem, (int)tree_far2_smem(), cache);
@@ -454,40 +470,22 @@ int launch_tree_engine(Engine* e, int pol, int half, int prec) {
 int launch_trees(Engine* e, int half) {
     if (!e->any_tree) return CTR_OK;
     CTR_TRY((launch_tree_engine<float, kTreeR[0], kTreeNT[0]>(e, 0, half, CTR_FP32_REFINE)));
-    CTR_TRY((launch_tree_engine<float, kTreeR[1], kTreeNT[1]>(e, 1, half, CTR_DF64)));
+    CTR_TRY((launch_tree_engine<double, kTreeR[1], kTreeNT[1]>(e, 1, half, CTR_DF64)));
     CTR_TRY((launch_tree_engine<double, kTreeR[2], kTreeNT[2]>(e, 2, half, CTR_FP64)));
     return CTR_OK;
 }
 
+// One persistent FP32 launch per kernel variant among the occupied slots
 int launch_fp32(Engine* e, int half) {
-    switch (e->var32) {
-        case 1: return launch_persistent<Fp32x2Policy, kR32, 4, 1>(e, 0, half, CTR_FP32_REFINE);
-        case 2: return launch_persistent<Fp32x2Policy, kR32, 8, 2>(e, 0, half, CTR_FP32_REFINE);
-        case 3: return launch_persistent<Fp32x2Policy, kR32, 4, 2>(e, 0, half, CTR_FP32_REFINE);
-        default: return launch_persistent<Fp32x2Policy, kR32, 8, 1>(e, 0, half, CTR_FP32_REFINE);
-    }
+    for (int v = 0; v < kNV; ++v)
+        if (e->var_used[v]) CTR_TRY(with_var32(v, PersistentRun{e, v, half}));
+    return CTR_OK;
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 static int policy_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
-
-static std::atomic<int> g_last_var{-1};
-
-void last_tuning(int* R, int* chunk, int* unroll) {
-    const int v = g_last_var.load();
-    *R = v < 0 ? 0 : kR32 * Fp32x2Policy::kPack;
-    *chunk = v < 0 ? 0 : kVariants32[v][0];
-    *unroll = v < 0 ? 0 : kVariants32[v][1];
-}
-
-int engine_fp32_variant(const Engine* e, int* R, int* chunk, int* unroll) {
-    *R = kR32 * Fp32x2Policy::kPack;
-    *chunk = kVariants32[e->var32][0];
-    *unroll = kVariants32[e->var32][1];
-    return CTR_OK;
-}
 
 Engine::~Engine() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -515,15 +513,15 @@ int engine_create(int device, int cap, Engine** out) {
     int st;
     if ((st = e->slots.alloc(sizeof(SlotDev) * cap)) < 0) return bad(st);
     if ((st = e->stats.alloc(sizeof(SlotStat) * cap)) < 0) return bad(st);
-    if ((st = e->n_items.alloc(sizeof(int) * 4)) < 0) return bad(st);
-    if ((st = e->counters.alloc(sizeof(int) * 8)) < 0) return bad(st);
+    if ((st = e->n_items.alloc(sizeof(int) * 3 * kNV)) < 0) return bad(st);
+    if ((st = e->counters.alloc(sizeof(int) * 2 * 3 * kNV)) < 0) return bad(st);
     if ((st = e->tree_cnt.alloc(sizeof(int) * 9)) < 0) return bad(st);
     if ((st = e->tree_counters.alloc(sizeof(int) * 12)) < 0) return bad(st);
     if (cudaMemsetAsync(e->tree_cnt.p, 0, sizeof(int) * 9, stream) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "memset"));
     if ((st = e->err.alloc(sizeof(int))) < 0) return bad(st);
     if (cudaMemsetAsync(e->err.p, 0, sizeof(int), stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "memset"));
-    if (cudaMemsetAsync(e->n_items.p, 0, sizeof(int) * 4, stream) != cudaSuccess)
+    if (cudaMemsetAsync(e->n_items.p, 0, sizeof(int) * 3 * kNV, stream) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "memset"));
     for (int q = 0; q < cap; ++q) e->host[q].stat.state = kSlotEmpty;
     if (cudaMemcpyAsync(e->slots.p, e->host.data(), sizeof(SlotDev) * cap, cudaMemcpyHostToDevice, stream) !=
@@ -533,8 +531,6 @@ int engine_create(int device, int cap, Engine** out) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "attribute"));
     e->sms = sms;
-    e->var32 = fp32_variant();
-    for (int p = 0; p < 3; ++p) e->item_cap[p] = 0;
     if ((st = exp_table(device, &e->exp_tab)) < 0) return bad(st);
     if (cudaStreamSynchronize(stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "sync"));
     *out = e;
@@ -595,24 +591,27 @@ static int rebuild_tree_items(Engine* e) {
     return CTR_OK;
 }
 
-// Rebuild the three work lists (every item of every occupied slot's schedule; each entry is filtered
-// by its slot's state at run time), sorted by decreasing cost for the atomic-counter scheduler.
+// Rebuild the work lists (every item of every occupied slot's schedule, one list per arithmetic and
+// kernel variant; each entry is filtered by its slot's state at run time), sorted by decreasing cost
+// for the atomic-counter scheduler.
 static int rebuild_items(Engine* e) {
+    bool used[kNV] = {};
     for (int p = 0; p < 3; ++p) {
         struct It {
             int2 v;
             double cost;
         };
-        std::vector<It> list;
+        std::vector<It> list[kNV];
         for (int q = 0; q < e->cap; ++q) {
             if (!e->owner[q]) continue;
             const SlotDev& s = e->host[q];
             const bool uses = (policy_index(s.inner_prec) == p) || (policy_index(s.res_prec) == p);
             if (!uses) continue;
             const PairSchedule& sc = e->owner[q]->sched[p];
-            for (size_t k = 0; k < sc.items.size(); ++k) list.push_back(It{make_int2(q, (int)k), sc.cost[k]});
+            const int var = (p == 0) ? sc.var : 0;
+            if (p == 0) used[var] = true;
+            for (size_t k = 0; k < sc.items.size(); ++k) list[var].push_back(It{make_int2(q, (int)k), sc.cost[k]});
         }
-        std::stable_sort(list.begin(), list.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
         // one set of pair constants for every slot of this arithmetic: pass it as a launch parameter
         bool shared = true, any = false;
         PairConsts val{};
@@ -635,21 +634,30 @@ static int rebuild_items(Engine* e) {
             e->kc_val[p] = val;
             e->graph_dirty = true;   // the captured launches carry the constants
         }
-        std::vector<int2> v(list.size());
-        for (size_t i = 0; i < list.size(); ++i) v[i] = list[i].v;
-        if ((int64_t)v.size() > e->item_cap[p]) {
-            const int64_t capn = std::max<int64_t>(1024, (int64_t)v.size() * 2);
-            CTR_TRY(e->items[p].alloc(sizeof(int2) * capn));
-            e->item_cap[p] = capn;
-            e->graph_dirty = true;   // the item buffer moved
-        }
-        if (!v.empty())
-            CTR_CUDA_TRY(cudaMemcpyAsync(e->items[p].p, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice,
+        for (int v = 0; v < kNV; ++v) {
+            std::stable_sort(list[v].begin(), list[v].end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+            std::vector<int2> ent(list[v].size());
+            for (size_t i = 0; i < ent.size(); ++i) ent[i] = list[v][i].v;
+            if ((int64_t)ent.size() > e->item_cap[p][v]) {
+                const int64_t capn = std::max<int64_t>(1024, (int64_t)ent.size() * 2);
+                CTR_TRY(e->items[p][v].alloc(sizeof(int2) * capn));
+                e->item_cap[p][v] = capn;
+                e->graph_dirty = true;   // the item buffer moved
+            }
+            if (!ent.empty())
+                CTR_CUDA_TRY(cudaMemcpyAsync(e->items[p][v].p, ent.data(), sizeof(int2) * ent.size(),
+                                             cudaMemcpyHostToDevice, e->stream));
+            const int cnt = (int)ent.size();
+            CTR_CUDA_TRY(cudaMemcpyAsync(e->n_items.as<int>() + p * kNV + v, &cnt, sizeof(int), cudaMemcpyHostToDevice,
                                          e->stream));
-        const int cnt = (int)v.size();
-        CTR_CUDA_TRY(cudaMemcpyAsync(e->n_items.as<int>() + p, &cnt, sizeof(int), cudaMemcpyHostToDevice, e->stream));
+        }
         CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
     }
+    for (int v = 0; v < kNV; ++v)
+        if (used[v] != e->var_used[v]) {
+            e->var_used[v] = used[v];
+            e->graph_dirty = true;   // the step gains or loses a variant's launches
+        }
     return rebuild_tree_items(e);
 }
 
@@ -664,11 +672,11 @@ static int enqueue_step(Engine* e) {
     // ---- inner half: one Arnoldi iteration
     k_prep_inner<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
-    CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, st));
+    CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 2 * 3 * kNV, st));
     if (e->any_tree) CTR_CUDA_TRY(cudaMemsetAsync(e->tree_counters.p, 0, sizeof(int) * 12, st));
     CTR_TRY(launch_fp32(e, 0));
-    CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, CTR_DF64)));
-    CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, CTR_FP64)));
+    CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, 0, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, 0, CTR_FP64)));
     CTR_TRY(launch_trees(e, 0));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 0);
     CTR_LAUNCHED();
@@ -696,8 +704,8 @@ static int enqueue_step(Engine* e) {
     k_update_x<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
     CTR_TRY(launch_fp32(e, 1));
-    CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 1, CTR_DF64)));
-    CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 1, CTR_FP64)));
+    CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, 1, CTR_DF64)));
+    CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, 1, CTR_FP64)));
     CTR_TRY(launch_trees(e, 1));
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 1);
     CTR_LAUNCHED();
@@ -779,7 +787,9 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     d.refine = (s->opt.precision == CTR_FP32_REFINE) ? 1 : 0;
     d.inner_prec = s->opt.precision;
     d.res_prec = d.refine ? s->opt.residual : s->opt.precision;
-    d.res_update = (d.refine && s->opt.residual_mode == CTR_RESIDUAL_UPDATE) ? 1 : 0;
+    // a treecode handle's FP32 operator carries its own approximation error (degree 6): its refinement
+    // residuals are always formed in full with the residual arithmetic
+    d.res_update = (d.refine && s->opt.residual_mode == CTR_RESIDUAL_UPDATE && !s->tree) ? 1 : 0;
     d.upd = 0;
     CTR_TRY(pair_consts(s, true, &d.kc));
     for (int p = 0; p < 3; ++p) {
@@ -872,73 +882,7 @@ int engine_retire(Engine* e, int q, ctr_solve_info* info) {
     return st.numeric_error ? fail(CTR_ERR_NUMERIC, "non-finite residual") : CTR_OK;
 }
 
-// Time one FP32 persistent launch per variant over the current work items and keep the fastest.
-// Variants differ only in the source chunk of the transposed sums and in loop unrolling: every
-// sum is formed in the same order, so results are identical whichever is chosen.  Cached per
-// device and size bucket; the choice also serves the single-system launches of the process.
-static int engine_autotune(Engine* e) {
-    static std::mutex mu;
-    static std::map<std::pair<int, int>, int> cache;
-    double pairs = 0.0;
-    bool fp32 = false;
-    for (int q = 0; q < e->cap; ++q)
-        if (e->owner[q] && e->host[q].inner_prec == CTR_FP32_REFINE) {
-            pairs += (double)e->host[q].M * (double)e->host[q].M;
-            fp32 = true;
-        }
-    e->tuned = true;
-    if (!fp32) return CTR_OK;
-    const int bucket = (int)std::floor(std::log2(std::max(pairs, 1.0)));
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = cache.find({e->device, bucket});
-        if (it != cache.end()) {
-            g_last_var = it->second;
-            set_fp32_variant(it->second);
-            if (it->second != e->var32) {
-                e->var32 = it->second;
-                e->graph_dirty = true;
-            }
-            return CTR_OK;
-        }
-    }
-    cudaEvent_t a, b;
-    CTR_CUDA_TRY(cudaEventCreate(&a));
-    CTR_CUDA_TRY(cudaEventCreate(&b));
-    int best = e->var32;
-    float best_ms = 1e30f;
-    for (int v = 0; v < kNumVariants32; ++v) {
-        e->var32 = v;
-        for (int rep = 0; rep < 2; ++rep) {   // first launch warms up, second is timed
-            CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 8, e->stream));
-            CTR_CUDA_TRY(cudaEventRecord(a, e->stream));
-            CTR_TRY(launch_fp32(e, 0));
-            CTR_CUDA_TRY(cudaEventRecord(b, e->stream));
-        }
-        CTR_CUDA_TRY(cudaEventSynchronize(b));
-        float ms = 0.f;
-        CTR_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = v;
-        }
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    // the timed launches added into the slots' accumulators with no finish after them: clear them
-    for (int q = 0; q < e->cap; ++q)
-        if (e->owner[q]) CTR_CUDA_TRY(cudaMemsetAsync(e->owner[q]->acc.p, 0, e->owner[q]->acc.bytes, e->stream));
-    e->var32 = best;
-    e->graph_dirty = true;
-    g_last_var = best;
-    set_fp32_variant(best);
-    std::lock_guard<std::mutex> lk(mu);
-    cache[{e->device, bucket}] = best;
-    return CTR_OK;
-}
-
 int engine_step(Engine* e, std::vector<SlotStat>* stats) {
-    if (!e->tuned && e->autotune) CTR_TRY(engine_autotune(e));
     CTR_TRY(ensure_graph(e));
     if (e->graph_exec) {
         CTR_CUDA_TRY(cudaGraphLaunch(e->graph_exec, e->stream));

@@ -65,18 +65,17 @@ struct Engine {
     int max_nblk = 1;
     int max_m = 1;
     int sms = 1;
-    int64_t item_cap[3] = {0, 0, 0};
+    // work lists per pair arithmetic and kernel variant (FP32: the variant of each slot's schedule)
+    int64_t item_cap[3][pk::kNumVar32] = {};
+    bool var_used[pk::kNumVar32] = {};   // FP32 variants of the occupied slots
     int64_t steps = 0;
     int64_t kernels_per_step = 0;
-    int var32 = 0;            // FP32 persistent variant (index into pk::kVariants32)
-    bool autotune = true;     // choose var32 by timing at the first step
-    bool tuned = false;
     const float2* exp_tab = nullptr;
     bool kc_shared[3] = {false, false, false};   // all slots of an arithmetic share their pair constants
     pk::PairConsts kc_val[3] = {};               // ... and these are they (launch parameter)
     std::vector<SlotDev> host;
     std::vector<ctr_ibim*> owner;
-    DevBuf slots, stats, items[3], n_items, counters, err;
+    DevBuf slots, stats, items[3][pk::kNumVar32], n_items, counters, err;
     // treecode work entries (slot, index) per pair arithmetic: moment chunks, far clusters, far items
     bool any_tree = false;
     int tree_np[3] = {0, 0, 0};   // largest proxy count per arithmetic among the treecode slots
@@ -94,8 +93,5 @@ int engine_prepare_handle(ctr_ibim* s);
 int engine_solve_all(ctr_ibim* const* hs, int64_t n, int use_graph, std::vector<ctr_solve_info>* infos,
                      int64_t* steps);
 int ensure_krylov_public(ctr_ibim* s);
-int engine_fp32_variant(const Engine* e, int* R, int* chunk, int* unroll);
-// Last variant the autotuner chose (R = 0 if none yet).
-void last_tuning(int* R, int* chunk, int* unroll);
 
 }  // namespace ctr

@@ -1164,14 +1164,41 @@ struct PairSmem {
           tab(reinterpret_cast<float2*>(raw + pair_ring_bytes<Policy>() + pair_jred_bytes<Policy>())) {}
 };
 
-// Fixed launch shapes of the schedules: thread slots (x the policy's kPack targets) and sources per
-// transposed chunk.  R fixes the target blocks and hence the summation order,
-// so it is the same for every kernel variant of an arithmetic.
+// Launch shapes of the schedules: thread slots (x the policy's kPack targets) and sources per
+// transposed chunk.  R and the tile fix the target blocks and the per-tile sums, hence the summation
+// order: they are a property of a system's schedule (set when the system is set up), the same
+// wherever the system runs.  The float-float and FP64 shapes are fixed; kR32 is the default FP32 one.
 constexpr int kR32 = 2, kRdf = 1, kR64 = 1;   // thread slots (FP32: 2 packed pairs = 4 targets)
 constexpr int kChunkDf = 8, kChunk64 = 8;
-// FP32 schedule-kernel variants: (sources per transposed chunk, unroll of the chunk loop)
-constexpr int kNumVariants32 = 4;
-extern const int kVariants32[kNumVariants32][2];
+
+// The packed FP32 policy with another source tile (sources per shared-memory stage).
+template <int TILE>
+struct Fp32x2T : Fp32x2Policy {
+    static constexpr int kTile = TILE;
+};
+
+// FP32 schedule-kernel variants, one of which each system's FP32 schedule uses: thread slots R (R x 2
+// targets per thread: 512 or 1024 per block), source tile, sources per transposed chunk V and unroll
+// U of the chunk loop.  Variant 0 is the default shape (the treecode's near items always use it).
+struct Var32 {
+    int R, tile, V, U;
+};
+constexpr int kNumVar32 = 6;
+constexpr Var32 kVar32[kNumVar32] = {{2, 256, 8, 1}, {2, 256, 8, 2}, {1, 256, 8, 2},
+                                     {2, 128, 8, 2}, {1, 128, 8, 2}, {2, 256, 4, 2}};
+
+// f.template run<Policy, R, V, U>() for FP32 variant v (a functor with a member template `run`)
+template <typename F>
+inline int with_var32(int v, const F& f) {
+    switch (v) {
+        case 1: return f.template run<Fp32x2T<256>, 2, 8, 2>();
+        case 2: return f.template run<Fp32x2T<256>, 1, 8, 2>();
+        case 3: return f.template run<Fp32x2T<128>, 2, 8, 2>();
+        case 4: return f.template run<Fp32x2T<128>, 1, 8, 2>();
+        case 5: return f.template run<Fp32x2T<256>, 2, 4, 2>();
+        default: return f.template run<Fp32x2T<256>, 2, 8, 1>();
+    }
+}
 
 // Per-block setup shared by every pair kernel: exponential tables and the two mbarriers.
 template <typename Policy>
@@ -1191,6 +1218,10 @@ inline float2 split_ff(double v) {
     const float hi = (float)v;
     return make_float2(hi, (float)(v - (double)hi));
 }
+__device__ __forceinline__ float2 split_ff_dev(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
 
 }  // namespace pk
 
@@ -1199,11 +1230,11 @@ int exp_table(int device, const float2** out);
 // Splits of the source range for equal-work items filling whole waves of `slots` resident blocks
 // (one-sided grid launch of the fixed-scratch entry point)
 PairPlan make_plan(int64_t M, int R, int tile, int slots);
-// Resident blocks of the schedule kernels of the three arithmetics: [0] FP32, [1] float-float, [2] FP64
+// Resident blocks of the schedule kernels of the three arithmetics: [0] FP32 (default variant),
+// [1] float-float, [2] FP64
 int schedule_slots(int sms, int slots[3]);
-// FP32 variant used by the schedule kernels of this process (set by the engine's autotuner)
-void set_fp32_variant(int v);
-int fp32_variant();
+// The FP32 variant of the most recent tuning in this process (-1 before any)
+int last_fp32_variant();
 // Runs a handle's schedule of one arithmetic (policy index 0 FP32, 1 float-float, 2 FP64) on its stream
 int launch_schedule(ctr_ibim* s, int pol, const void* src, const pk::PairConsts& kc);
 // Fill the f32x2 copies of a PairConsts from its FP32 fields

@@ -231,6 +231,18 @@ int pair_consts(ctr_ibim* s, bool tables, PairConsts* out) {
     return CTR_OK;
 }
 
+int pack_sources(ctr_ibim* s, const double* d_x, int precision) {
+    const int64_t M = s->M;
+    const double scale = s->h * s->h * s->h / (4.0 * kPi);
+    float4* s32 = (precision == CTR_FP32_REFINE) ? s->src32.as<float4>() : nullptr;
+    double4* s64 = (precision == CTR_FP64) ? s->src64.as<double4>() : nullptr;
+    float4* sdf = (precision == CTR_DF64) ? s->srcdf.as<float4>() : nullptr;
+    const int32_t* tinv = s->tree ? s->tree->d_tinv.as<int32_t>() : nullptr;
+    pack_kernel<<<grid_for(M, 256), 256, 0, s->stream>>>(d_x, s->na.W, M, scale, s32, s64, sdf, tinv);
+    CTR_LAUNCHED();
+    return CTR_OK;
+}
+
 int alloc_accumulators(ctr_ibim* s) {
     const size_t bytes = sizeof(unsigned long long) * (size_t)kFxWords * (size_t)s->M;
     CTR_TRY(s->acc.alloc(bytes));

@@ -19,6 +19,9 @@
 // which blocks add does not change a bit of the result).
 #include <algorithm>
 #include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
 #include <numeric>
 
 #include "pairkern.cuh"
@@ -209,25 +212,100 @@ int upload_schedule(PairSchedule& p, int64_t M, cudaStream_t st) {
     return CTR_OK;
 }
 
-std::atomic<int> g_var32{0};
+std::atomic<int> g_last_var32{-1};
+
+struct PerSm {
+    template <typename P, int R, int V, int U>
+    int run() const { return sched_per_sm<P, R, V, U>(); }
+};
+
+struct SchedRun {
+    ctr_ibim* s;
+    const void* src;
+    const PairConsts* kc;
+    int sms;
+    template <typename P, int R, int V, int U>
+    int run() const { return sched_launch<P, R, V, U>(s, 0, src, *kc, sms); }
+};
+
+// The FP32 variant of a system: fixed by its options, else the one timed fastest on the first system
+// of its size bucket (log2 M) on this device, cached for the process.  Timing: every variant's
+// schedule for this system, one application each after a warm-up, with the right-hand side as the
+// weights.  Leaves s->sched[0] planned for the chosen variant.
+int plan_fp32(ctr_ibim* s, const std::vector<uint8_t>& flags, int g0, int nb0, int sms) {
+    const int64_t M = s->M;
+    auto plan = [&](int v) -> int {
+        const int per = with_var32(v, PerSm{});
+        if (per < 0) return per;
+        plan_schedule(s->sched[0], M, kVar32[v].R * Fp32x2Policy::kPack, kVar32[v].tile, kSymCost[0], flags, g0, nb0,
+                      per * sms);
+        CTR_TRY(upload_schedule(s->sched[0], M, s->stream));
+        s->sched[0].var = v;
+        return CTR_OK;
+    };
+    const int want_bs = s->opt.fp32_block, want_tile = s->opt.fp32_tile;
+    if (want_bs > 0 || want_tile > 0) {
+        for (int v = 0; v < kNumVar32; ++v) {
+            const int bs = kThreads * kVar32[v].R * Fp32x2Policy::kPack;
+            if ((want_bs <= 0 || want_bs == bs) && (want_tile <= 0 || want_tile == kVar32[v].tile)) return plan(v);
+        }
+        return fail(CTR_ERR_INVALID, "fp32_block must be 512 or 1024 and fp32_tile 128 or 256");
+    }
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    const int bucket = (int)std::floor(std::log2((double)std::max<int64_t>(M, 1)));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({s->device, bucket});
+        if (it != cache.end()) {
+            g_last_var32.store(it->second);
+            return plan(it->second);
+        }
+    }
+    CTR_TRY(pack_sources(s, s->rhs.as<double>(), CTR_FP32_REFINE));
+    PairConsts kc;
+    CTR_TRY(pair_consts(s, false, &kc));
+    cudaEvent_t a = nullptr, b = nullptr;
+    CTR_CUDA_TRY(cudaEventCreate(&a));
+    CTR_CUDA_TRY(cudaEventCreate(&b));
+    int best = 0;
+    float best_ms = 1e30f;
+    int st = CTR_OK;
+    for (int v = 0; v < kNumVar32 && st == CTR_OK; ++v) {
+        st = plan(v);
+        const SchedRun r{s, s->src32.p, &kc, sms};
+        if (st == CTR_OK && v == 0) st = with_var32(v, r);   // warm-up
+        if (st == CTR_OK && cudaEventRecord(a, s->stream) != cudaSuccess) st = fail(CTR_ERR_CUDA, "event");
+        if (st == CTR_OK) st = with_var32(v, r);
+        if (st == CTR_OK && cudaEventRecord(b, s->stream) != cudaSuccess) st = fail(CTR_ERR_CUDA, "event");
+        float ms = 0.f;
+        if (st == CTR_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+            st = fail(CTR_ERR_CUDA, "event timing");
+        if (st == CTR_OK && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CTR_TRY(st);
+    CTR_TRY(check_device_error(s, "pair-kernel tuning"));
+    // the timed applications added into the accumulators with no finish after them
+    CTR_CUDA_TRY(cudaMemsetAsync(s->acc.p, 0, s->acc.bytes, s->stream));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        best = cache.emplace(std::make_pair(s->device, bucket), best).first->second;   // first tuning wins
+    }
+    g_last_var32.store(best);
+    return plan(best);
+}
 
 }  // namespace
 
-// FP32 schedule-kernel variants (sources per transposed chunk, unroll of the chunk loop); they
-// differ in speed only, not in results (same summation trees).
-const int pk::kVariants32[pk::kNumVariants32][2] = {{8, 1}, {4, 1}, {8, 2}, {4, 2}};
-
-void set_fp32_variant(int v) { g_var32.store((v >= 0 && v < kNumVariants32) ? v : 0); }
-int fp32_variant() { return g_var32.load(); }
+int last_fp32_variant() { return g_last_var32.load(); }
 
 int schedule_slots(int sms, int slots[3]) {
-    int a = 0;
-    switch (fp32_variant()) {
-        case 1: a = sched_per_sm<Fp32x2Policy, kR32, 4, 1>(); break;
-        case 2: a = sched_per_sm<Fp32x2Policy, kR32, 8, 2>(); break;
-        case 3: a = sched_per_sm<Fp32x2Policy, kR32, 4, 2>(); break;
-        default: a = sched_per_sm<Fp32x2Policy, kR32, 8, 1>(); break;
-    }
+    const int a = with_var32(0, PerSm{});
     if (a < 0) return a;
     const int b = sched_per_sm<Df64Policy, kRdf, kChunkDf, 1>();
     if (b < 0) return b;
@@ -242,14 +320,7 @@ int schedule_slots(int sms, int slots[3]) {
 int launch_schedule(ctr_ibim* s, int pol, const void* src, const PairConsts& kc) {
     int sms = 0;
     CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-    if (pol == 0) {
-        switch (fp32_variant()) {
-            case 1: return sched_launch<Fp32x2Policy, kR32, 4, 1>(s, 0, src, kc, sms);
-            case 2: return sched_launch<Fp32x2Policy, kR32, 8, 2>(s, 0, src, kc, sms);
-            case 3: return sched_launch<Fp32x2Policy, kR32, 4, 2>(s, 0, src, kc, sms);
-            default: return sched_launch<Fp32x2Policy, kR32, 8, 1>(s, 0, src, kc, sms);
-        }
-    }
+    if (pol == 0) return with_var32(s->sched[0].var, SchedRun{s, src, &kc, sms});
     if (pol == 1) return sched_launch<Df64Policy, kRdf, kChunkDf, 1>(s, 1, src, kc, sms);
     return sched_launch<Fp64Policy, kR64, kChunk64, 1>(s, 2, src, kc, sms);
 }
@@ -269,15 +340,17 @@ int build_schedules(ctr_ibim* s, const int slots[3]) {
     std::vector<uint8_t> flags((size_t)nb0 * nb0);
     CTR_CUDA_TRY(cudaMemcpyAsync(flags.data(), d_flags.p, flags.size(), cudaMemcpyDeviceToHost, s->stream));
     CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    const int Rs[3] = {kR32 * Fp32x2Policy::kPack, kRdf, kR64};   // targets per thread
-    const int tiles[3] = {Fp32x2Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
-    for (int p = 0; p < 3; ++p) {
+    CTR_TRY(alloc_accumulators(s));
+    CTR_TRY(s->counter.alloc(sizeof(int) * 4));
+    const int Rs[3] = {0, kRdf, kR64};   // targets per thread of the fixed shapes
+    const int tiles[3] = {0, Df64Policy::kTile, Fp64Policy::kTile};
+    for (int p = 1; p < 3; ++p) {
         plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], flags, g0, nb0, slots[p]);
         CTR_TRY(upload_schedule(s->sched[p], M, s->stream));
     }
-    CTR_TRY(alloc_accumulators(s));
-    CTR_TRY(s->counter.alloc(sizeof(int) * 4));
-    return CTR_OK;
+    int sms = 0;
+    CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+    return plan_fp32(s, flags, g0, nb0, sms);
 }
 
 }  // namespace ctr

@@ -24,10 +24,10 @@ namespace {
 
 constexpr int kTreeItemsPerSlot = 4;
 // A well-separated cluster is approximated when it has more than (degree+1)^3 / kMinFarDiv nodes: a
-// float-float pair costs about 16 FP32 proxy evaluations, an FP32 or FP64 pair about one.
-constexpr int kMinFarDiv[3] = {1, 16, 1};
+// float-float pair costs about two float-float proxy evaluations, an FP32 or FP64 pair about one.
+constexpr int kMinFarDiv[3] = {1, 2, 1};
 // Cost of one proxy evaluation relative to one one-sided pair of the arithmetic (item splitting only).
-constexpr double kFarCost[3] = {0.4, 0.04, 0.5};
+constexpr double kFarCost[3] = {0.4, 0.45, 0.5};
 
 template <typename T>
 __global__ void gather_rows(const T* __restrict__ src, T* __restrict__ dst, const int32_t* __restrict__ perm,
@@ -86,7 +86,14 @@ int launch_tree_t(ctr_ibim* s, int pol) {
     CTR_LAUNCHED();
     if (R * NT != s->sched[pol].BS) return fail(CTR_ERR_INVALID, "treecode: far kernel shape != target block");
     static std::map<std::pair<int, int>, int> cache;
-    if constexpr (sizeof(Real) == 4) {
+    if constexpr (sizeof(Real) == 8 && R == kTreeR[1] && NT == kTreeNT[1]) {   // float-float far field
+        auto kern = k_tree_far_ff<R, NT, OneTreeAcc>;
+        const int smem = (int)tree_farff_smem(P.np);
+        const int per_sm = far_per_sm(kern, NT, smem, (int)tree_farff_smem(), cache);
+        if (per_sm < 0) return per_sm;
+        kern<<<std::min<int64_t>((int64_t)per_sm * sms, (int64_t)P.far.size()), NT, smem, st>>>(
+            acc, P.d_ent_far.as<int2>(), counts + 2, counters + 1);
+    } else if constexpr (sizeof(Real) == 4) {
         auto kern = k_tree_far2<R / 2, NT, OneTreeAcc>;
         const int smem = (int)tree_far2_smem(P.np);
         const int per_sm = far_per_sm(kern, NT, smem, (int)tree_far2_smem(), cache);
@@ -109,7 +116,7 @@ int launch_tree_t(ctr_ibim* s, int pol) {
 int launch_tree(ctr_ibim* s, int pol) {
     if (!s->tree) return CTR_OK;
     if (pol == 0) return launch_tree_t<float, kTreeR[0], kTreeNT[0]>(s, 0);
-    if (pol == 1) return launch_tree_t<float, kTreeR[1], kTreeNT[1]>(s, 1);
+    if (pol == 1) return launch_tree_t<double, kTreeR[1], kTreeNT[1]>(s, 1);
     return launch_tree_t<double, kTreeR[2], kTreeNT[2]>(s, 2);
 }
 
@@ -208,7 +215,7 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
     // ---- per pair arithmetic: lists, items, chunks
     const int Rs[3] = {kR32 * Fp32x2Policy::kPack, kRdf, kR64};
     const int tiles[3] = {Fp32x2Policy::kTile, Df64Policy::kTile, Fp64Policy::kTile};
-    const size_t real_bytes[3] = {sizeof(float), sizeof(float), sizeof(double)};
+    const size_t real_bytes[3] = {sizeof(float), sizeof(double), sizeof(double)};   // moments and charges
     std::vector<int> counts(15, 0);
     for (int p = 0; p < 3; ++p) {
         PairSchedule& sc = s->sched[p];
@@ -379,6 +386,7 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         v.flist[p] = P.d_flist.as<int32_t>();
         v.BS[p] = s->sched[p].BS;
     }
+    CTR_TRY(exp_table(s->device, &v.exp_tab));
     v.src32 = s->src32.as<float4>();
     v.srcdf = s->srcdf.as<float4>();
     v.src64 = s->src64.as<double4>();

@@ -15,12 +15,16 @@
 //                  barycentric basis and derivative in shared memory; each
 //                  thread owns one (k2, k3) row of proxies);
 //   k_tree_momred  the chunks of a cluster added in a fixed order, Q formed;
-//   k_tree_far2    far items (target block x a run of its far clusters) with
-//                  FP32 charges, two targets per f32x2 instruction; the
-//                  cluster's proxies and charges in shared memory, FP32 sums
-//                  per cluster folded into FP64 per target, written to the
-//                  item's partial region like a one-sided pair item;
-//   k_tree_far     the same in scalar arithmetic, used for FP64 charges.
+//   k_tree_far2    far items (target block x a run of its far clusters) of the
+//                  FP32 operator: FP32 charges, two targets per f32x2
+//                  instruction; the cluster's proxies and charges in shared
+//                  memory, FP32 sums per cluster folded into FP64 per target,
+//                  added into the nodes' exact accumulators like a pair item's;
+//   k_tree_far_ff  the same for the float-float operator: FP64 moments of the
+//                  full float-float sources, charges and proxies split into
+//                  float-float, every evaluation in float-float arithmetic
+//                  (about 2^-44 relative, like its pair terms);
+//   k_tree_far     the same in scalar FP64 arithmetic (FP64 operator).
 // The blocks of each kernel take work entries (handle, index) from a list
 // through an atomic counter; `Acc` maps an entry's handle to its TreeView (or
 // to nothing when that handle is not in this pass).
@@ -50,10 +54,15 @@ __device__ __forceinline__ void tree_source(const TreeView& t, int pol, int64_t 
         const double4 u = t.src64[2 * p], v = t.src64[2 * p + 1];
         P[0] = (Real)u.x, P[1] = (Real)u.y, P[2] = (Real)u.z, a = (Real)u.w;
         n[0] = (Real)v.x, n[1] = (Real)v.y, n[2] = (Real)v.z, b = (Real)v.w;
-    } else if (pol == 1) {   // float-float sources: the leading floats
+    } else if (pol == 1) {   // float-float sources: hi + lo in FP64, the leading floats in FP32
         const float4 u = t.srcdf[4 * p], v = t.srcdf[4 * p + 2];
         P[0] = (Real)u.x, P[1] = (Real)u.y, P[2] = (Real)u.z, a = (Real)u.w;
         n[0] = (Real)v.x, n[1] = (Real)v.y, n[2] = (Real)v.z, b = (Real)v.w;
+        if constexpr (sizeof(Real) == 8) {
+            const float4 ul = t.srcdf[4 * p + 1], vl = t.srcdf[4 * p + 3];
+            P[0] += (Real)ul.x, P[1] += (Real)ul.y, P[2] += (Real)ul.z, a += (Real)ul.w;
+            n[0] += (Real)vl.x, n[1] += (Real)vl.y, n[2] += (Real)vl.z, b += (Real)vl.w;
+        }
     } else {                 // duplicated f32x2 layout {x,x,y,y}{z,z,a,a}{nx,nx,ny,ny}{nz,nz,-b,-b}
         const float4 u0 = t.src32[4 * p], u1 = t.src32[4 * p + 1], u2 = t.src32[4 * p + 2],
                      u3 = t.src32[4 * p + 3];
@@ -437,6 +446,125 @@ __global__ void __launch_bounds__(NT) k_tree_far2(Acc acc, const int2* __restric
         }
 #pragma unroll
         for (int r = 0; r < 2 * RP; ++r) {
+            if (pp[r] < M) {
+                pk::fx_add(t.acc + pp[r], M, 0, o1[r]);
+                pk::fx_add(t.acc + pp[r], M, 1, o2[r]);
+            }
+        }
+    }
+}
+
+// Float-float far items (the float-float operator): R targets per thread x NT threads = a 256-node block.
+// Dynamic shared memory: the cluster's proxy coordinates and charges as float-float pairs, then the
+// exponential tables.
+constexpr size_t tree_farff_smem(int np = kTreeMaxNp) {
+    return sizeof(float2) * (3 * kTreeMaxN1 + 3 * np + pk::kExpHi + pk::kExpLo);
+}
+
+template <int R, int NT, class Acc>
+__global__ void __launch_bounds__(NT) k_tree_far_ff(Acc acc, const int2* __restrict__ ent,
+                                                  const int* __restrict__ n_ent, int* __restrict__ counter) {
+    using pk::F2;
+    constexpr int pol = 1;
+    extern __shared__ __align__(16) unsigned char tree_smem[];
+    float2* sx = reinterpret_cast<float2*>(tree_smem);   // [3][kTreeMaxN1]
+    float2* sq = sx + 3 * kTreeMaxN1;                     // [3][np]
+    __shared__ int cur;
+    __shared__ const float2* tab_src;
+    const int tid = threadIdx.x;
+    const int total = *n_ent;
+    bool tab_ready = false;
+    for (;;) {
+        const int it = tree_next(counter, &cur);
+        if (it >= total) break;
+        const int2 w = ent[it];
+        const TreeView* tp = acc.view(w.x);
+        if (!tp) continue;
+        const TreeView& t = *tp;
+        const int n1 = t.n1[pol], np = t.np[pol], M = t.M, BS = t.BS[pol];
+        float2* tab = sq + 3 * np;
+        if (!tab_ready) {   // block-uniform; every handle's table is the same device table
+            if (tid == 0) tab_src = t.exp_tab;
+            __syncthreads();
+            for (int q = tid; q < pk::kExpHi + pk::kExpLo; q += NT) tab[q] = tab_src[q];
+            tab_ready = true;
+        }
+        const FarItem f = t.far[pol][w.y];
+        const F2 kap = pk::f2(pk::split_ff_dev(t.kappa));
+        F2 px[R], py[R], pz[R], nx[R], ny[R], nz[R];
+        double o1[R], o2[R];
+        int64_t pp[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            pp[r] = (int64_t)f.I * BS + r * NT + tid;
+            const int64_t p = pp[r] < M ? pp[r] : (int64_t)M - 1;
+            const float4 u = t.srcdf[4 * p], ul = t.srcdf[4 * p + 1], v = t.srcdf[4 * p + 2],
+                         vl = t.srcdf[4 * p + 3];
+            px[r] = F2{u.x, ul.x}, py[r] = F2{u.y, ul.y}, pz[r] = F2{u.z, ul.z};
+            nx[r] = F2{v.x, vl.x}, ny[r] = F2{v.y, vl.y}, nz[r] = F2{v.z, vl.z};
+            o1[r] = 0.0, o2[r] = 0.0;
+        }
+        for (int l = f.l0; l < f.l1; ++l) {
+            const int q = t.flist[pol][l];
+            __syncthreads();   // the previous cluster's proxies are no longer read (and the table is in)
+            const double* bx = t.box[pol] + 6 * (int64_t)q;
+            for (int i = tid; i < 3 * n1; i += NT) {
+                const int ax = i / n1, m = i % n1;
+                sx[ax * kTreeMaxN1 + m] = pk::split_ff_dev(bx[ax] + bx[3 + ax] * t.xref[pol][m]);
+            }
+            const double* Q = static_cast<const double*>(t.mom[pol]) + (size_t)q * 3 * np;
+            for (int i = tid; i < 3 * np; i += NT) sq[i] = pk::split_ff_dev(Q[i]);
+            __syncthreads();
+            F2 a1[R], a2[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) a1[r] = a2[r] = F2{0.f, 0.f};
+            for (int k3 = 0; k3 < n1; ++k3) {
+                const F2 sz = pk::f2(sx[2 * kTreeMaxN1 + k3]);
+                F2 dz2[R], dzn[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const F2 dz = pk::sub(pz[r], sz);
+                    dz2[r] = pk::mul(dz, dz);
+                    dzn[r] = pk::mul(dz, nz[r]);
+                }
+                for (int k2 = 0; k2 < n1; ++k2) {
+                    const F2 sy = pk::f2(sx[kTreeMaxN1 + k2]);
+                    F2 ryz[R], dyzn[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const F2 dy = pk::sub(py[r], sy);
+                        ryz[r] = pk::add(pk::mul(dy, dy), dz2[r]);
+                        dyzn[r] = pk::add(pk::mul(dy, ny[r]), dzn[r]);
+                    }
+                    const int kb = (k3 * n1 + k2) * n1;
+                    for (int k1 = 0; k1 < n1; ++k1) {
+                        const F2 sxk = pk::f2(sx[k1]);
+                        const F2 q0 = pk::f2(sq[kb + k1]), qk = pk::f2(sq[np + kb + k1]),
+                                 qkp = pk::f2(sq[2 * np + kb + k1]);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const F2 dx = pk::sub(px[r], sxk);
+                            const F2 r2 = pk::add(pk::mul(dx, dx), ryz[r]);
+                            const F2 dn = pk::add(pk::mul(dx, nx[r]), dyzn[r]);
+                            const F2 ri = pk::rsqrt_ff(r2);
+                            const F2 kr = pk::mul(kap, pk::mul(r2, ri));
+                            const F2 E = pk::exp_neg_ff(kr, tab);
+                            pk::acc_add(a1[r], pk::mull(ri, pk::add(pk::mul(E, qk), q0)));
+                            const F2 Ef = pk::mul(E, pk::add_f(kr, 1.f));
+                            const F2 ri3 = pk::mull(pk::mull(ri, ri), ri);
+                            pk::acc_add(a2[r], pk::mull(pk::mull(dn, ri3), pk::add(pk::mul(Ef, qkp), q0)));   // -(out2)
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                o1[r] += (double)a1[r].hi + (double)a1[r].lo;
+                o2[r] -= (double)a2[r].hi + (double)a2[r].lo;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
             if (pp[r] < M) {
                 pk::fx_add(t.acc + pp[r], M, 0, o1[r]);
                 pk::fx_add(t.acc + pp[r], M, 1, o2[r]);
