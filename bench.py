@@ -98,11 +98,13 @@ def parse():
     ap.add_argument("--skip-fp64-check", action="store_true",
                     help="do not solve the workload in plain FP64 for the error_vs_fp64 object")
     ap.add_argument("--skip-serve", action="store_true", help="do not run the bounded serving object")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels", "tree"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "kernels", "tree", "map"],
                     help="solve: the default single-system line; batch: many molecules in one engine; "
                          "serve: continuous-batching server under Poisson arrivals; kernels: two FP32, two "
                          "float-float and two FP64 operator applications of the ellipsoid at --h (the profiling "
-                         "case); tree: the solve step with the far-field treecode on the ellipsoid at --tree-h")
+                         "case); tree: the solve step with the far-field treecode on the ellipsoid at --tree-h; "
+                         "map: potential maps (psi_rxn at --map-points points) of the solved ellipsoid at --h")
+    ap.add_argument("--map-points", type=int, default=200000, help="map mode: points of the potential map")
     ap.add_argument("--tree-h", type=float, default=0.025, help="tree mode: grid spacing (0.025: ~714k nodes)")
     ap.add_argument("--tree-tol", type=float, default=1e-10, help="tree mode: solve tolerance")
     ap.add_argument("--tree-direct", action="store_true",
@@ -515,6 +517,53 @@ def run_kernels(args, ctr):
     print(json.dumps(out), flush=True)
 
 
+# Potential map (Eq. 2.31 at arbitrary points): FMA-pipe lane operations per (point, node) pair of the FP32
+# kernel counted from its source (potential.cu, MapFp32x2: 3 sub, 3 for r^2, 1 r, 2 for E's argument and
+# E1, 3 for d.n, 2 for 1/r^3, 1 for the ratio term, 3 for the first accumulation, 2 for the second; an
+# f32x2 instruction does two), plus 2 SFU operations (rsqrt, ex2).
+OPS_MAP = 22
+
+
+def run_map(args, ctr):
+    """psi_rxn of the solved default workload on a cloud of points inside and outside the ellipsoid, in the
+    three arithmetics: pair evaluations/s and the fraction of the FMA-pipe peak (FP32)."""
+    import torch
+    prob, cfg = workload(args.h)
+    rng = np.random.Generator(np.random.PCG64(17))
+    g = prob.grid
+    lo = np.asarray(g.origin)
+    hi = lo + g.h * (np.asarray(g.n) - 1)
+    pts = rng.uniform(lo, hi, size=(args.map_points, 3))
+    stream = torch.cuda.current_stream()
+    out = {"mode": "map", "config": dict(cfg, points=args.map_points,
+                                         points_recipe="uniform in the grid box (seed 17), both sides of the surface")}
+    with ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE)) as G:
+        psi, dpsi, _ = G.solve(device=True)
+        z = torch.tensor(pts, device="cuda")
+        M = G.M
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        peak = sms * 128 * 2070e6
+        res = {}
+        for prec, name, reps in ((ctr.FP32_REFINE, "fp32", 5), (ctr.DF64, "df64", 2), (ctr.FP64, "fp64", 1)):
+            G.potential_map(psi, dpsi, z, prec)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                G.potential_map(psi, dpsi, z, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3 / reps
+            res[name] = {"t_ms": t * 1e3, "pairs_per_s": args.map_points * M / t}
+        res["fp32"].update({"achieved": OPS_MAP * args.map_points * M / res["fp32"]["t_ms"] * 1e3, "peak": peak,
+                            "unit": "FP32-pipe lane ops/s", "frac": OPS_MAP * args.map_points * M /
+                            res["fp32"]["t_ms"] * 1e3 / peak,
+                            "basis": f"{OPS_MAP} FMA-pipe lane ops per (point, node) pair x {args.map_points} x {M}; "
+                                     f"peak {sms} SMs x 128 lanes x 2070 MHz"})
+        out.update(M=M, maps=res)
+    print(json.dumps(out), flush=True)
+
+
 def run_tree(args, ctr, world):
     """The solve step (setup, FP32-refined GMRES, energy) with the treecode far field, timed like the default
     line; value counts M^2 per operator application, as the direct sum would evaluate."""
@@ -646,7 +695,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.mode in ("batch", "serve", "kernels", "tree"):
+    if args.mode in ("batch", "serve", "kernels", "tree", "map"):
         import torch
         torch.cuda.set_device(local)
         import paper_2210_03699_gb300 as ctr
@@ -654,7 +703,7 @@ def main():
             if args.mode == "tree":
                 run_tree(args, ctr, 1)
             else:
-                {"batch": run_batch, "serve": run_serve, "kernels": run_kernels}[args.mode](args, ctr)
+                {"batch": run_batch, "serve": run_serve, "kernels": run_kernels, "map": run_map}[args.mode](args, ctr)
         return
     import torch
     torch.cuda.set_device(local)

@@ -116,6 +116,34 @@ def sphere_problem(h: float = 0.25, R: float = 2.0, half_box: float = 3.0, tube_
         info={"R": R, "q": q})
 
 
+def quadratic_sphere_problem(h: float = 0.1, R: float = 1.0, half_box: float = 1.9, tube: float = 0.65,
+                             kappa: float = KAPPA) -> Problem:
+    """Level-set function d = (|x|^2 - R^2) / (2R) (zero on the sphere of radius R, gradient |x|/R; not a
+    distance).  Central differences are exact on a quadratic, so a node's finite-difference geometry is known
+    in closed form: its level set is the sphere of radius r = |y|, curvature 1/r, and the surface curvature
+    at its point P = y - d n is 1/(r - d).  The grid is offset by h/2 (an even node count per axis,
+    symmetric about the origin), so no node sits at the centre, where the gradient vanishes.  One charge at
+    (0.1, 0, 0)."""
+    n = 2 * int(math.ceil(half_box / h))
+    grid = Grid((n, n, n), (-(n - 1) * h / 2.0,) * 3, float(h))
+    X, Y, Z = grid.points()
+    sd = (X * X + Y * Y + Z * Z - R * R) / (2.0 * R)
+    return Problem(name=f"quadsphere_R{R:g}_h{h:g}", grid=grid, sdist=sd, charge_xyz=np.array([[0.1, 0.0, 0.0]]),
+                   charge_q=np.array([1.0]), kappa=kappa, tube=tube, info={"R": R})
+
+
+def flat_cylinder_problem(h: float = 0.25, R: float = 1.5, c: float = 1.0, tube_mult: float = 2.0,
+                          kappa: float = KAPPA) -> Problem:
+    """A cylinder of radius R and height 2c with flat faces, d = max(|z| - c, rho - R) (rho = |(x, y)|): near
+    the centre of a face the level sets are exact planes z = c + d.  One charge at the origin."""
+    half = max(R, c) + tube_mult * h + 4 * h
+    grid = box_grid((-half,) * 3, (half,) * 3, h)
+    X, Y, Z = grid.points()
+    sd = np.maximum(np.abs(Z) - c, np.sqrt(X * X + Y * Y) - R)
+    return Problem(name=f"flatcyl_h{h:g}", grid=grid, sdist=sd, charge_xyz=np.zeros((1, 3)),
+                   charge_q=np.array([1.0]), kappa=kappa, tube=tube_mult * h, info={"R": R, "c": c})
+
+
 # ---------------------------------------------------------------- ellipsoid
 def _ellipsoid_root(axes, y):
     """Closest point on an axis-aligned ellipsoid for points |y| (first octant).

@@ -71,6 +71,26 @@ def molecule(ctr, oracle_tables):
 
 
 @pytest.fixture(scope="module")
+def quadsphere(ctr, oracle_tables):
+    """Exact finite-difference geometry (quadratic level set): the HYB threshold cuts through the tube."""
+    prob = syn.quadratic_sphere_problem(h=0.1, tube=0.65)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables)
+    G = ctr.CtrIbim.from_problem(prob)
+    yield prob, S, G
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def flatcyl_kreg(ctr, oracle_tables):
+    """Flat faces (exact planes near their centres), K-reg rows everywhere."""
+    prob = syn.flat_cylinder_problem(h=0.25)
+    S = OracleSystem.from_problem(prob, tables=oracle_tables, method="kreg")
+    G = ctr.CtrIbim.from_problem(prob, options=ctr.Options(tube_halfwidth=prob.tube, method=ctr.METHOD_KREG))
+    yield prob, S, G
+    G.close()
+
+
+@pytest.fixture(scope="module")
 def sphere_kreg(ctr, oracle_tables):
     """The K-reg method (Sec. 2.3) everywhere on the sphere."""
     prob = syn.sphere_problem(h=0.25)
@@ -80,7 +100,7 @@ def sphere_kreg(ctr, oracle_tables):
     G.close()
 
 
-@pytest.mark.parametrize("which", ["sphere", "ellipsoid", "molecule", "sphere_kreg"])
+@pytest.mark.parametrize("which", ["sphere", "ellipsoid", "molecule", "sphere_kreg", "quadsphere", "flatcyl_kreg"])
 def test_setup_parity(which, request):
     prob, S, G = request.getfixturevalue(which)
     assert G.M == S.M
@@ -101,7 +121,7 @@ def test_setup_parity(which, request):
     assert abs(G.area() / S.area() - 1) < 1e-12
 
 
-@pytest.mark.parametrize("which", ["sphere", "ellipsoid", "molecule", "sphere_kreg"])
+@pytest.mark.parametrize("which", ["sphere", "ellipsoid", "molecule", "sphere_kreg", "quadsphere", "flatcyl_kreg"])
 def test_operator_parity(which, request, ctr):
     prob, S, G = request.getfixturevalue(which)
     p = syn.random_density(S.M, seed=11, smooth_points=S.geo.P)

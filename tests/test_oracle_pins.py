@@ -338,6 +338,54 @@ def test_hybrid_classification_on_smooth_and_kinked_surfaces(oracle_tables):
     assert np.all(geo.J[geo.bad] == 1.0) and np.all(np.isfinite(geo.W)) and np.all(geo.W >= 0)
 
 
+def test_hybrid_threshold_on_a_quadratic_level_set():
+    """HYB classification (Sec. 3.2) against its closed form: with d = (|x|^2 - 1)/2 the finite differences
+    are exact, the surface curvature at a node is 1/(r - d), r = |y|, and a node is bad iff
+    (eps + h) / (r - d) >= 0.8.  eps + h = 0.75 puts the threshold inside the tube: nodes with
+    r <= 1 - sqrt(1/8) or r >= 1 + sqrt(1/8) are bad, the band between is not."""
+    prob = syn.quadratic_sphere_problem(h=0.1, tube=0.65)
+    g = prob.grid
+    geo = geometry.tube_geometry(g.n, g.origin, g.h, prob.sdist, prob.tube)
+    r = np.linalg.norm(geo.y, axis=1)
+    val = (prob.tube + g.h) / (r - geo.d)
+    clear = np.abs(val - 0.8) > 1e-9
+    assert clear.sum() > 0.99 * geo.M
+    assert np.array_equal(geo.bad[clear], val[clear] >= 0.8)
+    assert geo.bad.any() and not geo.bad.all()
+    assert np.all(geo.bad[r < 0.6]) and not np.any(geo.bad[(r > 0.7) & (r < 1.3)]) and np.all(geo.bad[r > 1.4])
+    # the closed form's other parts: level-set curvature 1/r (both principal values), W uses J = 1 at bad nodes
+    kp = geo.kprime[~geo.bad]
+    assert np.allclose(kp, 1.0 / r[~geo.bad, None], rtol=1e-12)
+    assert np.all(geo.J[geo.bad] == 1.0)
+
+
+def test_kreg_cylinder_on_a_flat_face():
+    """K-reg correction sets (Sec. 2.3) where the surface is a plane (the centre of a flat face, z = c): the
+    tube nodes whose tangent-plane distance to the target's P is below tau = 2h are the 9 lattice columns
+    with a^2 + b^2 < 4 times the 3 tube layers |z - c| < 2h, 27 nodes for every such target; a brute force
+    over every tube node on that face gives the same sets."""
+    from oracle.correction import correction_nodes
+    prob = syn.flat_cylinder_problem(h=0.25, R=1.5, c=1.0)
+    g = prob.grid
+    geo = geometry.tube_geometry(g.n, g.origin, g.h, prob.sdist, prob.tube, method="kreg")
+    assert geo.bad.all()
+    ent, _ = correction_nodes(geo)
+    tgt = ent[:, 0].astype(int)
+    node = ent[:, 1].astype(int)
+    tau = 2.0 * g.h
+    rho = np.linalg.norm(geo.y[:, :2], axis=1)
+    face = (rho <= 0.4 + 1e-9) & (np.abs(np.abs(geo.y[:, 2]) - 1.0) < 0.3)
+    assert np.allclose(np.abs(geo.n[face, 2]), 1.0, atol=1e-14)
+    counts = np.bincount(tgt, minlength=geo.M)
+    assert face.sum() >= 50 and np.all(counts[face] == 27)
+    for i in np.nonzero(face)[0]:
+        same_side = np.sign(geo.y[:, 2]) == np.sign(geo.y[i, 2])
+        v = geo.y - geo.P[i]
+        t = v - np.outer(v @ geo.n[i], geo.n[i])
+        brute = np.nonzero(same_side & (np.sum(t * t, axis=1) < tau * tau))[0]
+        assert np.array_equal(np.sort(node[tgt == i]), brute)
+
+
 def test_oracle_torus_area_converges():
     """Rotated torus of Sec. 3.3.2 (R1 = 1, R2 = 1/2): the tube rule with J_h (Eq. 2.6, f = 1) against the
     closed form 4 pi^2 R1 R2 at eps = 2h; at least second order (the paper tabulates 1e-6..1e-5 errors)."""
