@@ -121,6 +121,8 @@ def parse():
     ap.add_argument("--pool", type=int, default=12, help="serve mode: distinct problems requests draw from")
     ap.add_argument("--slots", type=int, default=16, help="serve mode: server slots")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per run of the default line's serve object")
+    ap.add_argument("--fp64-pool-only", action="store_true",
+                    help="serve mode: only time the plain FP64 one-at-a-time path on every pool problem")
     ap.add_argument("--fp64-max-M", type=int, default=120000,
                     help="serve mode: pool problems up to this size are also solved in plain FP64 one at a time")
     return ap.parse_args()
@@ -374,11 +376,33 @@ def run_batch(args, ctr):
     print(json.dumps(line), flush=True)
 
 
+def fp64_pool_times(ctr, pool, max_M):
+    """The plain FP64 one-at-a-time GPU path on every pool problem of at most max_M nodes: energy and
+    seconds per problem (None where skipped) and each problem's node count."""
+    import torch
+    Ms, G64, t = [], {}, {}
+    for k, p in enumerate(pool):
+        with ctr.CtrIbim.from_problem(p) as G:
+            Ms.append(G.M)
+        if G.M > max_M:
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP64,
+                                                             tol=SOLVE_TOL)) as G:
+            psi, dpsi, _ = G.solve(device=True)
+            G64[k] = G.energy(psi, dpsi)[0]
+        torch.cuda.synchronize()
+        t[k] = time.perf_counter() - t0
+    return Ms, G64, t
+
+
 def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, cap_requests=None):
     """Continuous-batching server over a pool of problems: capacity with every request submitted at once,
     then Poisson arrivals at each fraction of it; per load solves/s and p50/p99 latency (submission to
     result).  Served energies are compared with the plain FP64 one-at-a-time GPU path on every pool problem
-    of at most fp64_max_M nodes (the fixed sample), whose rate is reported as fp64_solves_per_s."""
+    of at most fp64_max_M nodes (the fixed sample); requests pick pool problems uniformly, so with every
+    problem in the sample 1 / (mean FP64 solve time) is that path's rate on the same mix."""
     import threading as th
     import torch
 
@@ -421,28 +445,17 @@ def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, c
     capacity = cap["solves_per_s"]
     levels = {f"{f:g}": run_load(f * capacity, n_requests, seed + 2) for f in loads}
     # the plain FP64 one-at-a-time GPU path on the sample
-    Ms, G64, t64, n64 = [], {}, 0.0, 0
-    for k, p in enumerate(pool):
-        with ctr.CtrIbim.from_problem(p) as G:
-            Ms.append(G.M)
-        if G.M > fp64_max_M:
-            continue
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with ctr.CtrIbim.from_problem(p, options=ctr.Options(tube_halfwidth=p.tube, precision=ctr.FP64,
-                                                             tol=SOLVE_TOL)) as G:
-            psi, dpsi, _ = G.solve(device=True)
-            G64[k] = G.energy(psi, dpsi)[0]
-        torch.cuda.synchronize()
-        t64 += time.perf_counter() - t0
-        n64 += 1
+    Ms, G64, t64 = fp64_pool_times(ctr, pool, fp64_max_M)
     errs = [abs(e / G64[k] - 1) for lv in list(levels.values()) + [cap] for k, e in lv["energies"] if k in G64]
     for lv in list(levels.values()) + [cap]:
         lv.pop("energies")
+    n64 = len(t64)
     return {"capacity_solves_per_s": capacity, "saturated": cap, "levels": levels,
             "M_min": int(min(Ms)), "M_max": int(max(Ms)), "pool": len(pool), "slots": slots,
-            "fp64_solves_per_s": n64 / t64 if t64 > 0 else None,
+            "fp64_solves_per_s": n64 / sum(t64.values()) if n64 else None,
+            "fp64_same_mix": n64 == len(pool),
             "fp64_sample": f"{n64} of the {len(pool)} pool problems (those with M <= {fp64_max_M}), one at a time",
+            "fp64_s_per_problem": {int(Ms[k]): round(v, 3) for k, v in t64.items()},
             "max_energy_err": float(max(errs)) if errs else None, "checked_requests": len(errs)}
 
 
@@ -482,6 +495,13 @@ def run_serve(args, ctr):
     """Serving workload (C5): Poisson arrivals at fractions of the measured capacity; latency and throughput."""
     pool = c5_pool(max(1, args.pool // 3), max(1, args.pool // 3), max(1, args.pool - 2 * (args.pool // 3)),
                    args.max_atoms)
+    if args.fp64_pool_only:   # only the plain FP64 one-at-a-time path on the whole pool (the same-mix rate)
+        Ms, G64, t64 = fp64_pool_times(ctr, pool, 10 ** 12)
+        print(json.dumps({"mode": "serve_fp64_pool", "pool": len(pool), "fp64_s_per_problem":
+                          {int(Ms[k]): round(v, 3) for k, v in t64.items()},
+                          "fp64_solves_per_s_same_mix": len(t64) / sum(t64.values()),
+                          "G_pol": {int(Ms[k]): v for k, v in G64.items()}}), flush=True)
+        return
     out = serve_experiment(ctr, pool, n_requests=args.requests, loads=[float(v) for v in args.loads.split(",") if v],
                            slots=args.slots, fp64_max_M=args.fp64_max_M, cap_requests=args.capacity_requests)
     line = {"metric": "CTR-IBIM served solves/s", "value": out["levels"][max(out["levels"], key=float)]["solves_per_s"],
