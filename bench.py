@@ -120,6 +120,8 @@ def parse():
     ap.add_argument("--loads", default="0.8", help="serve mode: offered load / measured capacity (comma list)")
     ap.add_argument("--pool", type=int, default=12, help="serve mode: distinct problems requests draw from")
     ap.add_argument("--slots", type=int, default=16, help="serve mode: server slots")
+    ap.add_argument("--step-quantum-ms", type=float, default=20.0,
+                    help="serve: pair work of one system per engine step (longer applications run in parts; 0: whole)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per run of the default line's serve object")
     ap.add_argument("--fp64-pool-only", action="store_true",
                     help="serve mode: only time the plain FP64 one-at-a-time path on every pool problem")
@@ -397,7 +399,7 @@ def fp64_pool_times(ctr, pool, max_M):
     return Ms, G64, t
 
 
-def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, cap_requests=None):
+def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, cap_requests=None, quantum_ms=20.0):
     """Continuous-batching server over a pool of problems: capacity with every request submitted at once,
     then Poisson arrivals at each fraction of it; per load solves/s and p50/p99 latency (submission to
     result).  Served energies are compared with the plain FP64 one-at-a-time GPU path on every pool problem
@@ -412,7 +414,7 @@ def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, c
             gaps = np.random.Generator(np.random.PCG64(sd)).exponential(1.0 / rate, size=n)
             arrivals = np.cumsum(gaps) - gaps[0]
         picks = np.random.Generator(np.random.PCG64(sd + 1)).integers(0, len(pool), size=n)
-        with ctr.Server(max_slots=slots) as sv:
+        with ctr.Server(max_slots=slots, step_quantum_ms=quantum_ms) as sv:
             tickets = [None] * n
             t0 = time.perf_counter()
 
@@ -452,6 +454,7 @@ def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, c
     n64 = len(t64)
     return {"capacity_solves_per_s": capacity, "saturated": cap, "levels": levels,
             "M_min": int(min(Ms)), "M_max": int(max(Ms)), "pool": len(pool), "slots": slots,
+            "step_quantum_ms": quantum_ms,
             "fp64_solves_per_s": n64 / sum(t64.values()) if n64 else None,
             "fp64_same_mix": n64 == len(pool),
             "fp64_sample": f"{n64} of the {len(pool)} pool problems (those with M <= {fp64_max_M}), one at a time",
@@ -483,7 +486,7 @@ def run_serve_bounded(ctr, args):
         pool.append(syn.sphere_with_nodes(M, q=float(rng.choice([-1.0, 1.0]))))
     pool += [syn.ellipsoid_problem(h=0.2, seed=1), syn.ellipsoid_problem(h=0.1, seed=2)]
     out = serve_experiment(ctr, pool, n_requests=args.serve_requests, loads=[0.8], slots=args.slots,
-                           fp64_max_M=10 ** 9)
+                           fp64_max_M=10 ** 9, quantum_ms=args.step_quantum_ms)
     out["workload"] = (f"{args.serve_requests} requests per run drawn from a pool of {len(pool)} problems (SES "
                        f"molecules of 60 and 150 atoms at h 0.5 / 0.35, spheres of 6k and 30k nodes, ellipsoids at "
                        f"h 0.2 / 0.1), FP32 pairs + float-float refinement to {SOLVE_TOL:g}; capacity with all "
@@ -503,14 +506,15 @@ def run_serve(args, ctr):
                           "G_pol": {int(Ms[k]): v for k, v in G64.items()}}), flush=True)
         return
     out = serve_experiment(ctr, pool, n_requests=args.requests, loads=[float(v) for v in args.loads.split(",") if v],
-                           slots=args.slots, fp64_max_M=args.fp64_max_M, cap_requests=args.capacity_requests)
+                           slots=args.slots, fp64_max_M=args.fp64_max_M, cap_requests=args.capacity_requests,
+                           quantum_ms=args.step_quantum_ms)
     line = {"metric": "CTR-IBIM served solves/s", "value": out["levels"][max(out["levels"], key=float)]["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 pairs + f64",
             "data": "synthetic",
             "config": {"workload": f"{args.requests} requests per load level, Poisson arrivals, drawn from a pool of "
                                    f"{len(pool)} problems (SES molecules, spheres, ellipsoids), FP32 pairs + "
                                    f"float-float refinement to {SOLVE_TOL:g}", "M_min": out["M_min"],
-                       "M_max": out["M_max"], "slots": args.slots}}
+                       "M_max": out["M_max"], "slots": args.slots, "step_quantum_ms": args.step_quantum_ms}}
     line.update(out)
     print(json.dumps(line), flush=True)
 

@@ -66,7 +66,7 @@ class _Info(ctypes.Structure):
 
 
 class _ServerOptions(ctypes.Structure):
-    _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64)]
+    _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64), ("step_quantum_ms", ctypes.c_double)]
 
 
 class _RequestResult(ctypes.Structure):
@@ -443,8 +443,10 @@ class RequestResult:
 class Server:
     """Continuous-batching request server (ctr_server_*): submit problems, poll or wait for results."""
 
-    def __init__(self, max_slots: int = 16, hbm_budget_bytes: int = 0):
-        o = _ServerOptions(int(max_slots), int(hbm_budget_bytes))
+    def __init__(self, max_slots: int = 16, hbm_budget_bytes: int = 0, step_quantum_ms: float = 20.0):
+        """step_quantum_ms: pair work of one system per engine step; a longer operator application runs
+        in parts over consecutive steps (0: never split).  Results do not depend on it."""
+        o = _ServerOptions(int(max_slots), int(hbm_budget_bytes), float(step_quantum_ms))
         h = ctypes.c_void_p()
         _check(lib.ctr_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

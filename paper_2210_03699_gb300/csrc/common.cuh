@@ -126,10 +126,21 @@ struct PairSchedule {
     int tile = 128;       // sources per shared-memory tile
     int nb = 0;           // target blocks
     int64_t pairs_sym = 0, pairs_one = 0;   // evaluated pair orientations of each kind
+    double total_cost = 0.0;                // sum of the item costs
     std::vector<PairItem> items;   // in the order of d_items (decreasing cost)
     std::vector<double> cost;
     DevBuf d_items;
 };
+
+// Throughput of each pair arithmetic ([0] FP32, [1] float-float, [2] FP64) on the whole GPU in the cost
+// units of a schedule (one-sided pair evaluations; a symmetric evaluation counts its relative cost),
+// as measured on a GB300 at M = 178,575 (1.23e12, 1.25e11 and 1.55e10 pair interactions/s).  Used only
+// to size work (item lengths, engine parts), never in the arithmetic.
+constexpr double kUnitRate[3] = {7.9e11, 7.5e10, 9.0e9};
+// Longest item per arithmetic: this many seconds of one resident block at the rates above.  Short
+// items keep the tail of a persistent launch short and let the engine split a large system's
+// application into parts (an FP32 application of 180k nodes takes 26 ms, a float-float one 256 ms).
+constexpr double kItemSeconds[3] = {8e-3, 4e-3, 4e-3};
 
 // ---------------------------------------------------------------- far field (treecode)
 constexpr int kTreeMaxN1 = 13;                                        // degree <= 12

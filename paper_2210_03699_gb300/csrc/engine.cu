@@ -40,6 +40,11 @@ namespace {
 
 constexpr int kVecThreads = 256;
 constexpr double kUpdateGate = 1e-4;   // |r| / |g| below which refinement residuals are updated
+// Work entries carry (slot, item | part << kPartShift): items of a schedule < 2^24, parts <= kMaxParts.
+constexpr int kPartShift = 24;
+constexpr int kItemMask = (1 << kPartShift) - 1;
+constexpr int kMaxParts = 127;
+constexpr int kMinItemsPerPart = 64;
 
 __device__ __forceinline__ double block_sum_d(double v) {
     __shared__ double sh[kVecThreads / 32];
@@ -79,7 +84,7 @@ __device__ __forceinline__ void pack_weights(const SlotDev& s, int prec, int64_t
 // inner: z = Lambda^-1 V_j and the weights of z
 __global__ void k_prep_inner(SlotDev* S) {
     const SlotDev& s = S[blockIdx.y];
-    if (!inner_active(s)) return;
+    if (!inner_active(s) || s.part != 0) return;   // later parts reuse the packed weights
     const int64_t M = s.M;
     const double* v = s.V + (size_t)s.j * s.n;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
@@ -94,7 +99,7 @@ __global__ void k_prep_inner(SlotDev* S) {
 // residual update, d kept in z and its weights in the inner arithmetic (residual r - A d)
 __global__ void k_update_x(SlotDev* S) {
     const SlotDev& s = S[blockIdx.y];
-    if (!update_active(s)) return;
+    if (!update_active(s) || s.part != 0) return;
     const int64_t M = s.M, n = s.n;
     const int k = s.kdone;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
@@ -144,16 +149,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
         const int it = cur;
         __syncthreads();
         if (it >= total) break;
-        const int2 w = items[it];   // slot, item
+        const int2 w = items[it];   // slot, item | part << kPartShift
         const SlotDev& s = S[w.x];
         const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec)
                                     : (update_active(s) && res_arith(s) == prec);
-        if (!want) continue;
+        if (!want || (w.y >> kPartShift) != s.part) continue;
+        const int item = w.y & kItemMask;
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
                                                                          : (const void*)s.src64);
         if constexpr (kShared) {
-            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.acc, pkc, err, sm.ring,
+            if (!run_item<Policy, R, V, U>(s.items[pol][item], src, s.M, s.eptr, s.excl, s.acc, pkc, err, sm.ring,
                                            sm.jred, sm.tab, bar, gt))
                 return;
         } else {
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
             }
             __syncthreads();
             const PairConsts k = kc;   // block-uniform register copy: no shared loads in the pair loops
-            if (!run_item<Policy, R, V, U>(s.items[pol][w.y], src, s.M, s.eptr, s.excl, s.acc, k, err, sm.ring,
+            if (!run_item<Policy, R, V, U>(s.items[pol][item], src, s.M, s.eptr, s.excl, s.acc, k, err, sm.ring,
                                            sm.jred, sm.tab, bar, gt))
                 return;
         }
@@ -316,7 +322,7 @@ __global__ void k_upper_solve(SlotDev* S, int cap) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cap) return;
     SlotDev& s = S[q];
-    if (!update_active(s)) return;
+    if (!update_active(s) || s.part != 0) return;
     const int k = s.kdone, ldh = s.m + 1;
     for (int i = k - 1; i >= 0; --i) {
         double v = s.sv[i];
@@ -374,6 +380,33 @@ __global__ void k_start_scalars(SlotDev* S, int cap) {
     s.sv[0] = s.beta;
     s.j = 0;
     s.stat.state = kSlotInner;
+}
+
+// Start of a step: slots between two parts of an application take their next part.
+__global__ void k_resume(SlotDev* S, int cap) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (s.stat.state == kSlotInnerWait) s.stat.state = kSlotInner;
+    else if (s.stat.state == kSlotUpdateWait) s.stat.state = kSlotUpdate;
+}
+
+__device__ __forceinline__ int arith_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
+
+// After a half's pair launches: a slot whose application has parts left waits for the next step (the
+// rest of this step skips it); one that ran its last part goes on to finish the application.
+__global__ void k_part(SlotDev* S, int cap, int half) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cap) return;
+    SlotDev& s = S[q];
+    if (half == 0 ? !inner_active(s) : !update_active(s)) return;
+    const int np = s.nparts[arith_index(half == 0 ? s.inner_prec : res_arith(s))];
+    if (s.part + 1 < np) {
+        s.part += 1;
+        s.stat.state = half == 0 ? kSlotInnerWait : kSlotUpdateWait;
+    } else {
+        s.part = 0;
+    }
 }
 
 __global__ void k_stats(const SlotDev* S, int cap, SlotStat* out) {
@@ -592,25 +625,29 @@ static int rebuild_tree_items(Engine* e) {
 }
 
 // Rebuild the work lists (every item of every occupied slot's schedule, one list per arithmetic and
-// kernel variant; each entry is filtered by its slot's state at run time), sorted by decreasing cost
-// for the atomic-counter scheduler.
+// kernel variant; each entry is filtered by its slot's state and part at run time), in decreasing cost
+// for the atomic-counter scheduler: each slot's items are already in that order, so the lists are a
+// merge of the slots' sequences (ties: lower slot, then lower item first).  A slot whose application
+// is split gets its items dealt to the parts in that order, back and forth (0, 1, .., n-1, n-1, .., 0),
+// which balances the parts' costs.
 static int rebuild_items(Engine* e) {
     bool used[kNV] = {};
     for (int p = 0; p < 3; ++p) {
-        struct It {
-            int2 v;
-            double cost;
+        struct Seq {
+            int q, np;
+            const std::vector<double>* cost;
         };
-        std::vector<It> list[kNV];
+        std::vector<Seq> seqs[kNV];
         for (int q = 0; q < e->cap; ++q) {
             if (!e->owner[q]) continue;
             const SlotDev& s = e->host[q];
             const bool uses = (policy_index(s.inner_prec) == p) || (policy_index(s.res_prec) == p);
             if (!uses) continue;
             const PairSchedule& sc = e->owner[q]->sched[p];
+            if (sc.items.size() > (size_t)kItemMask) return fail(CTR_ERR_CAPACITY, "engine: schedule too long");
             const int var = (p == 0) ? sc.var : 0;
             if (p == 0) used[var] = true;
-            for (size_t k = 0; k < sc.items.size(); ++k) list[var].push_back(It{make_int2(q, (int)k), sc.cost[k]});
+            seqs[var].push_back(Seq{q, std::max(1, s.nparts[p]), &sc.cost});
         }
         // one set of pair constants for every slot of this arithmetic: pass it as a launch parameter
         bool shared = true, any = false;
@@ -635,9 +672,30 @@ static int rebuild_items(Engine* e) {
             e->graph_dirty = true;   // the captured launches carry the constants
         }
         for (int v = 0; v < kNV; ++v) {
-            std::stable_sort(list[v].begin(), list[v].end(), [](const It& a, const It& b) { return a.cost > b.cost; });
-            std::vector<int2> ent(list[v].size());
-            for (size_t i = 0; i < ent.size(); ++i) ent[i] = list[v][i].v;
+            size_t total = 0;
+            for (const Seq& a : seqs[v]) total += a.cost->size();
+            std::vector<int2> ent;
+            ent.reserve(total);
+            std::vector<size_t> pos(seqs[v].size(), 0);
+            auto later = [&](int a, int b) {   // heap order: the entry to take next on top
+                const double ca = (*seqs[v][a].cost)[pos[a]], cb = (*seqs[v][b].cost)[pos[b]];
+                return ca != cb ? ca < cb : a > b;
+            };
+            std::vector<int> heap;
+            for (int a = 0; a < (int)seqs[v].size(); ++a)
+                if (!seqs[v][a].cost->empty()) heap.push_back(a);
+            std::make_heap(heap.begin(), heap.end(), later);
+            while (!heap.empty()) {
+                std::pop_heap(heap.begin(), heap.end(), later);
+                const int a = heap.back();
+                const Seq& sq = seqs[v][a];
+                const size_t k = pos[a];
+                const int round = (int)(k / (size_t)sq.np), at = (int)(k % (size_t)sq.np);
+                const int part = (round & 1) ? sq.np - 1 - at : at;
+                ent.push_back(make_int2(sq.q, (int)k | (part << kPartShift)));
+                if (++pos[a] < sq.cost->size()) std::push_heap(heap.begin(), heap.end(), later);
+                else heap.pop_back();
+            }
             if ((int64_t)ent.size() > e->item_cap[p][v]) {
                 const int64_t capn = std::max<int64_t>(1024, (int64_t)ent.size() * 2);
                 CTR_TRY(e->items[p][v].alloc(sizeof(int2) * capn));
@@ -669,6 +727,8 @@ static int enqueue_step(Engine* e) {
     const int mx = e->max_nblk;
     const dim3 vec(e->vec_blocks, cap);
     const unsigned one = grid_for(cap, 128);
+    k_resume<<<one, 128, 0, st>>>(S, cap);
+    CTR_LAUNCHED();
     // ---- inner half: one Arnoldi iteration
     k_prep_inner<<<vec, kVecThreads, 0, st>>>(S);
     CTR_LAUNCHED();
@@ -678,6 +738,8 @@ static int enqueue_step(Engine* e) {
     CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, 0, CTR_DF64)));
     CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, 0, CTR_FP64)));
     CTR_TRY(launch_trees(e, 0));
+    k_part<<<one, 128, 0, st>>>(S, cap, 0);
+    CTR_LAUNCHED();
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 0);
     CTR_LAUNCHED();
     for (int pass = 0; pass < 2; ++pass) {
@@ -707,6 +769,8 @@ static int enqueue_step(Engine* e) {
     CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, 1, CTR_DF64)));
     CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, 1, CTR_FP64)));
     CTR_TRY(launch_trees(e, 1));
+    k_part<<<one, 128, 0, st>>>(S, cap, 1);
+    CTR_LAUNCHED();
     k_finish<<<vec, kVecThreads, 0, st>>>(S, 1);
     CTR_LAUNCHED();
     k_dots_partial<<<dim3(mx, cap), kVecThreads, 0, st>>>(S, 3);
@@ -791,6 +855,16 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     // residuals are always formed in full with the residual arithmetic
     d.res_update = (d.refine && s->opt.residual_mode == CTR_RESIDUAL_UPDATE && !s->tree) ? 1 : 0;
     d.upd = 0;
+    d.part = 0;
+    for (int p = 0; p < 3; ++p) {   // parts of one application (treecode handles: always whole)
+        const PairSchedule& sc = s->sched[p];
+        int64_t np = 1;
+        if (e->quantum_s > 0.0 && !s->tree) {
+            np = (int64_t)std::ceil(sc.total_cost / kUnitRate[p] / e->quantum_s);
+            np = std::min<int64_t>(np, (int64_t)sc.items.size() / kMinItemsPerPart);
+        }
+        d.nparts[p] = (int)std::max<int64_t>(1, std::min<int64_t>(np, kMaxParts));
+    }
     CTR_TRY(pair_consts(s, true, &d.kc));
     for (int p = 0; p < 3; ++p) {
         d.items[p] = s->sched[p].d_items.as<PairItem>();
@@ -865,6 +939,13 @@ int engine_retire(Engine* e, int q, ctr_solve_info* info) {
     SlotStat st;
     CTR_CUDA_TRY(cudaMemcpyAsync(&st, e->stats.as<SlotStat>() + q, sizeof(SlotStat), cudaMemcpyDeviceToHost, e->stream));
     CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (st.state == kSlotInnerWait || st.state == kSlotUpdateWait) {
+        // retired between two parts of an application (cancelled): its node accumulators hold partial
+        // sums; clear them so the handle's next application starts from zero
+        ctr_ibim* h = e->owner[q];
+        CTR_CUDA_TRY(cudaMemsetAsync(h->acc.p, 0, h->acc.bytes, e->stream));
+        CTR_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    }
     if (info) {
         info->iterations = st.iterations;
         info->refinements = st.refinements;

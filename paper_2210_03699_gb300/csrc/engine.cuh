@@ -9,7 +9,17 @@
 
 namespace ctr {
 
-enum : int { kSlotEmpty = 0, kSlotInner = 1, kSlotUpdate = 2, kSlotDone = 3, kSlotStart = 4 };
+// A slot whose operator application is split into parts (Engine::quantum_s) waits in kSlotInnerWait /
+// kSlotUpdateWait between the steps that run its parts.
+enum : int {
+    kSlotEmpty = 0,
+    kSlotInner = 1,
+    kSlotUpdate = 2,
+    kSlotDone = 3,
+    kSlotStart = 4,
+    kSlotInnerWait = 5,
+    kSlotUpdateWait = 6
+};
 
 // Per-slot counters and state, read back by the host after every step.
 struct SlotStat {
@@ -30,6 +40,8 @@ struct SlotDev {
     int refine, inner_prec, res_prec, max_refine;
     int res_update;          // refinement residuals after the first: r -= A d in the inner arithmetic
     int upd;                 // this cycle's residual is such an update (d = the cycle's correction, in z)
+    int part;                // part of the current operator application run in this step
+    int nparts[3];           // parts of one application per pair arithmetic (1: whole in one step)
     int64_t budget;
     // system (owned by the handle)
     const double* W;
@@ -70,6 +82,11 @@ struct Engine {
     bool var_used[pk::kNumVar32] = {};   // FP32 variants of the occupied slots
     int64_t steps = 0;
     int64_t kernels_per_step = 0;
+    // Pair work of one slot per step (seconds at kUnitRate): an application expected to take longer is
+    // split into parts (balanced sets of its schedule's items) run in consecutive steps, so that the
+    // steps of the other slots do not wait for it.  0: every application runs whole.  The exact node
+    // accumulators make the result independent of the split.
+    double quantum_s = 0.0;
     const float2* exp_tab = nullptr;
     bool kc_shared[3] = {false, false, false};   // all slots of an arithmetic share their pair constants
     pk::PairConsts kc_val[3] = {};               // ... and these are they (launch parameter)

@@ -13,8 +13,9 @@
 // block pair with J > I gets symmetric items.  Since the correction nodes of i
 // lie within a few h of P_i, near pairs form a band around the diagonal.
 //
-// Items are split to at most a quarter-wave of work each and sorted by cost
-// for the atomic-counter scheduler.  Every item adds its sums into the nodes'
+// Items are split to at most a quarter-wave of work each, and to at most
+// kItemSeconds of one resident block's time, and sorted by cost for the
+// atomic-counter scheduler.  Every item adds its sums into the nodes'
 // exact accumulators (pairkern.cuh, fx_add: integer addition, so the order in
 // which blocks add does not change a bit of the result).
 #include <algorithm>
@@ -117,8 +118,8 @@ int sched_launch(ctr_ibim* s, int pol, const void* src, const PairConsts& kc, in
 }
 
 // Items of one arithmetic for a system of M nodes with the given near-flag matrix.
-void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost, const std::vector<uint8_t>& flags,
-                   int g0, int nb0, int slots) {
+void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost, double item_cost,
+                   const std::vector<uint8_t>& flags, int g0, int nb0, int slots) {
     p.R = R;
     p.BS = kThreads * R;
     p.tile = tile;
@@ -162,8 +163,11 @@ void plan_schedule(PairSchedule& p, int64_t M, int R, int tile, double sym_cost,
         }
     }
     for (const Run& r : runs) total += (double)BS * (r.j1 - r.j0) * (r.sym ? sym_cost : 1.0);
-    // split runs into items of at most a quarter-wave of work (whole tiles, at least two when possible)
-    const double cmax = std::max(1.0, total / ((double)kItemsPerSlot * std::max(1, slots)));
+    // split runs into items of at most a quarter-wave of work and kItemSeconds of one block (item_cost:
+    // the arithmetic's rate x kItemSeconds; whole tiles, at least two when possible)
+    const double nslots = (double)std::max(1, slots);
+    const double cmax = std::max(1.0, std::min(total / ((double)kItemsPerSlot * nslots), item_cost / nslots));
+    p.total_cost = total;
     p.items.clear();
     p.cost.clear();
     p.pairs_sym = p.pairs_one = 0;
@@ -237,8 +241,8 @@ int plan_fp32(ctr_ibim* s, const std::vector<uint8_t>& flags, int g0, int nb0, i
     auto plan = [&](int v) -> int {
         const int per = with_var32(v, PerSm{});
         if (per < 0) return per;
-        plan_schedule(s->sched[0], M, kVar32[v].R * Fp32x2Policy::kPack, kVar32[v].tile, kSymCost[0], flags, g0, nb0,
-                      per * sms);
+        plan_schedule(s->sched[0], M, kVar32[v].R * Fp32x2Policy::kPack, kVar32[v].tile, kSymCost[0],
+                      kUnitRate[0] * kItemSeconds[0], flags, g0, nb0, per * sms);
         CTR_TRY(upload_schedule(s->sched[0], M, s->stream));
         s->sched[0].var = v;
         return CTR_OK;
@@ -345,7 +349,8 @@ int build_schedules(ctr_ibim* s, const int slots[3]) {
     const int Rs[3] = {0, kRdf, kR64};   // targets per thread of the fixed shapes
     const int tiles[3] = {0, Df64Policy::kTile, Fp64Policy::kTile};
     for (int p = 1; p < 3; ++p) {
-        plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], flags, g0, nb0, slots[p]);
+        plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], kUnitRate[p] * kItemSeconds[p], flags, g0, nb0,
+                      slots[p]);
         CTR_TRY(upload_schedule(s->sched[p], M, s->stream));
     }
     int sms = 0;

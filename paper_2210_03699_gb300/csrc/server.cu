@@ -371,6 +371,7 @@ void ctr_default_server_options(ctr_server_options* o) {
     if (!o) return;
     o->max_slots = 16;
     o->hbm_budget_bytes = 0;
+    o->step_quantum_ms = 20.0;
 }
 
 int ctr_server_create(const ctr_server_options* opt, ctr_server** out) {
@@ -380,6 +381,8 @@ int ctr_server_create(const ctr_server_options* opt, ctr_server** out) {
     ctr_default_server_options(&o);
     if (opt) o = *opt;
     if (o.max_slots <= 0 || o.max_slots > 4096) return fail(CTR_ERR_INVALID, "max_slots must be in [1, 4096]");
+    if (!(o.step_quantum_ms >= 0.0 && o.step_quantum_ms <= 1e6))
+        return fail(CTR_ERR_INVALID, "step_quantum_ms must be in [0, 1e6]");
     ctr_server* sv = new ctr_server();
     if (cudaGetDevice(&sv->device) != cudaSuccess) {
         delete sv;
@@ -402,6 +405,7 @@ int ctr_server_create(const ctr_server_options* opt, ctr_server** out) {
         return st;
     }
     sv->engine->vec_blocks = 1;
+    sv->engine->quantum_s = o.step_quantum_ms * 1e-3;
     sv->worker = std::thread(worker_loop, sv);
     sv->setup = std::thread(setup_loop, sv);
     *out = sv;
