@@ -45,7 +45,7 @@ RESTART, INNER_TOL, SOLVE_TOL = 64, 1e-5, 1e-10
 # in-warp transposed sums), for the packed FP32 and the float-float pair arithmetics (a packed f32x2
 # instruction counts as two lane operations, the FMA pipe's throughput being the same either way).
 # SFU work (rsqrt, ex2) and shared-memory loads are not counted.
-OPS_FP32 = {"one": 41, "sym": 50}
+OPS_FP32 = {"one": 41, "sym": 49}
 OPS_DF64 = {"one": 507, "sym": 501}
 # FP64 pipe lane operations per pair evaluation of the FP64 schedule (CUDA's exp and rsqrt included): the
 # ncu count sm__inst_executed_pipe_fp64 x 32 / evaluations over one launch at h = 0.1 (69); its peak is the
@@ -436,9 +436,15 @@ def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, c
         lat = np.array([r.latency for r in res])
         t_first = min(r.t_submit for r in res)
         t_last = max(r.t_done for r in res)
+        statuses = {}
+        for r in res:
+            statuses[str(r.status)] = statuses.get(str(r.status), 0) + 1
+        failed = [{"pick": int(picks[i]), "status": res[i].status, "M": res[i].M,
+                   "iterations": res[i].info.iterations} for i in range(n) if res[i].status != 0][:8]
         return {"requests": n, "solves_per_s": n / (t_last - t_first), "p50_s": float(np.percentile(lat, 50)),
                 "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
-                "all_ok": all(r.status == 0 for r in res), "peak_slots": st["peak_slots"],
+                "all_ok": all(r.status == 0 for r in res), "statuses": statuses, "failed": failed,
+                "peak_slots": st["peak_slots"],
                 "peak_used_GB": st["peak_used_bytes"] / 1e9, "steps": st["steps"],
                 "energies": [(int(picks[i]), res[i].G_pol) for i in range(n)]}
 

@@ -860,7 +860,11 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
         const PairSchedule& sc = s->sched[p];
         int64_t np = 1;
         if (e->quantum_s > 0.0 && !s->tree) {
-            np = (int64_t)std::ceil(sc.total_cost / kUnitRate[p] / e->quantum_s);
+            // a part lasts at least as long as its longest item runs on one block (kItemSeconds): keep
+            // every part at twice that or more, and at kMinItemsPerPart items or more
+            const double t = sc.total_cost / kUnitRate[p];
+            np = (int64_t)std::ceil(t / e->quantum_s);
+            np = std::min<int64_t>(np, (int64_t)(t / (2.0 * kItemSeconds[p])));
             np = std::min<int64_t>(np, (int64_t)sc.items.size() / kMinItemsPerPart);
         }
         d.nparts[p] = (int)std::max<int64_t>(1, std::min<int64_t>(np, kMaxParts));

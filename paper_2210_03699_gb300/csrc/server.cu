@@ -87,6 +87,7 @@ struct ctr_server {
     std::deque<ctr::Request*> waiting;
     std::deque<ctr::Request*> ready;     // set up, not yet in an engine slot
     int preparing = 0;                   // requests the setup thread is working on
+    int admitting = 0;                   // set-up requests the worker has taken from `ready` to admit
     std::map<uint64_t, ctr::Request*> all;
     std::vector<ctr::Request*> running;
     uint64_t next_ticket = 1;
@@ -172,7 +173,7 @@ void setup_loop(ctr_server* sv) {
             auto can = [&] {
                 if (sv->stop || sv->fatal) return true;
                 if (sv->waiting.empty()) return false;
-                const int in_flight = (int)(sv->running.size() + sv->ready.size()) + sv->preparing;
+                const int in_flight = (int)(sv->running.size() + sv->ready.size()) + sv->preparing + sv->admitting;
                 if (in_flight >= sv->cap) return false;
                 // the oldest request goes in when it fits, or alone when it exceeds the budget
                 return sv->used + sv->waiting.front()->need <= sv->budget || in_flight == 0;
@@ -254,6 +255,7 @@ void worker_loop(ctr_server* sv) {
                 sv->cv_work.wait(lk, [&] { return sv->stop || !sv->ready.empty(); });
             if (sv->stop) break;
             take.swap(sv->ready);
+            sv->admitting = (int)take.size();   // still holding slots until admitted (or dropped)
         }
         for (Request* r : take) {
             bool cancelled;
@@ -265,6 +267,7 @@ void worker_loop(ctr_server* sv) {
                 ctr_ibim_destroy(r->sys);
                 release_stream(r);
                 std::lock_guard<std::mutex> lk(sv->mu);
+                sv->admitting--;
                 r->sys = nullptr;
                 sv->used -= r->charged;
                 r->charged = 0;
@@ -279,6 +282,7 @@ void worker_loop(ctr_server* sv) {
                 release_stream(r);
             }
             std::lock_guard<std::mutex> lk(sv->mu);
+            sv->admitting--;
             if (s1 < 0) {
                 r->sys = nullptr;
                 sv->used -= r->charged;
@@ -522,7 +526,7 @@ int ctr_server_stats(ctr_server* sv, ctr_server_stats_t* out) {
     out->peak_used_bytes = sv->peak_used;
     out->peak_slots = sv->peak_slots;
     out->running = (int)sv->running.size();
-    out->waiting = (int)(sv->waiting.size() + sv->ready.size()) + sv->preparing;
+    out->waiting = (int)(sv->waiting.size() + sv->ready.size()) + sv->preparing + sv->admitting;
     out->steps = sv->steps;
     return CTR_OK;
 }
