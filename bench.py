@@ -55,7 +55,8 @@ OPS_FP64 = {"one": 69, "sym": 69}
 # ncu capture, valid only while the kernel sources hash to `sources` (otherwise reported as null).
 TRAFFIC = {"profile": "profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt", "h": 0.05,
            "sources": None, "fp32": 2.286e8, "df64": 1.0483e9, "fp64": None}
-KERNEL_SOURCES = ("paper_2210_03699_gb300/csrc/pairkern.cuh", "paper_2210_03699_gb300/csrc/schedule.cu")
+KERNEL_SOURCES = ("paper_2210_03699_gb300/csrc/pairkern.cuh", "paper_2210_03699_gb300/csrc/schedule.cu",
+                  "paper_2210_03699_gb300/csrc/common.cuh")
 # Treecode far field of the FP32 operator (FP32 charges): FMA-pipe lane operations per proxy evaluation
 # counted from the kernel source (tree.cuh, k_tree_far2: 1 sub, 6 fma, 7 mul; an f32x2 instruction does
 # two), plus 2 SFU operations (rsqrt, ex2).  The float-float operator's far field (k_tree_far_ff): 196
@@ -120,6 +121,8 @@ def parse():
     ap.add_argument("--loads", default="0.8", help="serve mode: offered load / measured capacity (comma list)")
     ap.add_argument("--pool", type=int, default=12, help="serve mode: distinct problems requests draw from")
     ap.add_argument("--slots", type=int, default=16, help="serve mode: server slots")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="serve mode: one run at this arrival rate (requests/s) instead of the capacity run and loads")
     ap.add_argument("--step-quantum-ms", type=float, default=20.0,
                     help="serve: pair work of one system per engine step (longer applications run in parts; 0: whole)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per run of the default line's serve object")
@@ -399,7 +402,8 @@ def fp64_pool_times(ctr, pool, max_M):
     return Ms, G64, t
 
 
-def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, cap_requests=None, quantum_ms=20.0):
+def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, cap_requests=None, quantum_ms=20.0,
+                     rate=None):
     """Continuous-batching server over a pool of problems: capacity with every request submitted at once,
     then Poisson arrivals at each fraction of it; per load solves/s and p50/p99 latency (submission to
     result).  Served energies are compared with the plain FP64 one-at-a-time GPU path on every pool problem
@@ -449,13 +453,18 @@ def serve_experiment(ctr, pool, n_requests, loads, slots, fp64_max_M, seed=11, c
                 "energies": [(int(picks[i]), res[i].G_pol) for i in range(n)]}
 
     run_load(None, min(len(pool), 4), 7)              # warm-up (autotuning, first touch)
-    cap = run_load(None, cap_requests or n_requests, seed)   # saturated: everything submitted at once
-    capacity = cap["solves_per_s"]
-    levels = {f"{f:g}": run_load(f * capacity, n_requests, seed + 2) for f in loads}
+    if rate is not None:   # one run at a fixed arrival rate (policies compared on the same arrivals)
+        cap, capacity = None, None
+        levels = {f"rate {rate:g}/s": run_load(rate, n_requests, seed + 2)}
+    else:
+        cap = run_load(None, cap_requests or n_requests, seed)   # saturated: everything submitted at once
+        capacity = cap["solves_per_s"]
+        levels = {f"{f:g}": run_load(f * capacity, n_requests, seed + 2) for f in loads}
     # the plain FP64 one-at-a-time GPU path on the sample
     Ms, G64, t64 = fp64_pool_times(ctr, pool, fp64_max_M)
-    errs = [abs(e / G64[k] - 1) for lv in list(levels.values()) + [cap] for k, e in lv["energies"] if k in G64]
-    for lv in list(levels.values()) + [cap]:
+    runs = list(levels.values()) + ([cap] if cap else [])
+    errs = [abs(e / G64[k] - 1) for lv in runs for k, e in lv["energies"] if k in G64]
+    for lv in runs:
         lv.pop("energies")
     n64 = len(t64)
     return {"capacity_solves_per_s": capacity, "saturated": cap, "levels": levels,
@@ -513,8 +522,9 @@ def run_serve(args, ctr):
         return
     out = serve_experiment(ctr, pool, n_requests=args.requests, loads=[float(v) for v in args.loads.split(",") if v],
                            slots=args.slots, fp64_max_M=args.fp64_max_M, cap_requests=args.capacity_requests,
-                           quantum_ms=args.step_quantum_ms)
-    line = {"metric": "CTR-IBIM served solves/s", "value": out["levels"][max(out["levels"], key=float)]["solves_per_s"],
+                           quantum_ms=args.step_quantum_ms, rate=args.rate)
+    top = list(out["levels"])[-1] if args.rate is not None else max(out["levels"], key=float)   # highest load
+    line = {"metric": "CTR-IBIM served solves/s", "value": out["levels"][top]["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 pairs + f64",
             "data": "synthetic",
             "config": {"workload": f"{args.requests} requests per load level, Poisson arrivals, drawn from a pool of "

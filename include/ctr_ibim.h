@@ -361,12 +361,14 @@ typedef struct ctr_server ctr_server;
 typedef struct {
     int max_slots;             /* systems resident at once, 1..4096 (default 16) */
     int64_t hbm_budget_bytes;  /* device memory the resident systems may hold; <= 0: 80% of free memory */
-    /* Pair work of one system per engine step, in milliseconds at the GPU's estimated pair rate
-     * (default 20; 0: never split).  A system whose operator application would take longer runs it
-     * in parts over consecutive steps (at most 127, each a balanced set of its schedule's items, at
-     * least 64 items each), so that small systems in the same engine are not held back by a large
-     * one's application.  The node accumulators are exact, so the result does not depend on the
-     * split.  Must be finite and in [0, 1e6]; CTR_ERR_INVALID otherwise. */
+    /* Size of the parts of a large operator application, in milliseconds at the GPU's estimated
+     * pair rate (default 20; 0: never split).  A system whose application would take longer runs it
+     * in parts over consecutive engine steps (at most 127, each a balanced set of its schedule's
+     * items, at least 64 items and twice the longest item's time each).  In every step such a system
+     * runs one part, or as many as fit in the pair work of all other systems in that step: small
+     * systems are not held back for a large system's whole application, and a large system keeps
+     * about half of a busy step.  The node accumulators are exact, so the result does not depend
+     * on the split.  Must be finite and in [0, 1e6]; CTR_ERR_INVALID otherwise. */
     double step_quantum_ms;
 } ctr_server_options;
 

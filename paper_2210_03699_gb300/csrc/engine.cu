@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* _
         const SlotDev& s = S[w.x];
         const bool want = half == 0 ? (inner_active(s) && s.inner_prec == prec)
                                     : (update_active(s) && res_arith(s) == prec);
-        if (!want || (w.y >> kPartShift) != s.part) continue;
+        const int pe = w.y >> kPartShift;
+        if (!want || pe < s.part || pe >= s.part + s.span) continue;
         const int item = w.y & kItemMask;
         const Src* src = reinterpret_cast<const Src*>(prec == CTR_FP32_REFINE ? (const void*)s.src32
                                                       : prec == CTR_DF64 ? (const void*)s.srcdf
@@ -382,16 +383,48 @@ __global__ void k_start_scalars(SlotDev* S, int cap) {
     s.stat.state = kSlotInner;
 }
 
-// Start of a step: slots between two parts of an application take their next part.
-__global__ void k_resume(SlotDev* S, int cap) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= cap) return;
-    SlotDev& s = S[q];
-    if (s.stat.state == kSlotInnerWait) s.stat.state = kSlotInner;
-    else if (s.stat.state == kSlotUpdateWait) s.stat.state = kSlotUpdate;
+__device__ __forceinline__ int arith_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
+
+// Estimated pair work of a slot in the step ahead (seconds), and its arithmetic.
+__device__ __forceinline__ float step_work(const SlotDev& s, int& a) {
+    if (s.stat.state == kSlotInner) a = arith_index(s.inner_prec);
+    else if (s.stat.state == kSlotUpdate) a = arith_index(res_arith(s));
+    else return 0.f;
+    return s.part_s[a];
 }
 
-__device__ __forceinline__ int arith_index(int prec) { return prec == CTR_FP32_REFINE ? 0 : (prec == CTR_DF64 ? 1 : 2); }
+// Start of a step (one block): slots between two parts of an application resume; every slot whose
+// application is split gets its span of parts for this step: at least one, and as many as fit in the
+// pair work of all other slots in the step, so that a large system takes at most about half of a busy
+// step and the whole of an idle one, while the others' steps grow by one part at a time.
+__global__ void k_plan_step(SlotDev* S, int cap) {
+    __shared__ float red[kVecThreads];
+    float w = 0.f;
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) {
+        SlotDev& s = S[q];
+        if (s.stat.state == kSlotInnerWait) s.stat.state = kSlotInner;
+        else if (s.stat.state == kSlotUpdateWait) s.stat.state = kSlotUpdate;
+        int a = 0;
+        w += step_work(s, a);
+    }
+    red[threadIdx.x] = w;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const float total = red[0];
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) {
+        SlotDev& s = S[q];
+        int a = 0;
+        const float mine = step_work(s, a);
+        s.span = 1;
+        if (mine > 0.f && s.nparts[a] > 1) {
+            const float fit = floorf((total - mine) / mine);
+            s.span = max(1, min(s.nparts[a] - s.part, (int)fminf(fit, (float)kMaxParts)));
+        }
+    }
+}
 
 // After a half's pair launches: a slot whose application has parts left waits for the next step (the
 // rest of this step skips it); one that ran its last part goes on to finish the application.
@@ -401,11 +434,12 @@ __global__ void k_part(SlotDev* S, int cap, int half) {
     SlotDev& s = S[q];
     if (half == 0 ? !inner_active(s) : !update_active(s)) return;
     const int np = s.nparts[arith_index(half == 0 ? s.inner_prec : res_arith(s))];
-    if (s.part + 1 < np) {
-        s.part += 1;
+    if (s.part + s.span < np) {
+        s.part += s.span;
         s.stat.state = half == 0 ? kSlotInnerWait : kSlotUpdateWait;
     } else {
         s.part = 0;
+        s.span = 1;   // a residual started later in this step runs one part
     }
 }
 
@@ -727,7 +761,7 @@ static int enqueue_step(Engine* e) {
     const int mx = e->max_nblk;
     const dim3 vec(e->vec_blocks, cap);
     const unsigned one = grid_for(cap, 128);
-    k_resume<<<one, 128, 0, st>>>(S, cap);
+    k_plan_step<<<1, kVecThreads, 0, st>>>(S, cap);
     CTR_LAUNCHED();
     // ---- inner half: one Arnoldi iteration
     k_prep_inner<<<vec, kVecThreads, 0, st>>>(S);
@@ -868,7 +902,9 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
             np = std::min<int64_t>(np, (int64_t)sc.items.size() / kMinItemsPerPart);
         }
         d.nparts[p] = (int)std::max<int64_t>(1, std::min<int64_t>(np, kMaxParts));
+        d.part_s[p] = (float)(sc.total_cost / kUnitRate[p] / d.nparts[p]);
     }
+    d.span = 1;
     CTR_TRY(pair_consts(s, true, &d.kc));
     for (int p = 0; p < 3; ++p) {
         d.items[p] = s->sched[p].d_items.as<PairItem>();

@@ -40,8 +40,10 @@ struct SlotDev {
     int refine, inner_prec, res_prec, max_refine;
     int res_update;          // refinement residuals after the first: r -= A d in the inner arithmetic
     int upd;                 // this cycle's residual is such an update (d = the cycle's correction, in z)
-    int part;                // part of the current operator application run in this step
+    int part;                // first part of the current operator application run in this step
+    int span;                // parts run in this step (set by the step's planning kernel)
     int nparts[3];           // parts of one application per pair arithmetic (1: whole in one step)
+    float part_s[3];         // estimated seconds of one part (of the whole application when nparts = 1)
     int64_t budget;
     // system (owned by the handle)
     const double* W;
@@ -82,9 +84,10 @@ struct Engine {
     bool var_used[pk::kNumVar32] = {};   // FP32 variants of the occupied slots
     int64_t steps = 0;
     int64_t kernels_per_step = 0;
-    // Pair work of one slot per step (seconds at kUnitRate): an application expected to take longer is
-    // split into parts (balanced sets of its schedule's items) run in consecutive steps, so that the
-    // steps of the other slots do not wait for it.  0: every application runs whole.  The exact node
+    // Part size (seconds at kUnitRate): an application expected to take longer is split into parts
+    // (balanced sets of its schedule's items) run over consecutive steps, one or more per step (as
+    // many as fit in the other slots' work of the step; k_plan_step), so that the steps of the other
+    // slots do not wait for its whole application.  0: every application runs whole.  The exact node
     // accumulators make the result independent of the split.
     double quantum_s = 0.0;
     const float2* exp_tab = nullptr;
