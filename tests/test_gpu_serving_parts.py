@@ -129,3 +129,25 @@ def test_many_requests_at_once_are_all_admitted(ctr):
             assert r.status == 0 and r.G_pol == refs[k][2]
             sv.release(t)
         assert sv.stats()["peak_slots"] <= 2
+
+
+def test_served_result_matches_oracle(ctr, sphere_c1):
+    """A small request served beside a split 250k-node system, checked against the oracle's own solve
+    (FP64, GMRES to 1e-13) of the same sphere: psi, dpsi_n and G_pol within 1e-6 (the FP32+refinement
+    bar; observed about 1e-9)."""
+    from oracle import energy as oenergy
+    prob, S = sphere_c1
+    psi_o, dpsi_o, _ = S.solve(tol=1e-13)
+    Go, _ = oenergy.polarization_energy(S, psi_o, dpsi_o)
+    big = syn.sphere_with_nodes(250000)
+    with ctr.Server(max_slots=2, step_quantum_ms=10.0) as sv:
+        tb = sv.submit_problem(big, ctr.Options(tube_halfwidth=big.tube, precision=ctr.FP32_REFINE))
+        time.sleep(0.3)
+        ts = sv.submit_problem(prob, ctr.Options(tube_halfwidth=prob.tube, precision=ctr.FP32_REFINE))
+        r = sv.wait(ts, 300)
+        assert r.status == 0
+        psi, dpsi = sv.fetch(ts, r.M)
+        assert np.max(np.abs(psi - psi_o)) / np.max(np.abs(psi_o)) < 1e-6
+        assert np.max(np.abs(dpsi - dpsi_o)) / np.max(np.abs(dpsi_o)) < 1e-6
+        assert abs(r.G_pol / Go - 1) < 1e-6
+        assert sv.wait(tb, 300).status == 0
