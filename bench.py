@@ -59,11 +59,12 @@ KERNEL_SOURCES = ("paper_2210_03699_gb300/csrc/pairkern.cuh", "paper_2210_03699_
                   "paper_2210_03699_gb300/csrc/common.cuh")
 # Treecode far field of the FP32 operator (FP32 charges): FMA-pipe lane operations per proxy evaluation
 # counted from the kernel source (tree.cuh, k_tree_far2: 1 sub, 6 fma, 7 mul; an f32x2 instruction does
-# two), plus 2 SFU operations (rsqrt, ex2).  The float-float operator's far field (k_tree_far_ff): 196
-# FP32-pipe operations per evaluation (float-float differences, squares, dot products, rsqrt by one Newton
-# step, the table exponential, the two charge combinations and accumulations), 1 SFU operation.
+# two), plus 2 SFU operations (rsqrt, ex2).  The float-float operator's far field (k_tree_far_ff): 171
+# FP32 add/sub/mul/fma instructions per evaluation (difference 11, r^2 12, d.n 18, rsqrt by one Newton
+# step 16, kappa r 8, the table exponential 29, the two charge combinations and accumulations 27 and 31,
+# 1 + kappa r times E 11, r^-3 8; table indexing and loads not counted), 1 SFU operation.
 OPS_FAR = 14
-OPS_FAR_DF = 196
+OPS_FAR_DF = 171
 SFU_FAR = 2
 
 

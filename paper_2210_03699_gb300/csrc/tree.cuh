@@ -47,6 +47,17 @@ constexpr int kTreeR[3] = {4, 2, 1};
 constexpr int kTreeNT[3] = {256, 128, 256};
 constexpr int kChunkSrc = 2048;   // sources per moment chunk
 
+// Float-float sums of two values that cannot cancel (same sign), left unnormalised like pk::mull's
+// products: exact two_sum of the high parts, plain sum of the low parts.
+__device__ __forceinline__ pk::F2 ff_addl(pk::F2 a, pk::F2 b) {
+    const pk::F2 s = pk::two_sum(a.hi, b.hi);
+    return pk::F2{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ pk::F2 ff_add_fl(pk::F2 a, float b) {
+    const pk::F2 s = pk::two_sum(a.hi, b);
+    return pk::F2{s.hi, __fadd_rn(s.lo, a.lo)};
+}
+
 template <typename Real>
 __device__ __forceinline__ void tree_source(const TreeView& t, int pol, int64_t p, Real P[3], Real n[3], Real& a,
                                             Real& b) {
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(NT) k_tree_far_ff(Acc acc, const int2* __restr
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const F2 dz = pk::sub(pz[r], sz);
-                    dz2[r] = pk::mul(dz, dz);
+                    dz2[r] = pk::mull(dz, dz);
                     dzn[r] = pk::mul(dz, nz[r]);
                 }
                 for (int k2 = 0; k2 < n1; ++k2) {
@@ -533,7 +544,7 @@ __global__ void __launch_bounds__(NT) k_tree_far_ff(Acc acc, const int2* __restr
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const F2 dy = pk::sub(py[r], sy);
-                        ryz[r] = pk::add(pk::mul(dy, dy), dz2[r]);
+                        ryz[r] = ff_addl(pk::mull(dy, dy), dz2[r]);
                         dyzn[r] = pk::add(pk::mul(dy, ny[r]), dzn[r]);
                     }
                     const int kb = (k3 * n1 + k2) * n1;
@@ -543,16 +554,19 @@ __global__ void __launch_bounds__(NT) k_tree_far_ff(Acc acc, const int2* __restr
                                  qkp = pk::f2(sq[2 * np + kb + k1]);
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
+                            // lazy (unnormalised) values wherever no cancellation can follow: the squares
+                            // and r^2, kappa r, the exponential, 1 + kappa r and the products; the
+                            // differences, the dot product and the two charge combinations stay normalised
                             const F2 dx = pk::sub(px[r], sxk);
-                            const F2 r2 = pk::add(pk::mul(dx, dx), ryz[r]);
+                            const F2 r2 = ff_addl(pk::mull(dx, dx), ryz[r]);
                             const F2 dn = pk::add(pk::mul(dx, nx[r]), dyzn[r]);
                             const F2 ri = pk::rsqrt_ff(r2);
-                            const F2 kr = pk::mul(kap, pk::mul(r2, ri));
-                            const F2 E = pk::exp_neg_ff(kr, tab);
-                            pk::acc_add(a1[r], pk::mull(ri, pk::add(pk::mul(E, qk), q0)));
-                            const F2 Ef = pk::mul(E, pk::add_f(kr, 1.f));
+                            const F2 kr = pk::mull(kap, pk::mull(r2, ri));
+                            const F2 E = pk::exp_neg_ffl(kr, tab);
+                            pk::acc_add(a1[r], pk::mull(ri, pk::add(pk::mull(E, qk), q0)));
+                            const F2 Ef = pk::mull(E, ff_add_fl(kr, 1.f));
                             const F2 ri3 = pk::mull(pk::mull(ri, ri), ri);
-                            pk::acc_add(a2[r], pk::mull(pk::mull(dn, ri3), pk::add(pk::mul(Ef, qkp), q0)));   // -(out2)
+                            pk::acc_add(a2[r], pk::mull(pk::mull(dn, ri3), pk::add(pk::mull(Ef, qkp), q0)));   // -(out2)
                         }
                     }
                 }
