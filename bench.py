@@ -46,7 +46,7 @@ RESTART, INNER_TOL, SOLVE_TOL = 64, 1e-5, 1e-10
 # instruction counts as two lane operations, the FMA pipe's throughput being the same either way).
 # SFU work (rsqrt, ex2) and shared-memory loads are not counted.
 OPS_FP32 = {"one": 41, "sym": 49}
-OPS_DF64 = {"one": 507, "sym": 501}
+OPS_DF64 = {"one": 423, "sym": 501}
 # FP64 pipe lane operations per pair evaluation of the FP64 schedule (CUDA's exp and rsqrt included): the
 # ncu count sm__inst_executed_pipe_fp64 x 32 / evaluations over one launch at h = 0.1 (69); its peak is the
 # measured DFMA probe rate, there being no FP64 unit count to go by.

@@ -725,30 +725,33 @@ struct Df64Policy {
             Pz = T.pz;
             A = Bw = F2{0.f, 0.f};
         }
+        // lazy products and unnormalised accumulation as in pair_sym (the target rows of its terms); the
+        // differences that can cancel (d, the dot products, 1 - E, 1 - E1, 3 - E q, X) stay normalised
         const F2 dx = sub(T.px, Px), dy = sub(T.py, Py), dz = sub(T.pz, Pz);
         const F2 r2 = dot3(dx, dy, dz, dx, dy, dz);
         const F2 rinv = rsqrt_ff(r2);
-        const F2 r = mul(r2, rinv);
-        const F2 kr = mul(f2(k.kappad), r);
-        const F2 E = exp_neg_ff(kr, tab);
-        const F2 E1 = mul(E, add_f(kr, 1.f));
+        const F2 r = mull(r2, rinv);
+        const F2 kr = mull(f2(k.kappad), r);
+        const F2 E = exp_neg_ffl(kr, tab);
+        const F2 E1 = mull(E, add_f(kr, 1.f));
         const F2 dny = dot3(dx, dy, dz, Nx, Ny, Nz);
         const F2 dnx = dot3(dx, dy, dz, T.qx, T.qy, T.qz);
         const F2 nn = dot3(T.qx, T.qy, T.qz, Nx, Ny, Nz);
-        const F2 rinv2 = mul(rinv, rinv);
-        const F2 s = mul(rinv2, rinv);
-        const F2 as = mul(A, s), bs = mul(Bw, s);
-        const F2 t1 = add_f(neg(mul(E1, f2(k.c1d))), 1.f);
-        acc.a1 = add(acc.a1, mul(as, mul(dny, t1)));
-        const F2 om = mul(rinv, add_f(neg(E), 1.f));
-        acc.a1 = sub(acc.a1, mul(Bw, om));
-        const F2 t2 = add_f(neg(mul(E1, f2(k.c2d))), 1.f);
-        acc.a2 = add(acc.a2, mul(bs, mul(dnx, t2)));
+        const F2 rinv2 = mull(rinv, rinv);
+        const F2 s = mull(rinv2, rinv);
+        const F2 t1 = add_f(neg(mull(E1, f2(k.c1d))), 1.f);
+        const F2 om = mull(rinv, add_f(neg(E), 1.f));
+        const F2 t2 = add_f(neg(mull(E1, f2(k.c2d))), 1.f);
         const F2 u = add_f(neg(E1), 1.f);
-        const F2 q = add_f(mul(kr, add_f(kr, 3.f)), 3.f);
-        const F2 t3 = add_f(neg(mul(E, q)), 3.f);
-        const F2 Bt = mul(mul(t3, mul(dnx, dny)), rinv2);
-        acc.a2 = add(acc.a2, mul(as, sub(mul(u, nn), Bt)));
+        const F2 q = add_f(mull(kr, add_f(kr, 3.f)), 3.f);
+        const F2 t3 = add_f(neg(mull(E, q)), 3.f);
+        const F2 Bt = mull(mull(t3, mull(dnx, dny)), rinv2);
+        const F2 X = sub(mull(u, nn), Bt);
+        const F2 as = mull(A, s), bs = mull(Bw, s);
+        acc_add(acc.a1, mull(as, mull(dny, t1)));
+        acc_add(acc.a1, neg(mull(Bw, om)));
+        acc_add(acc.a2, mull(bs, mull(dnx, t2)));
+        acc_add(acc.a2, mull(as, X));
     }
     // Both orientations with lazy products (mull) and unnormalised accumulation (acc_add); the
     // differences that can cancel (d, the dot products, 1 - E, 1 - E1, 3 - E q, X) stay normalised.
