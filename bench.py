@@ -54,7 +54,7 @@ OPS_FP64 = {"one": 69, "sym": 69}
 # DRAM bytes (read + write) per launch of the schedule kernels at the default workload (h = 0.05) from one
 # ncu capture, valid only while the kernel sources hash to `sources` (otherwise reported as null).
 TRAFFIC = {"profile": "profiles/dram_traffic_sched_kernels_ellipsoid_h0.05.txt", "h": 0.05,
-           "sources": "4bab67d8f7072ead", "fp32": 2.670e7, "df64": 3.297e7, "fp64": None}
+           "sources": "03cf69bebaf50fb0", "fp32": 2.659e7, "df64": 3.306e7, "fp64": None}
 KERNEL_SOURCES = ("paper_2210_03699_gb300/csrc/pairkern.cuh", "paper_2210_03699_gb300/csrc/schedule.cu",
                   "paper_2210_03699_gb300/csrc/common.cuh")
 # Treecode far field of the FP32 operator (FP32 charges): FMA-pipe lane operations per proxy evaluation

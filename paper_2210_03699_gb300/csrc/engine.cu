@@ -394,9 +394,9 @@ __device__ __forceinline__ float step_work(const SlotDev& s, int& a) {
 }
 
 // Start of a step (one block): slots between two parts of an application resume; every slot whose
-// application is split gets its span of parts for this step: at least one, and as many as fit in the
-// pair work of all other slots in the step, so that a large system takes at most about half of a busy
-// step and the whole of an idle one, while the others' steps grow by one part at a time.
+// application is split gets its span of parts for this step: one, or as many as fit in the pair work of
+// all other slots in the step.  A large system thus takes about half of a busy step and one part of an
+// otherwise idle one, and the other slots' steps grow by at most that much.
 __global__ void k_plan_step(SlotDev* S, int cap) {
     __shared__ float red[kVecThreads];
     float w = 0.f;
