@@ -131,8 +131,10 @@ template <typename Policy, int R, int V, int U, bool kShared>
 __global__ void __launch_bounds__(kThreads, 2) k_pairs(SlotDev* S, const int2* __restrict__ items,
                                                     const int* __restrict__ n_items, int* __restrict__ counter,
                                                     int half, int prec, int pol, const float2* __restrict__ exp_tab,
-                                                    int* __restrict__ err, const PairConsts pkc) {
+                                                    int* __restrict__ err, const PairConsts pkc,
+                                                    const int* __restrict__ need) {
     using Src = typename Policy::Src;
+    if (need[pol] == 0) return;   // no slot in this half uses this arithmetic: skip the whole list
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PairSmem<Policy> sm(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
@@ -426,6 +428,22 @@ __global__ void k_plan_step(SlotDev* S, int cap) {
     }
 }
 
+// Before a half's pair launches (one block): which pair arithmetics any slot applies in this half (the
+// inner arithmetic of slots in INNER, the residual arithmetic of slots in UPDATE).  The persistent pair
+// kernels of the others return at once instead of walking their whole work lists.
+__global__ void k_need(const SlotDev* S, int cap, int half, int* need) {
+    __shared__ int f[3];
+    if (threadIdx.x < 3) f[threadIdx.x] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) {
+        const SlotDev& s = S[q];
+        if (half == 0 ? inner_active(s) : update_active(s))
+            f[arith_index(half == 0 ? s.inner_prec : res_arith(s))] = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) need[threadIdx.x] = f[threadIdx.x];
+}
+
 // After a half's pair launches: a slot whose application has parts left waits for the next step (the
 // rest of this step skips it); one that ran its last part goes on to finish the application.
 __global__ void k_part(SlotDev* S, int cap, int half) {
@@ -470,7 +488,8 @@ int launch_persistent_k(Engine* e, int pol, int var, int half, int prec) {
     const int list = pol * kNV + var;
     k_pairs<Policy, R, V, U, kShared><<<per_sm * e->sms, kThreads, smem, e->stream>>>(
         e->slots.as<SlotDev>(), e->items[pol][var].as<int2>(), e->n_items.as<int>() + list,
-        e->counters.as<int>() + 2 * list + half, half, prec, pol, e->exp_tab, e->err.as<int>(), e->kc_val[pol]);
+        e->counters.as<int>() + 2 * list + half, half, prec, pol, e->exp_tab, e->err.as<int>(), e->kc_val[pol],
+        e->need.as<int>());
     CTR_LAUNCHED();
     return CTR_OK;
 }
@@ -587,6 +606,7 @@ int engine_create(int device, int cap, Engine** out) {
     if (cudaMemsetAsync(e->tree_cnt.p, 0, sizeof(int) * 9, stream) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "memset"));
     if ((st = e->err.alloc(sizeof(int))) < 0) return bad(st);
+    if ((st = e->need.alloc(sizeof(int) * 3)) < 0) return bad(st);
     if (cudaMemsetAsync(e->err.p, 0, sizeof(int), stream) != cudaSuccess) return bad(fail(CTR_ERR_CUDA, "memset"));
     if (cudaMemsetAsync(e->n_items.p, 0, sizeof(int) * 3 * kNV, stream) != cudaSuccess)
         return bad(fail(CTR_ERR_CUDA, "memset"));
@@ -768,6 +788,8 @@ static int enqueue_step(Engine* e) {
     CTR_LAUNCHED();
     CTR_CUDA_TRY(cudaMemsetAsync(e->counters.p, 0, sizeof(int) * 2 * 3 * kNV, st));
     if (e->any_tree) CTR_CUDA_TRY(cudaMemsetAsync(e->tree_counters.p, 0, sizeof(int) * 12, st));
+    k_need<<<1, kVecThreads, 0, st>>>(S, cap, 0, e->need.as<int>());
+    CTR_LAUNCHED();
     CTR_TRY(launch_fp32(e, 0));
     CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, 0, CTR_DF64)));
     CTR_TRY((launch_persistent<Fp64Policy, kR64, kChunk64, 1>(e, 2, 0, 0, CTR_FP64)));
@@ -798,6 +820,8 @@ static int enqueue_step(Engine* e) {
     k_upper_solve<<<one, 128, 0, st>>>(S, cap);
     CTR_LAUNCHED();
     k_update_x<<<vec, kVecThreads, 0, st>>>(S);
+    CTR_LAUNCHED();
+    k_need<<<1, kVecThreads, 0, st>>>(S, cap, 1, e->need.as<int>());
     CTR_LAUNCHED();
     CTR_TRY(launch_fp32(e, 1));
     CTR_TRY((launch_persistent<Df64Policy, kRdf, kChunkDf, 1>(e, 1, 0, 1, CTR_DF64)));

@@ -96,6 +96,7 @@ struct Engine {
     std::vector<SlotDev> host;
     std::vector<ctr_ibim*> owner;
     DevBuf slots, stats, items[3][pk::kNumVar32], n_items, counters, err;
+    DevBuf need;   // per pair arithmetic: does any slot need its pair launch in the current half (k_need)
     // treecode work entries (slot, index) per pair arithmetic: moment chunks, far clusters, far items
     bool any_tree = false;
     int tree_np[3] = {0, 0, 0};   // largest proxy count per arithmetic among the treecode slots
