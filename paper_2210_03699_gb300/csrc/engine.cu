@@ -993,7 +993,7 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
         e->vec_blocks = vb;
         e->graph_dirty = true;
     }
-    CTR_TRY(rebuild_items(e));
+    e->lists_dirty = true;   // the work lists gain its items before the next step
     *slot_out = q;
     return CTR_OK;
 }
@@ -1023,11 +1023,15 @@ int engine_retire(Engine* e, int q, ctr_solve_info* info) {
     e->host[q] = empty;
     e->owner[q] = nullptr;
     CTR_CUDA_TRY(cudaMemcpyAsync(e->slots.as<SlotDev>() + q, &empty, sizeof(SlotDev), cudaMemcpyHostToDevice, e->stream));
-    CTR_TRY(rebuild_items(e));
+    e->lists_dirty = true;   // its entries are inert (an empty slot matches no state) until the next rebuild
     return st.numeric_error ? fail(CTR_ERR_NUMERIC, "non-finite residual") : CTR_OK;
 }
 
 int engine_step(Engine* e, std::vector<SlotStat>* stats) {
+    if (e->lists_dirty) {   // one rebuild for all admissions and retirements since the last step
+        CTR_TRY(rebuild_items(e));
+        e->lists_dirty = false;
+    }
     CTR_TRY(ensure_graph(e));
     if (e->graph_exec) {
         CTR_CUDA_TRY(cudaGraphLaunch(e->graph_exec, e->stream));

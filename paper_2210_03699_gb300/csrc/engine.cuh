@@ -75,6 +75,7 @@ struct Engine {
     int cap = 0;
     bool use_graph = true;
     bool graph_dirty = true;
+    bool lists_dirty = false;   // slots admitted or retired since the work lists were built (engine_step rebuilds)
     int vec_blocks = 1;
     int max_nblk = 1;
     int max_m = 1;
