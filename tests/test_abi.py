@@ -51,6 +51,10 @@ def test_status_strings_and_defaults(library):
     d = ctr.Options()
     assert (d.tree_degree, d.tree_theta, d.tree_leaf, d.tree_degree_fp32, d.tree_theta_fp32) == (
         o.tree_degree, o.tree_theta, o.tree_leaf, o.tree_degree_fp32, o.tree_theta_fp32)
+    # server options: the binding's struct has the C layout (defaults written by the library)
+    so = ctr._ServerOptions(0, 7, -1.0)
+    ctr.lib.ctr_default_server_options(ctypes.byref(so))
+    assert (so.max_slots, so.hbm_budget_bytes, so.step_quantum_ms) == (16, 0, 20.0)
 
 
 def test_invalid_arguments_rejected_without_gpu(library):
@@ -70,3 +74,8 @@ def test_invalid_arguments_rejected_without_gpu(library):
     assert ctr.lib.ctr_ibim_time_operator(None, ctr.FP32_REFINE, 1, ctypes.byref(d), None, None, None) == -1
     assert ctr.lib.ctr_farfield_plan(0, None, None, None, 2, 10, 0.8, 128, 256, 0, None, None, None, None, None,
                                      None, None, None) == -1
+    # server options are validated before any device call
+    sv = ctypes.c_void_p()
+    for bad in (ctr._ServerOptions(0, 0, 20.0), ctr._ServerOptions(4, 0, -1.0),
+                ctr._ServerOptions(4, 0, float("nan")), ctr._ServerOptions(4, 0, float("inf"))):
+        assert ctr.lib.ctr_server_create(ctypes.byref(bad), ctypes.byref(sv)) == -1 and sv.value is None
