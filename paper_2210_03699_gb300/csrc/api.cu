@@ -121,6 +121,8 @@ int ctr_ibim_pair_tuning(const ctr_ibim* s, int precision, int* block_targets, i
     if (precision != CTR_FP32_REFINE && precision != CTR_DF64 && precision != CTR_FP64)
         return fail(CTR_ERR_INVALID, "precision");
     const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
+    // an arithmetic the handle's options do not use is planned on first use (the handle's plan, not its state)
+    CTR_TRY(ctr::ensure_schedule(const_cast<ctr_ibim*>(s), pol));
     const ctr::PairSchedule& p = s->sched[pol];
     if (block_targets) *block_targets = p.BS;
     if (tile) *tile = p.tile;
@@ -335,6 +337,8 @@ int ctr_ibim_pair_schedule(const ctr_ibim* s, int precision, int64_t* one_sided,
     if (precision != CTR_FP32_REFINE && precision != CTR_DF64 && precision != CTR_FP64)
         return fail(CTR_ERR_INVALID, "precision");
     const int pol = (precision == CTR_FP32_REFINE) ? 0 : (precision == CTR_DF64 ? 1 : 2);
+    // an arithmetic the handle's options do not use is planned on first use (the handle's plan, not its state)
+    CTR_TRY(ctr::ensure_schedule(const_cast<ctr_ibim*>(s), pol));
     const ctr::PairSchedule& p = s->sched[pol];
     if (one_sided) *one_sided = p.pairs_one;
     if (symmetric) *symmetric = p.pairs_sym;

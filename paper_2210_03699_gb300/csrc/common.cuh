@@ -120,6 +120,7 @@ struct PairItem {
 // The pair schedule of one system for one pair arithmetic: items (device list
 // sorted by decreasing cost; host copy and costs kept for the engine).
 struct PairSchedule {
+    bool planned = false; // items built (an arithmetic the handle's options do not use is planned on first use)
     int var = 0;          // kernel variant (FP32: index into pk::kVar32; 0 for the fixed shapes)
     int R = 1;            // targets per thread
     int BS = 256;         // nodes per target block
@@ -275,6 +276,7 @@ int launch_tree(ctr_ibim* s, int pol);
 int64_t tree_bytes(const ctr_ibim* s);
 // schedule.cu: symmetric / one-sided pair schedules of a handle
 int build_schedules(ctr_ibim* s, const int slots[3]);
+int ensure_schedule(ctr_ibim* s, int pol);   // plans pair arithmetic `pol` if it has not been planned yet
 // the handle's exact node accumulators, allocated and cleared (pairsum.cu)
 int alloc_accumulators(ctr_ibim* s);
 // the weights a = h^3 W x1 / (4 pi), b = h^3 W x2 / (4 pi) of x (2M doubles, device) into the packed

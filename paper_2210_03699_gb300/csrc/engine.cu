@@ -912,6 +912,9 @@ int engine_admit(Engine* e, ctr_ibim* s, int* slot_out) {
     // a treecode handle's FP32 operator carries its own approximation error (degree 6): its refinement
     // residuals are always formed in full with the residual arithmetic
     d.res_update = (d.refine && s->opt.residual_mode == CTR_RESIDUAL_UPDATE && !s->tree) ? 1 : 0;
+    // the slot's two arithmetics were planned at setup from the same options: these are guards
+    CTR_TRY(ensure_schedule(s, policy_index(d.inner_prec)));
+    CTR_TRY(ensure_schedule(s, policy_index(d.res_prec)));
     d.upd = 0;
     d.part = 0;
     for (int p = 0; p < 3; ++p) {   // parts of one application (treecode handles: always whole)

@@ -322,6 +322,7 @@ int schedule_slots(int sms, int slots[3]) {
 }
 
 int launch_schedule(ctr_ibim* s, int pol, const void* src, const PairConsts& kc) {
+    CTR_TRY(ensure_schedule(s, pol));
     int sms = 0;
     CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
     if (pol == 0) return with_var32(s->sched[0].var, SchedRun{s, src, &kc, sms});
@@ -329,33 +330,67 @@ int launch_schedule(ctr_ibim* s, int pol, const void* src, const PairConsts& kc)
     return sched_launch<Fp64Policy, kR64, kChunk64, 1>(s, 2, src, kc, sms);
 }
 
-int build_schedules(ctr_ibim* s, const int slots[3]) {
+// Near flags on base blocks of g0 nodes (the smallest target block, coarsened for huge systems).
+static int near_flags(ctr_ibim* s, std::vector<uint8_t>& flags, int& g0, int& nb0) {
     const int64_t M = s->M;
-    // near flags on base blocks of g0 nodes (the smallest target block, coarsened for huge systems)
-    int g0 = kThreads;
+    g0 = kThreads;
     while ((M + g0 - 1) / g0 > kMaxBaseBlocks) g0 *= 2;
-    const int nb0 = (int)((M + g0 - 1) / g0);
+    nb0 = (int)((M + g0 - 1) / g0);
     DevBuf d_flags;
     CTR_TRY(d_flags.alloc((size_t)nb0 * nb0));
     CTR_CUDA_TRY(cudaMemsetAsync(d_flags.p, 0, (size_t)nb0 * nb0, s->stream));
     near_flags_kernel<<<grid_for(M, 256), 256, 0, s->stream>>>(s->corr_ptr.as<int32_t>(), s->excl.as<int32_t>(), M,
                                                               g0, nb0, d_flags.as<uint8_t>());
     CTR_LAUNCHED();
-    std::vector<uint8_t> flags((size_t)nb0 * nb0);
+    flags.assign((size_t)nb0 * nb0, 0);
     CTR_CUDA_TRY(cudaMemcpyAsync(flags.data(), d_flags.p, flags.size(), cudaMemcpyDeviceToHost, s->stream));
     CTR_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    CTR_TRY(alloc_accumulators(s));
-    CTR_TRY(s->counter.alloc(sizeof(int) * 4));
+    return CTR_OK;
+}
+
+// The float-float (pol 1) or FP64 (pol 2) schedule with its fixed shape.
+static int plan_fixed(ctr_ibim* s, int pol, const std::vector<uint8_t>& flags, int g0, int nb0, const int slots[3]) {
     const int Rs[3] = {0, kRdf, kR64};   // targets per thread of the fixed shapes
     const int tiles[3] = {0, Df64Policy::kTile, Fp64Policy::kTile};
-    for (int p = 1; p < 3; ++p) {
-        plan_schedule(s->sched[p], M, Rs[p], tiles[p], kSymCost[p], kUnitRate[p] * kItemSeconds[p], flags, g0, nb0,
-                      slots[p]);
-        CTR_TRY(upload_schedule(s->sched[p], M, s->stream));
-    }
+    plan_schedule(s->sched[pol], s->M, Rs[pol], tiles[pol], kSymCost[pol], kUnitRate[pol] * kItemSeconds[pol], flags,
+                  g0, nb0, slots[pol]);
+    CTR_TRY(upload_schedule(s->sched[pol], s->M, s->stream));
+    s->sched[pol].planned = true;
+    return CTR_OK;
+}
+
+// Setup: the FP32 schedule (tuned), and the float-float and FP64 ones if the handle's options use them
+// (inner precision or refinement residual); an unused one is planned on first use (ensure_schedule).
+int build_schedules(ctr_ibim* s, const int slots[3]) {
+    std::vector<uint8_t> flags;
+    int g0 = 0, nb0 = 0;
+    CTR_TRY(near_flags(s, flags, g0, nb0));
+    CTR_TRY(alloc_accumulators(s));
+    CTR_TRY(s->counter.alloc(sizeof(int) * 4));
+    const int prec = s->opt.precision;
+    const bool uses[3] = {true, prec == CTR_DF64 || (prec == CTR_FP32_REFINE && s->opt.residual == CTR_DF64),
+                          prec == CTR_FP64 || (prec == CTR_FP32_REFINE && s->opt.residual == CTR_FP64)};
+    for (int p = 1; p < 3; ++p)
+        if (uses[p]) CTR_TRY(plan_fixed(s, p, flags, g0, nb0, slots));
     int sms = 0;
     CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-    return plan_fp32(s, flags, g0, nb0, sms);
+    CTR_TRY(plan_fp32(s, flags, g0, nb0, sms));
+    s->sched[0].planned = true;
+    return CTR_OK;
+}
+
+int ensure_schedule(ctr_ibim* s, int pol) {
+    if (pol < 0 || pol > 2) return fail(CTR_ERR_INVALID, "pair arithmetic");
+    if (s->sched[pol].planned) return CTR_OK;
+    if (pol == 0 || s->tree) return fail(CTR_ERR_INVALID, "schedule missing");   // planned at setup
+    int sms = 0;
+    CTR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+    int slots[3] = {0, 0, 0};
+    CTR_TRY(schedule_slots(sms, slots));
+    std::vector<uint8_t> flags;
+    int g0 = 0, nb0 = 0;
+    CTR_TRY(near_flags(s, flags, g0, nb0));
+    return plan_fixed(s, pol, flags, g0, nb0, slots);
 }
 
 }  // namespace ctr

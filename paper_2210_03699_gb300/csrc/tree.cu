@@ -322,6 +322,7 @@ int build_tree_schedules(ctr_ibim* s, const int slots[3]) {
         sc.pairs_one = P.near_pairs;
         sc.pairs_sym = 0;
         sc.total_cost = near_total;
+        sc.planned = true;
         // near items in decreasing cost (the host copy follows the device order)
         std::vector<int> order(items.size());
         std::iota(order.begin(), order.end(), 0);
